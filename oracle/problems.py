@@ -1,0 +1,134 @@
+"""Boundary data, loads and exact solutions of the two test families.
+
+Terzaghi column (reading A9; the paper's model, Sec. 2.1, with its standard
+consolidation set-up): unit square, traction (0, -load) on the top for every
+t_n >= tau, drained top (p = 0), fixed bottom (u = 0), roller sides (u_x = 0),
+no flux elsewhere, initial state x0 = 0.
+
+Trigonometric manufactured solution (Sec. 4.1): u1 = u2 = p =
+cos(t) cos(3 pi x) cos(3 pi y), Dirichlet data for u and p on all sides, initial
+state the exact solution at t = 0. The printed body force f matches the PDE; the
+printed source g carries a sign error in its first term (it must be symmetric
+under x <-> y because the solution is). Reading A3: both sources are derived
+here from the PDE (biotsys1)-(biotsys2) for the stated solution.
+"""
+import numpy as np
+
+from .mesh import boundary_nodes
+from .fem import lame, p1_geometry
+
+K3 = 3.0 * np.pi
+
+
+def mms_exact(x, y, t):
+    """Exact (u1, u2, p) of the trigonometric test at time t."""
+    v = np.cos(t) * np.cos(K3 * x) * np.cos(K3 * y)
+    return v, v, v
+
+
+def mms_sources(x, y, t, lam, mu, alpha, K):
+    """Body force (f1, f2) and fluid source g for the trigonometric test.
+
+    With c = cos, s = sin of 3 pi x / 3 pi y and k = 3 pi:
+      f1 = k^2 cos t [(lam + 3 mu) cx cy - (lam + mu) sx sy] - alpha k cos t sx cy
+      f2 = k^2 cos t [(lam + 3 mu) cx cy - (lam + mu) sx sy] - alpha k cos t cx sy
+      g  = alpha k sin t (sx cy + cx sy) + 2 K k^2 cos t cx cy
+    """
+    k = K3
+    cx, sx = np.cos(k * x), np.sin(k * x)
+    cy, sy = np.cos(k * y), np.sin(k * y)
+    common = k * k * np.cos(t) * ((lam + 3 * mu) * cx * cy - (lam + mu) * sx * sy)
+    f1 = common - alpha * k * np.cos(t) * sx * cy
+    f2 = common - alpha * k * np.cos(t) * cx * sy
+    g = alpha * k * np.sin(t) * (sx * cy + cx * sy) + 2.0 * K * k * k * np.cos(t) * cx * cy
+    return f1, f2, g
+
+
+def mms_f_as_printed(x, y, t, lam, mu, alpha):
+    """The body force exactly as Sec. 4.1 prints it (used only to pin mms_sources)."""
+    k = K3
+    cx, sx = np.cos(k * x), np.sin(k * x)
+    cy, sy = np.cos(k * y), np.sin(k * y)
+    f1 = -k * np.cos(t) * (alpha * sx * cy - k * (lam + 3 * mu) * cx * cy + k * (lam + mu) * sx * sy)
+    f2 = -k * np.cos(t) * (alpha * cx * sy - k * (lam + 3 * mu) * cx * cy + k * (lam + mu) * sx * sy)
+    return f1, f2
+
+
+def area_load(coords, tris, values_at):
+    """Nodal load int fun * phi_a by the 3-point edge-midpoint rule (exact to degree 2).
+
+    values_at(x, y) evaluates the source at arrays of points. Returns a nodal
+    vector of length n_nodes.
+    """
+    area, _, _ = p1_geometry(coords, tris)
+    p = coords[tris]
+    out = np.zeros(coords.shape[0])
+    mids = [(0, 1), (1, 2), (2, 0)]
+    fm = [values_at(0.5 * (p[:, a, 0] + p[:, b, 0]), 0.5 * (p[:, a, 1] + p[:, b, 1])) for a, b in mids]
+    # phi_a is 1/2 at the midpoints of the two edges through vertex a, 0 at the third.
+    for a in range(3):
+        s = np.zeros(tris.shape[0])
+        for q, (i0, i1) in enumerate(mids):
+            if a in (i0, i1):
+                s += 0.5 * fm[q]
+        np.add.at(out, tris[:, a], area / 3.0 * s)
+    return out
+
+
+def top_traction_y(n, coords, ty):
+    """Nodal load int t_y phi_a ds over the top edge for a constant traction t_y."""
+    top = boundary_nodes(n)["top"]
+    out = np.zeros(coords.shape[0])
+    for k in range(n):
+        a, b = top[k], top[k + 1]
+        length = coords[b, 0] - coords[a, 0]
+        out[a] += 0.5 * length * ty
+        out[b] += 0.5 * length * ty
+    return out
+
+
+def dirichlet_dofs(case):
+    """Sorted array of constrained DOFs for the case's boundary-condition family."""
+    sides = boundary_nodes(case.n)
+    if case.problem == "terzaghi":
+        d = [3 * sides["bottom"], 3 * sides["bottom"] + 1,
+             3 * sides["left"], 3 * sides["right"], 3 * sides["top"] + 2]
+    elif case.problem == "mms":
+        nodes = np.unique(np.concatenate(list(sides.values())))
+        d = [3 * nodes, 3 * nodes + 1, 3 * nodes + 2]
+    else:
+        raise ValueError(case.problem)
+    return np.unique(np.concatenate(d))
+
+
+def dirichlet_values(case, coords, dofs, t):
+    """Prescribed values g_D(t) at the constrained DOFs."""
+    if case.problem == "terzaghi":
+        return np.zeros(dofs.shape[0])
+    node, field = dofs // 3, dofs % 3
+    u1, u2, p = mms_exact(coords[node, 0], coords[node, 1], t)
+    return np.where(field == 0, u1, np.where(field == 1, u2, p))
+
+
+def initial_state(case, coords):
+    """x0 in node-interleaved layout."""
+    x0 = np.zeros(3 * coords.shape[0])
+    if case.problem == "mms":
+        u1, u2, p = mms_exact(coords[:, 0], coords[:, 1], 0.0)
+        x0[0::3], x0[1::3], x0[2::3] = u1, u2, p
+    return x0
+
+
+def load_vector(case, coords, tris, t):
+    """Unconstrained right-hand side f^n = [F^n; -tau G^n] of Eq. (fullysystem) at t = t_n."""
+    nn = coords.shape[0]
+    out = np.zeros(3 * nn)
+    if case.problem == "terzaghi":
+        out[1::3] += top_traction_y(case.n, coords, -case.load)
+    else:
+        lam, mu = lame(case.E, case.nu)
+        K = float(case.kappa_elem()[0])
+        out[0::3] += area_load(coords, tris, lambda x, y: mms_sources(x, y, t, lam, mu, case.alpha, K)[0])
+        out[1::3] += area_load(coords, tris, lambda x, y: mms_sources(x, y, t, lam, mu, case.alpha, K)[1])
+        out[2::3] += -case.tau * area_load(coords, tris, lambda x, y: mms_sources(x, y, t, lam, mu, case.alpha, K)[2])
+    return out
