@@ -1,0 +1,206 @@
+/*
+ * biot_pint.h -- C ABI of the GB300 parallel-in-time Biot solver.
+ *
+ * Method: arxiv 2310.10430, "A Parallel-in-time Method Based on Preconditioner
+ * for Biot's Model". The quasi-static two-field Biot model (Sec. 2.1, Eqs.
+ * biotsys1-biotsys2) is discretised with stabilised P1-P1 elements and backward
+ * Euler (Sec. 2.2, Eq. diseq1), giving one saddle-point system per time step
+ * (Eq. fullysystem / axb):
+ *
+ *     AA x_n = A' x_{n-1} + f^n,   AA = [[A, B], [B^T, -(tau + beta/K) C]],
+ *                                  A' = [[0, 0], [B^T, -(beta/K) C]].
+ *
+ * The inverted time stepping of Algorithms 2-3 (Sec. 3.2) swaps the loops: the
+ * outer loop iterates the preconditioned solver, the inner loop runs over the
+ * time steps. Every outer iteration ("sweep") forms, for all active time steps
+ * at once, the residual r_n = f^n + A' x_{n-1} - AA x_n, applies the block
+ * preconditioner P1 (Eq. p1, lower block triangular) or P2 (Eq. p2, block
+ * diagonal) built on the approximate Schur complement S = (tau + beta/K) C, and
+ * updates x_n with one cycle of the inner Krylov solver K(P, AA, X, b, n_iter).
+ *
+ * Conventions (all entry points):
+ *  - Unknowns are node-interleaved: DOF 3*v + f, f = 0 (u_x), 1 (u_y), 2 (p);
+ *    node v = j*(n+1) + i of the structured n x n grid (x fastest).
+ *  - Host buffers are owned by the caller; device memory is owned by the
+ *    context and released by biot_destroy. Work is stream-ordered on the CUDA
+ *    stream given to biot_mesh_create; calls that return host data synchronise
+ *    that stream before returning.
+ *  - No C++ exception or exit() crosses the ABI. Every call returns a
+ *    biot_status; biot_last_error() gives a one-line message for the last
+ *    failure on that context. A call made in the wrong order returns
+ *    BIOT_E_STATE and changes nothing.
+ *  - A context is not thread safe; distinct contexts are independent.
+ */
+#ifndef BIOT_PINT_H
+#define BIOT_PINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct biot_ctx biot_ctx;
+
+typedef enum {
+  BIOT_OK = 0,
+  BIOT_E_INVALID = 1,        /* bad argument (null pointer, size, enum) */
+  BIOT_E_OOM = 2,            /* device allocation failed */
+  BIOT_E_CUDA = 3,           /* CUDA runtime error (message in biot_last_error) */
+  BIOT_E_STATE = 4,          /* call made before the step it depends on */
+  BIOT_E_NOT_CONVERGED = 5,  /* max_outer sweeps done, tolerance not met; state stays readable */
+  BIOT_E_DIVERGED = 6,       /* residual non-finite or grew by more than 1e6 */
+  BIOT_E_TIMEOUT = 7         /* a bounded device wait ran out (batched persistent launch) */
+} biot_status;
+
+typedef enum {
+  BIOT_PRECOND_TRI = 1,      /* P1 = [[A, 0], [B^T, -S]], Eq. (p1) */
+  BIOT_PRECOND_DIAG = 2      /* P2 = [[A, 0], [0, -S]],   Eq. (p2) */
+} biot_precond_kind;
+
+typedef enum {
+  BIOT_FP64 = 0,             /* every kernel in FP64 */
+  BIOT_FP32 = 1,             /* FP32 sweep (SpMM, preconditioner, Krylov), FP64 true residual + refinement */
+  BIOT_BF16VAL_FP32ACC = 2   /* as BIOT_FP32 with the SpMM matrix values stored in BF16 */
+} biot_precision;
+
+typedef enum { BIOT_TERZAGHI = 0, BIOT_MMS_TRIG = 1 } biot_problem;
+
+typedef enum {
+  BIOT_BETA_H2 = 0,          /* beta = h^2 / (4 (lambda + 2 mu)) (dimensionally consistent reading) */
+  BIOT_BETA_H = 1,           /* beta = h / (4 (lambda + 2 mu)), as printed in Sec. 2.2 */
+  BIOT_BETA_NONE = 2         /* no stabilisation */
+} biot_beta_mode;
+
+typedef enum {
+  BIOT_SCHED_TOL = 0,        /* retire the oldest active step once its relative residual <= tol */
+  BIOT_SCHED_PAPER = 1       /* every step gets exactly `window` outer iterations (N_thread of Alg. 3) */
+} biot_schedule;
+
+typedef struct {
+  double E, nu, alpha;       /* Young's modulus, Poisson ratio, Biot-Willis constant (Sec. 2.1) */
+  double kappa_const;        /* permeability / viscosity K, used when kappa_elem is NULL */
+  const double* kappa_elem;  /* host, nullable: per-triangle K, length 2 n^2, triangle 2(j n + i) lower,
+                                2(j n + i) + 1 upper of cell (i, j); copied during biot_assemble */
+  double tau;                /* time step */
+  int32_t n_t;               /* number of time steps N_t (>= 1) */
+  int32_t problem;           /* biot_problem */
+  int32_t beta_mode;         /* biot_beta_mode */
+  double load;               /* Terzaghi top traction magnitude (traction (0, -load) for t >= tau) */
+  int32_t n_iter;            /* Krylov steps per call of K (1..32) */
+  int32_t window;            /* BIOT_SCHED_TOL: max active steps (0 = N_t); BIOT_SCHED_PAPER: iterations per step */
+  int32_t schedule;          /* biot_schedule */
+  int32_t precision;         /* biot_precision */
+} biot_params;
+
+typedef struct {
+  int32_t n;                 /* cells per side */
+  int32_t n_nodes, n_dof;    /* (n+1)^2, 3 (n+1)^2 */
+  int64_t nnz;               /* nonzeros of AA's pattern, 9 (7 n^2 + 6 n + 1) */
+  int32_t n_pairs;           /* node adjacency pairs P = 7 n^2 + 6 n + 1 */
+  int32_t n_t;               /* time steps (0 before biot_assemble) */
+  int32_t window_cap;        /* columns of the device Krylov work buffers */
+  int32_t band_u, band_p;    /* half-bandwidths of A (u-ordering 2 v + f) and S (node ordering) */
+  int32_t precond;           /* biot_precond_kind set up, 0 if none */
+  int32_t precision;         /* biot_precision in use */
+  double beta;               /* stabilisation factor actually used */
+  int64_t device_bytes;      /* device memory held by the context */
+} biot_info;
+
+/* ---- context life cycle ------------------------------------------------- */
+
+/* Create a context for the structured n x n right-triangle mesh of [0,Lx]x[0,Ly]
+ * (uniform grid with h = Lx/n, each cell split along its "/" diagonal; Sec. 4,
+ * "uniform right triangular grid"). Builds the node adjacency and the int32 CSR
+ * pattern of AA on the device. cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream). Errors: BIOT_E_INVALID (n < 1, n > 4096, Lx or Ly <= 0, out
+ * NULL), BIOT_E_OOM, BIOT_E_CUDA. */
+biot_status biot_mesh_create(int32_t n, double Lx, double Ly, void* cuda_stream, biot_ctx** out);
+
+/* Assemble AA, A' (Eq. fullysystem) and the right-hand sides f^n for n = 1..N_t
+ * (Eq. axb), apply the Dirichlet data, and set x_0 (Sec. 2.1 initial data).
+ * Element-parallel coloured assembly on the device (8 colours, no atomics).
+ * Allocates the solution store X[N_dof][N_t+1] and the Krylov work buffers for
+ * min(N_t, window) columns (window 0 = N_t). May be called again to reassemble.
+ * Errors: BIOT_E_INVALID (null params, E <= 0, nu outside (-1, 0.5), tau <= 0,
+ * n_t < 1, n_iter outside 1..32, bad enum, kappa <= 0), BIOT_E_OOM, BIOT_E_CUDA. */
+biot_status biot_assemble(biot_ctx* ctx, const biot_params* params);
+
+/* Build the preconditioner of Sec. 3.1: extract A (u-block of AA) and
+ * S = (tau + beta/K) C (minus the p-block of AA) as band matrices and factor
+ * both by band Cholesky on the device, so that the block solves of P1/P2 are
+ * exact up to rounding. Errors: BIOT_E_STATE (before biot_assemble),
+ * BIOT_E_INVALID (kind), BIOT_E_CUDA (including a non-positive pivot). */
+biot_status biot_precond_setup(biot_ctx* ctx, int32_t kind);
+
+/* Run the inverted time stepping (Alg. 3) as windowed snapshot sweeps: at sweep
+ * w every active step n uses x_{n-1} and x_n from the state after sweep w-1;
+ * step n becomes active at sweep n, which reproduces Alg. 3's iterates
+ * X^{n,m}, m = w - n + 1. Tol schedule: the oldest active step retires once its
+ * predecessor is retired and |D^{-1/2} r_n| <= tol |D^{-1/2} b_n| (D = |diag AA|);
+ * paper schedule: every step gets `window` outer iterations, tol is ignored.
+ * With precision BIOT_FP32/BF16, the sweep runs in reduced precision as the
+ * correction solver of an FP64 iterative refinement on the space-time system.
+ * Outputs (nullable): sweeps_done, final_rel_res = relative equilibrated
+ * space-time residual |D^{-1/2}(F - calA X)| / |D^{-1/2} F| in FP64.
+ * Returns BIOT_E_NOT_CONVERGED after max_outer sweeps without convergence
+ * (state readable), BIOT_E_DIVERGED, BIOT_E_STATE (no preconditioner). */
+biot_status biot_pint_solve(biot_ctx* ctx, double tol, int32_t max_outer,
+                            int32_t* sweeps_done, double* final_rel_res);
+
+/* One outer iteration (sweep) over the window of steps lo..hi (1 <= lo <= hi <= N_t,
+ * hi - lo + 1 <= window_cap): residuals from the current state, one cycle of
+ * K = right-preconditioned FGMRES(n_iter) per step, state updated in place.
+ * rel_out (host, nullable, length hi - lo + 1) receives the relative residual
+ * of each step before the update. This is the unit of work the paper's threads
+ * perform in one wave of Alg. 4 (one b^{n_t} + one call of K). */
+biot_status biot_sweep(biot_ctx* ctx, int32_t lo, int32_t hi, double* rel_out);
+
+/* Relative equilibrated residuals of steps lo..hi for the current state (no update). */
+biot_status biot_residual_norms(biot_ctx* ctx, int32_t lo, int32_t hi, double* rel_out);
+
+/* ---- data exchange ------------------------------------------------------ */
+
+/* Copy x_step (0 <= step <= N_t; step 0 is x_0) to host_out[N_dof]. */
+biot_status biot_get_solution(const biot_ctx* ctx, int32_t step, double* host_out);
+
+/* Copy steps lo..hi of the solution store to/from host[(hi-lo+1)][N_dof]
+ * (step-major). For end-to-end runs and checkpoint/resume. */
+biot_status biot_get_state(const biot_ctx* ctx, int32_t lo, int32_t hi, double* host);
+biot_status biot_set_state(biot_ctx* ctx, int32_t lo, int32_t hi, const double* host);
+
+/* Copy the CSR of AA (rowptr[N_dof+1], col[nnz] int32, val[nnz] FP64) and the
+ * pressure-pressure entries of A' (ap_pp[P], node-pair order) to the host. Any
+ * output may be NULL. nnz_out receives the number of nonzeros. */
+biot_status biot_get_csr(const biot_ctx* ctx, int32_t* rowptr, int32_t* col, double* val,
+                         double* ap_pp, int64_t* nnz_out);
+
+/* Copy the right-hand sides f^n, n = 0..N_t, to host[(N_t+1)][N_dof] (row 0 is zero). */
+biot_status biot_get_rhs(const biot_ctx* ctx, double* host);
+
+/* Compute the window residuals r_n = f^n + A' x_{n-1} - AA x_n, n = lo..hi, of
+ * the current state in the context's precision and copy them to
+ * host[(hi-lo+1)][N_dof] (step-major). */
+biot_status biot_get_residual(biot_ctx* ctx, int32_t lo, int32_t hi, double* host);
+
+/* Apply P^{-1} (the preconditioner set up) to ncols host vectors
+ * host_in[ncols][N_dof] -> host_out[ncols][N_dof] on the device (ncols <= window_cap). */
+biot_status biot_precond_apply(biot_ctx* ctx, int32_t ncols, const double* host_in, double* host_out);
+
+biot_status biot_get_info(const biot_ctx* ctx, biot_info* out);
+
+/* Kernel launches issued by this library since it was loaded (all contexts). */
+int64_t biot_launch_count(void);
+
+/* One-line description of the last error on ctx (or of the last failed
+ * biot_mesh_create when ctx is NULL). Never NULL. */
+const char* biot_last_error(const biot_ctx* ctx);
+
+void biot_destroy(biot_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BIOT_PINT_H */

@@ -1,0 +1,545 @@
+// C ABI of the parallel-in-time Biot solver (include/biot_pint.h).
+//
+// Host-side orchestration only: argument checks, device memory, the window
+// schedule of the inverted time stepping (Alg. 3 as snapshot sweeps), and data
+// exchange. Every arithmetic step of the method runs in the kernels of
+// assembly.cu, spmm.cu, band.cu and krylov.cu.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <new>
+
+namespace biot {
+
+std::atomic<int64_t> g_launches{0};
+int krylov_record_doubles();
+
+namespace {
+thread_local std::string g_create_error = "no error";
+}
+
+biot_status fail(biot_ctx* ctx, biot_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else g_create_error = buf;
+  return st;
+}
+
+biot_status cuda_check(biot_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return BIOT_OK;
+  return fail(ctx, e == cudaErrorMemoryAllocation ? BIOT_E_OOM : BIOT_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+biot_status dalloc(biot_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(ctx, e == cudaErrorMemoryAllocation ? BIOT_E_OOM : BIOT_E_CUDA, "cudaMalloc(%zu): %s", bytes,
+                cudaGetErrorString(e));
+  }
+  ctx->allocs.push_back(*p);
+  ctx->device_bytes += (int64_t)bytes;
+  return BIOT_OK;
+}
+
+void dfree_all(biot_ctx* ctx) {
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  ctx->device_bytes = 0;
+}
+
+namespace {
+
+// Tiled transposes between the device layout [dof][ld] (time fastest) and the
+// host layout [step][n_dof].
+__global__ void k_dof_to_step(const double* __restrict__ src, int lds, int col0, int ncols, int nrows,
+                              const double* __restrict__ rowscale, double* __restrict__ dst) {
+  __shared__ double tile[32][33];
+  const int r0 = blockIdx.x * 32, cb = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int r = r0 + k, c = cb + threadIdx.x;
+    double v = 0.0;
+    if (r < nrows && c < ncols) {
+      v = src[(size_t)r * lds + col0 + c];
+      if (rowscale) v /= rowscale[r];
+    }
+    tile[k][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int c = cb + k, r = r0 + threadIdx.x;
+    if (r < nrows && c < ncols) dst[(size_t)c * nrows + r] = tile[threadIdx.x][k];
+  }
+}
+
+__global__ void k_step_to_dof(const double* __restrict__ src, int ncols, int nrows, const double* __restrict__ rowscale,
+                              double* __restrict__ dst, int ldd, int col0) {
+  __shared__ double tile[32][33];
+  const int r0 = blockIdx.x * 32, cb = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int c = cb + k, r = r0 + threadIdx.x;
+    tile[k][threadIdx.x] = (r < nrows && c < ncols) ? src[(size_t)c * nrows + r] : 0.0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int r = r0 + k, c = cb + threadIdx.x;
+    if (r < nrows && c < ncols) {
+      double v = tile[threadIdx.x][k];
+      if (rowscale) v *= rowscale[r];
+      dst[(size_t)r * ldd + col0 + c] = v;
+    }
+  }
+}
+
+// |D^{-1/2} f_ST|^2 contributions per step n (f_ST = f^n, plus A' x0 for n = 1).
+__global__ void k_fst_norms(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
+                            const int32_t* __restrict__ rowptr, const double* __restrict__ val,
+                            const double* __restrict__ apval, const double* __restrict__ dsc,
+                            const double* __restrict__ X, const double* __restrict__ F, int ldx, int lo, int ncols,
+                            double* __restrict__ part, int ldp) {
+  __shared__ double sm[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = (nn + gridDim.x - 1) / gridDim.x;
+  const int vb = blockIdx.x * per, ve = min(nn, vb + per);
+  for (int cb = 0; cb < ncols; cb += 32) {
+    const int c = cb + lane;
+    const bool cv = c < ncols;
+    const int tn = lo + (cv ? c : 0);
+    double acc = 0.0;
+    for (int v = vb + warp; v < ve; v += 8) {
+      double b2 = F[(size_t)(3 * v + 2) * ldx + tn];
+      if (tn == 1) {
+        const int32_t np = nodeptr[v];
+        const int deg = nodeptr[v + 1] - np;
+        const int32_t r2 = rowptr[3 * v] + 6 * deg;
+        for (int k = 0; k < deg; ++k) {
+          const int m = nbr[np + k];
+          b2 += val[r2 + 3 * k] * X[(size_t)(3 * m) * ldx] + val[r2 + 3 * k + 1] * X[(size_t)(3 * m + 1) * ldx] +
+                apval[np + k] * X[(size_t)(3 * m + 2) * ldx];
+        }
+      }
+      const double p0 = dsc[3 * v] * F[(size_t)(3 * v) * ldx + tn];
+      const double p1 = dsc[3 * v + 1] * F[(size_t)(3 * v + 1) * ldx + tn];
+      const double p2 = dsc[3 * v + 2] * b2;
+      if (cv) acc += p0 * p0 + p1 * p1 + p2 * p2;
+    }
+    sm[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && cv) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += sm[w][lane];
+      part[(size_t)blockIdx.x * ldp + c] = s;
+    }
+    __syncthreads();
+  }
+}
+
+bool bad_ctx(const biot_ctx* ctx) { return ctx == nullptr; }
+
+biot_status need_assembled(biot_ctx* ctx) {
+  if (!ctx->assembled) return fail(ctx, BIOT_E_STATE, "biot_assemble has not been called");
+  return BIOT_OK;
+}
+
+biot_status need_precond(biot_ctx* ctx) {
+  BIOT_TRY(need_assembled(ctx));
+  if (ctx->precond == 0) return fail(ctx, BIOT_E_STATE, "biot_precond_setup has not been called");
+  return BIOT_OK;
+}
+
+biot_status check_window(biot_ctx* ctx, int lo, int hi) {
+  if (lo < 1 || hi > ctx->n_t || lo > hi)
+    return fail(ctx, BIOT_E_INVALID, "window [%d, %d] outside 1..%d", lo, hi, ctx->n_t);
+  if (hi - lo + 1 > ctx->wcap)
+    return fail(ctx, BIOT_E_INVALID, "window of %d steps exceeds the work buffers (%d)", hi - lo + 1, ctx->wcap);
+  return BIOT_OK;
+}
+
+// Residual of steps lo..lo+ncols-1 into V_0 (equilibrated), |d r|^2 and |d b|^2 into the
+// column scalars; optionally the relative residuals to the host.
+biot_status residual_window(biot_ctx* ctx, int lo, int ncols, double* rel_host) {
+  launch_residual(ctx, lo, ncols, ctx->V, ctx->wcap);
+  reduce_partials(ctx, 2, ncols, ctx->colscal + CS_RR * ctx->wcap, ctx->wcap, 0);
+  BIOT_CU(ctx, cudaGetLastError());
+  if (rel_host) {
+    std::vector<double> rb(2 * (size_t)ctx->wcap);
+    BIOT_CU(ctx, cudaMemcpyAsync(rb.data(), ctx->colscal, sizeof(double) * 2 * ctx->wcap, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < ncols; ++c) {
+      const double rr = std::sqrt(rb[c]), bb = std::sqrt(rb[ctx->wcap + c]);
+      rel_host[c] = bb > 0.0 ? rr / bb : (rr == 0.0 ? 0.0 : INFINITY);
+    }
+  }
+  return BIOT_OK;
+}
+
+biot_status spacetime_residual(biot_ctx* ctx, double* out) {
+  double num = 0.0, den = 0.0;
+  std::vector<double> rb(ctx->wcap);
+  for (int lo = 1; lo <= ctx->n_t; lo += ctx->wcap) {
+    const int nc = std::min(ctx->wcap, ctx->n_t - lo + 1);
+    launch_residual(ctx, lo, nc, ctx->V, ctx->wcap);
+    reduce_partials(ctx, 1, nc, ctx->colscal + CS_RR * ctx->wcap, ctx->wcap, 0);
+    BIOT_CU(ctx, cudaMemcpyAsync(rb.data(), ctx->colscal + CS_RR * ctx->wcap, sizeof(double) * nc,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < nc; ++c) num += rb[c];
+    BIOT_LAUNCH(k_fst_norms, kRedBlocks, 256, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr, ctx->nbr, ctx->rowptr,
+                ctx->val, ctx->apval, ctx->dsc, ctx->X, ctx->F, ctx->ldx, lo, nc, ctx->part, ctx->wcap);
+    reduce_partials(ctx, 1, nc, ctx->colscal + CS_BB * ctx->wcap, ctx->wcap, 0);
+    BIOT_CU(ctx, cudaMemcpyAsync(rb.data(), ctx->colscal + CS_BB * ctx->wcap, sizeof(double) * nc,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < nc; ++c) den += rb[c];
+  }
+  *out = den > 0.0 ? std::sqrt(num / den) : std::sqrt(num);
+  return BIOT_OK;
+}
+
+biot_status sweep_impl(biot_ctx* ctx, int lo, int hi, double* rel_out) {
+  const int ncols = hi - lo + 1;
+  BIOT_TRY(residual_window(ctx, lo, ncols, rel_out));
+  BIOT_TRY(fgmres_cycle(ctx, lo, 0, ncols));
+  return BIOT_OK;
+}
+
+// Work buffers sized by N_t, the window capacity and n_iter.
+biot_status alloc_time_buffers(biot_ctx* ctx) {
+  const size_t nd = ctx->n_dof, wc = ctx->wcap, ld = ctx->ldx;
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->X, sizeof(double) * nd * ld));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->F, sizeof(double) * nd * ld));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->V, sizeof(double) * nd * wc * (ctx->n_iter + 1)));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->Z, sizeof(double) * nd * wc * ctx->n_iter));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->Wv, sizeof(double) * nd * wc));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->part, sizeof(double) * kRedBlocks * (kMaxIter + 2) * wc));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->colscal, sizeof(double) * kColScalars * wc));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->H, sizeof(double) * krylov_record_doubles() * wc));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->hvec, sizeof(double) * 2 * (kMaxIter + 1) * wc));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->kcol, sizeof(int32_t) * wc));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->tu, sizeof(double) * 2 * ctx->n_nodes * wc));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->tp, sizeof(double) * ctx->n_nodes * wc));
+  return BIOT_OK;
+}
+
+void release_time_buffers(biot_ctx* ctx) {
+  void** bufs[] = {(void**)&ctx->X,       (void**)&ctx->F,    (void**)&ctx->V,    (void**)&ctx->Z,
+                   (void**)&ctx->Wv,      (void**)&ctx->part, (void**)&ctx->colscal, (void**)&ctx->H,
+                   (void**)&ctx->hvec,    (void**)&ctx->kcol, (void**)&ctx->tu,   (void**)&ctx->tp};
+  for (void** b : bufs) {
+    if (!*b) continue;
+    auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), *b);
+    if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+    cudaFree(*b);
+    *b = nullptr;
+  }
+}
+
+// Copy steps [lo, lo + nc) of a [dof][ld] device array to host[nc][n_dof] (staged through Wv).
+biot_status copy_out_steps(biot_ctx* ctx, const double* src, int lds, int col0, int nc, const double* rowscale,
+                           double* host) {
+  const int nd = ctx->n_dof;
+  for (int c = 0; c < nc; c += ctx->wcap) {
+    const int m = std::min(ctx->wcap, nc - c);
+    dim3 grid(div_up(nd, 32), div_up(m, 32)), block(32, 8);
+    BIOT_LAUNCH(k_dof_to_step, grid, block, 0, ctx->stream, src, lds, col0 + c, m, nd, rowscale, ctx->Wv);
+    BIOT_CU(ctx, cudaGetLastError());
+    BIOT_CU(ctx, cudaMemcpyAsync(host + (size_t)c * nd, ctx->Wv, sizeof(double) * nd * m, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  }
+  BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  return BIOT_OK;
+}
+
+biot_status copy_in_steps(biot_ctx* ctx, const double* host, int nc, const double* rowscale, double* dst, int ldd,
+                          int col0) {
+  const int nd = ctx->n_dof;
+  for (int c = 0; c < nc; c += ctx->wcap) {
+    const int m = std::min(ctx->wcap, nc - c);
+    BIOT_CU(ctx, cudaMemcpyAsync(ctx->Wv, host + (size_t)c * nd, sizeof(double) * nd * m, cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    dim3 grid(div_up(nd, 32), div_up(m, 32)), block(32, 8);
+    BIOT_LAUNCH(k_step_to_dof, grid, block, 0, ctx->stream, ctx->Wv, m, nd, rowscale, dst, ldd, col0 + c);
+    BIOT_CU(ctx, cudaGetLastError());
+  }
+  BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  return BIOT_OK;
+}
+
+}  // namespace
+}  // namespace biot
+
+using namespace biot;
+
+extern "C" {
+
+biot_status biot_mesh_create(int32_t n, double Lx, double Ly, void* cuda_stream, biot_ctx** out) {
+  if (!out) return fail(nullptr, BIOT_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > 4096) return fail(nullptr, BIOT_E_INVALID, "n = %d outside 1..4096", n);
+  if (!(Lx > 0.0) || !(Ly > 0.0)) return fail(nullptr, BIOT_E_INVALID, "domain size must be positive");
+  biot_ctx* ctx = new (std::nothrow) biot_ctx();
+  if (!ctx) return fail(nullptr, BIOT_E_OOM, "host allocation failed");
+  ctx->n = n;
+  ctx->Lx = Lx;
+  ctx->Ly = Ly;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->n_nodes = (n + 1) * (n + 1);
+  ctx->n_dof = 3 * ctx->n_nodes;
+  ctx->n_pairs = 7 * n * n + 6 * n + 1;
+  ctx->nnz = 9LL * ctx->n_pairs;
+  ctx->band_u = 2 * (n + 2) + 1;
+  ctx->band_p = n + 2;
+  biot_status st = BIOT_OK;
+  do {
+    if ((st = dalloc(ctx, (void**)&ctx->status, sizeof(int32_t))) != BIOT_OK) break;
+    if ((st = dalloc(ctx, (void**)&ctx->val, sizeof(double) * ctx->nnz)) != BIOT_OK) break;
+    if ((st = dalloc(ctx, (void**)&ctx->apval, sizeof(double) * ctx->n_pairs)) != BIOT_OK) break;
+    if ((st = dalloc(ctx, (void**)&ctx->dsc, sizeof(double) * ctx->n_dof)) != BIOT_OK) break;
+    if ((st = dalloc(ctx, (void**)&ctx->dmask, ctx->n_dof)) != BIOT_OK) break;
+    if ((st = dalloc(ctx, (void**)&ctx->kappa, sizeof(double) * 2 * (size_t)n * n)) != BIOT_OK) break;
+    if ((st = build_pattern(ctx)) != BIOT_OK) break;
+    if ((st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "pattern")) != BIOT_OK) break;
+  } while (0);
+  if (st != BIOT_OK) {
+    g_create_error = ctx->err;
+    dfree_all(ctx);
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return BIOT_OK;
+}
+
+biot_status biot_assemble(biot_ctx* ctx, const biot_params* p) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  if (!p) return fail(ctx, BIOT_E_INVALID, "params is NULL");
+  if (!(p->E > 0.0) || !(p->nu > -1.0 && p->nu < 0.5) || !(p->alpha > 0.0) || !(p->tau > 0.0))
+    return fail(ctx, BIOT_E_INVALID, "material or time step out of range");
+  if (p->n_t < 1 || p->n_iter < 1 || p->n_iter > kMaxIter)
+    return fail(ctx, BIOT_E_INVALID, "n_t >= 1 and 1 <= n_iter <= %d required", kMaxIter);
+  if (p->problem != BIOT_TERZAGHI && p->problem != BIOT_MMS_TRIG) return fail(ctx, BIOT_E_INVALID, "problem");
+  if (p->beta_mode < BIOT_BETA_H2 || p->beta_mode > BIOT_BETA_NONE) return fail(ctx, BIOT_E_INVALID, "beta_mode");
+  if (p->schedule != BIOT_SCHED_TOL && p->schedule != BIOT_SCHED_PAPER) return fail(ctx, BIOT_E_INVALID, "schedule");
+  if (p->precision != BIOT_FP64) return fail(ctx, BIOT_E_INVALID, "precision %d not available", p->precision);
+  if (p->window < 0) return fail(ctx, BIOT_E_INVALID, "window must be >= 0");
+  const size_t ne = 2 * (size_t)ctx->n * ctx->n;
+  std::vector<double> kap(ne, p->kappa_const);
+  if (p->kappa_elem) kap.assign(p->kappa_elem, p->kappa_elem + ne);
+  for (double k : kap)
+    if (!(k > 0.0) || !std::isfinite(k)) return fail(ctx, BIOT_E_INVALID, "permeability must be positive");
+  const int wcap = std::max(1, std::min(p->n_t, p->window > 0 ? p->window : p->n_t));
+  if (ctx->X && (p->n_t != ctx->n_t || wcap != ctx->wcap || p->n_iter != ctx->n_iter)) {
+    release_time_buffers(ctx);
+    ctx->assembled = false;
+  }
+  ctx->prm = *p;
+  ctx->prm.kappa_elem = nullptr;
+  ctx->precond = 0;
+  if (!ctx->X) {
+    ctx->n_t = p->n_t;
+    ctx->ldx = p->n_t + 1;
+    ctx->wcap = wcap;
+    ctx->n_iter = p->n_iter;
+    BIOT_TRY(alloc_time_buffers(ctx));
+  }
+  BIOT_CU(ctx, cudaMemcpyAsync(ctx->kappa, kap.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, ctx->stream));
+  BIOT_TRY(assemble_system(ctx));
+  BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->assembled = true;
+  return BIOT_OK;
+}
+
+biot_status biot_precond_setup(biot_ctx* ctx, int32_t kind) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_TRY(need_assembled(ctx));
+  if (kind != BIOT_PRECOND_TRI && kind != BIOT_PRECOND_DIAG) return fail(ctx, BIOT_E_INVALID, "precond kind %d", kind);
+  ctx->precond = 0;
+  BIOT_TRY(band_setup(ctx, kind));
+  BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  return BIOT_OK;
+}
+
+biot_status biot_sweep(biot_ctx* ctx, int32_t lo, int32_t hi, double* rel_out) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_TRY(need_precond(ctx));
+  BIOT_TRY(check_window(ctx, lo, hi));
+  BIOT_TRY(sweep_impl(ctx, lo, hi, rel_out));
+  if (!rel_out) BIOT_CU(ctx, cudaGetLastError());
+  return BIOT_OK;
+}
+
+biot_status biot_residual_norms(biot_ctx* ctx, int32_t lo, int32_t hi, double* rel_out) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_TRY(need_assembled(ctx));
+  BIOT_TRY(check_window(ctx, lo, hi));
+  if (!rel_out) return fail(ctx, BIOT_E_INVALID, "rel_out is NULL");
+  return residual_window(ctx, lo, hi - lo + 1, rel_out);
+}
+
+biot_status biot_pint_solve(biot_ctx* ctx, double tol, int32_t max_outer, int32_t* sweeps_done,
+                            double* final_rel_res) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_TRY(need_precond(ctx));
+  if (max_outer < 1) return fail(ctx, BIOT_E_INVALID, "max_outer must be >= 1");
+  if (ctx->prm.schedule == BIOT_SCHED_TOL && !(tol >= 0.0)) return fail(ctx, BIOT_E_INVALID, "tol must be >= 0");
+  const int n_t = ctx->n_t;
+  int w = 0;
+  biot_status result = BIOT_OK;
+  std::vector<double> rel(ctx->wcap);
+  if (ctx->prm.schedule == BIOT_SCHED_PAPER) {
+    const int M = ctx->prm.window > 0 ? ctx->prm.window : n_t;
+    if (M > ctx->wcap) return fail(ctx, BIOT_E_INVALID, "paper schedule needs window <= %d", ctx->wcap);
+    const int total = n_t + M - 1;
+    for (w = 1; w <= total; ++w) {
+      if (w > max_outer) {
+        --w;
+        result = fail(ctx, BIOT_E_NOT_CONVERGED, "paper schedule stopped after %d of %d sweeps", max_outer, total);
+        break;
+      }
+      const int a = std::max(1, w - M + 1), z = std::min(w, n_t);
+      BIOT_TRY(sweep_impl(ctx, a, z, nullptr));
+    }
+    if (result == BIOT_OK) w = total;
+  } else {
+    int lo = 1;
+    double first = -1.0;
+    while (lo <= n_t) {
+      if (w >= max_outer) {
+        result = fail(ctx, BIOT_E_NOT_CONVERGED, "tolerance %.3g not met after %d sweeps (step %d open)", tol,
+                      max_outer, lo);
+        break;
+      }
+      ++w;
+      const int hi = std::min(std::min(w, n_t), lo + ctx->wcap - 1);
+      const int nc = hi - lo + 1;
+      BIOT_TRY(residual_window(ctx, lo, nc, rel.data()));
+      for (int c = 0; c < nc; ++c)
+        if (!std::isfinite(rel[c]))
+          return fail(ctx, BIOT_E_DIVERGED, "non-finite residual at step %d, sweep %d", lo + c, w);
+      if (first < 0.0) first = rel[0];
+      if (first > 0.0 && rel[0] > 1e6 * std::max(first, 1.0))
+        return fail(ctx, BIOT_E_DIVERGED, "residual of step %d grew to %.3g", lo, rel[0]);
+      int k = 0;
+      while (k < nc && rel[k] <= tol) ++k;
+      BIOT_TRY(fgmres_cycle(ctx, lo, k, nc - k));
+      lo += k;
+    }
+  }
+  if (sweeps_done) *sweeps_done = w;
+  if (final_rel_res) BIOT_TRY(spacetime_residual(ctx, final_rel_res));
+  BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  return result;
+}
+
+biot_status biot_get_solution(const biot_ctx* cctx, int32_t step, double* host_out) {
+  biot_ctx* ctx = const_cast<biot_ctx*>(cctx);
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_TRY(need_assembled(ctx));
+  if (!host_out || step < 0 || step > ctx->n_t) return fail(ctx, BIOT_E_INVALID, "step %d outside 0..%d", step, ctx->n_t);
+  return copy_out_steps(ctx, ctx->X, ctx->ldx, step, 1, nullptr, host_out);
+}
+
+biot_status biot_get_state(const biot_ctx* cctx, int32_t lo, int32_t hi, double* host) {
+  biot_ctx* ctx = const_cast<biot_ctx*>(cctx);
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_TRY(need_assembled(ctx));
+  if (!host || lo < 0 || hi > ctx->n_t || lo > hi) return fail(ctx, BIOT_E_INVALID, "bad state range");
+  return copy_out_steps(ctx, ctx->X, ctx->ldx, lo, hi - lo + 1, nullptr, host);
+}
+
+biot_status biot_set_state(biot_ctx* ctx, int32_t lo, int32_t hi, const double* host) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_TRY(need_assembled(ctx));
+  if (!host || lo < 0 || hi > ctx->n_t || lo > hi) return fail(ctx, BIOT_E_INVALID, "bad state range");
+  return copy_in_steps(ctx, host, hi - lo + 1, nullptr, ctx->X, ctx->ldx, lo);
+}
+
+biot_status biot_get_csr(const biot_ctx* cctx, int32_t* rowptr, int32_t* col, double* val, double* ap_pp,
+                         int64_t* nnz_out) {
+  biot_ctx* ctx = const_cast<biot_ctx*>(cctx);
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  if (nnz_out) *nnz_out = ctx->nnz;
+  cudaStream_t s = ctx->stream;
+  if (rowptr)
+    BIOT_CU(ctx, cudaMemcpyAsync(rowptr, ctx->rowptr, sizeof(int32_t) * (ctx->n_dof + 1), cudaMemcpyDeviceToHost, s));
+  if (col) BIOT_CU(ctx, cudaMemcpyAsync(col, ctx->col, sizeof(int32_t) * ctx->nnz, cudaMemcpyDeviceToHost, s));
+  if (val || ap_pp) BIOT_TRY(need_assembled(ctx));
+  if (val) BIOT_CU(ctx, cudaMemcpyAsync(val, ctx->val, sizeof(double) * ctx->nnz, cudaMemcpyDeviceToHost, s));
+  if (ap_pp) BIOT_CU(ctx, cudaMemcpyAsync(ap_pp, ctx->apval, sizeof(double) * ctx->n_pairs, cudaMemcpyDeviceToHost, s));
+  BIOT_CU(ctx, cudaStreamSynchronize(s));
+  return BIOT_OK;
+}
+
+biot_status biot_get_rhs(const biot_ctx* cctx, double* host) {
+  biot_ctx* ctx = const_cast<biot_ctx*>(cctx);
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_TRY(need_assembled(ctx));
+  if (!host) return fail(ctx, BIOT_E_INVALID, "host is NULL");
+  return copy_out_steps(ctx, ctx->F, ctx->ldx, 0, ctx->n_t + 1, nullptr, host);
+}
+
+biot_status biot_get_residual(biot_ctx* ctx, int32_t lo, int32_t hi, double* host) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_TRY(need_assembled(ctx));
+  BIOT_TRY(check_window(ctx, lo, hi));
+  if (!host) return fail(ctx, BIOT_E_INVALID, "host is NULL");
+  BIOT_TRY(residual_window(ctx, lo, hi - lo + 1, nullptr));
+  // V_0 holds d .* r; undo the equilibration while transposing.
+  return copy_out_steps(ctx, ctx->V, ctx->wcap, 0, hi - lo + 1, ctx->dsc, host);
+}
+
+biot_status biot_precond_apply(biot_ctx* ctx, int32_t ncols, const double* host_in, double* host_out) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_TRY(need_precond(ctx));
+  if (ncols < 1 || ncols > ctx->wcap || !host_in || !host_out)
+    return fail(ctx, BIOT_E_INVALID, "ncols must be in 1..%d and buffers non-NULL", ctx->wcap);
+  // precond_apply computes P^{-1}(V ./ d); load V = d .* in.
+  BIOT_TRY(copy_in_steps(ctx, host_in, ncols, ctx->dsc, ctx->V, ctx->wcap, 0));
+  precond_apply(ctx, ctx->V, ctx->Z, 0, ncols);
+  BIOT_CU(ctx, cudaGetLastError());
+  return copy_out_steps(ctx, ctx->Z, ctx->wcap, 0, ncols, nullptr, host_out);
+}
+
+biot_status biot_get_info(const biot_ctx* ctx, biot_info* out) {
+  if (bad_ctx(ctx) || !out) return fail(nullptr, BIOT_E_INVALID, "NULL argument");
+  out->n = ctx->n;
+  out->n_nodes = ctx->n_nodes;
+  out->n_dof = ctx->n_dof;
+  out->nnz = ctx->nnz;
+  out->n_pairs = ctx->n_pairs;
+  out->n_t = ctx->n_t;
+  out->window_cap = ctx->wcap;
+  out->band_u = ctx->band_u;
+  out->band_p = ctx->band_p;
+  out->precond = ctx->precond;
+  out->precision = ctx->prm.precision;
+  out->beta = ctx->beta;
+  out->device_bytes = ctx->device_bytes;
+  return BIOT_OK;
+}
+
+int64_t biot_launch_count(void) { return g_launches.load(); }
+
+const char* biot_last_error(const biot_ctx* ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->err.empty() ? "no error" : ctx->err.c_str();
+}
+
+void biot_destroy(biot_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  dfree_all(ctx);
+  delete ctx;
+}
+
+}  // extern "C"

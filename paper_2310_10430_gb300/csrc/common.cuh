@@ -1,0 +1,147 @@
+// Internal declarations shared by the CUDA translation units of the Biot PinT
+// library. Nothing here is part of the public ABI (include/biot_pint.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/biot_pint.h"
+
+namespace biot {
+
+// Kernel launches issued by the library (reported by biot_launch_count).
+extern std::atomic<int64_t> g_launches;
+
+// Launch helper: counts the launch and records launch-configuration errors.
+#define BIOT_LAUNCH(kernel, grid, block, smem, stream, ...)              \
+  do {                                                                   \
+    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);          \
+    ::biot::g_launches.fetch_add(1, std::memory_order_relaxed);          \
+  } while (0)
+
+// Fixed reduction grid: partial sums per block are reduced in a second pass in
+// block order, so every norm and dot product is deterministic.
+constexpr int kRedBlocks = 304;         // 2 x 152 SMs
+constexpr int kMaxIter = 32;            // n_iter upper bound
+constexpr double kBreakdownRtol = 1e-14;  // lucky-breakdown test h_{j+1,j} <= rtol |A z_j|
+
+struct DeviceBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Per-precision copy of the matrix values used by the sweep kernels.
+struct Values32 {
+  float* val = nullptr;     // AA values, CSR order
+  float* apval = nullptr;   // A' pressure-pressure values, node-pair order
+  __nv_bfloat16* val_bf16 = nullptr;
+  __nv_bfloat16* apval_bf16 = nullptr;
+};
+
+}  // namespace biot
+
+struct biot_ctx {
+  // mesh
+  int n = 0;
+  double Lx = 1.0, Ly = 1.0;
+  cudaStream_t stream = nullptr;
+  int n_nodes = 0, n_dof = 0, n_pairs = 0;
+  int64_t nnz = 0;
+  // pattern (device)
+  int32_t* nodeptr = nullptr;   // [n_nodes + 1]
+  int32_t* nbr = nullptr;       // [n_pairs] sorted neighbour lists (self included)
+  int32_t* rowptr = nullptr;    // [n_dof + 1]
+  int32_t* col = nullptr;       // [nnz]
+  // values (device, FP64)
+  double* val = nullptr;        // AA after Dirichlet elimination, CSR order
+  double* apval = nullptr;      // A'_pp after elimination, node-pair order
+  double* dsc = nullptr;        // d = |diag AA|^{-1/2}
+  uint8_t* dmask = nullptr;     // 1 on Dirichlet DOFs
+  double* kappa = nullptr;      // [2 n^2]
+  // time data
+  int n_t = 0;
+  int ldx = 0;                  // leading dimension of X and F (>= n_t + 1)
+  double* X = nullptr;          // [n_dof][ldx], column n = step n
+  double* F = nullptr;          // [n_dof][ldx], column 0 zero
+  // Krylov work buffers, [n_dof][wcap] each
+  int wcap = 0;
+  int n_iter = 0;
+  double* V = nullptr;          // (n_iter + 1) vectors
+  double* Z = nullptr;          // n_iter vectors
+  double* Wv = nullptr;         // Arnoldi candidate w
+  double* part = nullptr;       // [kRedBlocks][(kMaxIter + 2)][wcap] partial sums
+  double* colscal = nullptr;    // per-column scalars: see krylov.cu (layout kColScalars x wcap)
+  double* H = nullptr;          // [wcap][(kMaxIter + 1) * kMaxIter]
+  double* hvec = nullptr;       // [kMaxIter + 1][wcap] reduced dots of the current step
+  int32_t* kcol = nullptr;      // [wcap] Arnoldi steps taken per column
+  // band preconditioner
+  int band_u = 0, band_p = 0;
+  int precond = 0;
+  double* Lu = nullptr;         // A = L L^T, lower band rows [2 n_nodes][band_u + 1]
+  double* Uu = nullptr;         // L^T band rows [2 n_nodes][band_u + 1]
+  double* Lp = nullptr;         // S = L L^T, [n_nodes][band_p + 1]
+  double* Up = nullptr;
+  double* tu = nullptr;         // [2 n_nodes][wcap] forward-solve scratch (u)
+  double* tp = nullptr;         // [n_nodes][wcap] coupling / forward scratch (p)
+  int32_t* status = nullptr;    // device status word (factorisation pivots)
+  // params
+  biot_params prm{};
+  double beta = 0.0;
+  bool assembled = false;
+  // bookkeeping
+  int64_t device_bytes = 0;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace biot {
+
+// Error plumbing: every failing call stores a message in ctx->err.
+biot_status fail(biot_ctx* ctx, biot_status st, const char* fmt, ...);
+biot_status cuda_check(biot_ctx* ctx, cudaError_t e, const char* what);
+biot_status dalloc(biot_ctx* ctx, void** p, size_t bytes);
+void dfree_all(biot_ctx* ctx);
+
+#define BIOT_CU(ctx, call)                                                   \
+  do {                                                                       \
+    biot_status _st = ::biot::cuda_check((ctx), (call), #call);              \
+    if (_st != BIOT_OK) return _st;                                          \
+  } while (0)
+#define BIOT_TRY(call)                                                       \
+  do {                                                                       \
+    biot_status _st = (call);                                                \
+    if (_st != BIOT_OK) return _st;                                          \
+  } while (0)
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ---- assembly.cu ----
+biot_status build_pattern(biot_ctx* ctx);
+biot_status assemble_system(biot_ctx* ctx);
+
+// ---- spmm.cu ----
+// R-window residual: V0[:, c] = d .* (F[:, lo+c] + A' X[:, lo+c-1] - AA X[:, lo+c]) for c < ncols,
+// partials of |d r|^2 and |d b|^2 per column into part (slots 0 and 1).
+void launch_residual(biot_ctx* ctx, int lo, int ncols, double* out, int ldo);
+// w = d .* (AA z) for columns [c0, c0 + ncols) of z (ld wcap); partial |w|^2 into slot 0.
+void launch_spmm_scaled(biot_ctx* ctx, const double* z, double* w, int c0, int ncols);
+// t_p[v][c] = sum_m B^T[v][m] z_u[m][c] - v_p[v][c]/d (P1 coupling).
+void launch_coupling(biot_ctx* ctx, const double* z, const double* vin, double* tp, int c0, int ncols);
+
+// ---- band.cu ----
+biot_status band_setup(biot_ctx* ctx, int kind);
+// z = P^{-1} (vin ./ d) for columns [c0, c0 + ncols); vin, z in [n_dof][wcap].
+void precond_apply(biot_ctx* ctx, const double* vin, double* z, int c0, int ncols);
+
+// ---- krylov.cu ----
+enum ColScalar { CS_RR = 0, CS_BB, CS_BETA0, CS_WN0, CS_WW, CS_INVH, CS_ACTIVE, kColScalars };
+void reduce_partials(biot_ctx* ctx, int nslots, int ncols, double* out, int ldo, int c0);
+biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols);
+
+}  // namespace biot

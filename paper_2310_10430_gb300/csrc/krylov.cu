@@ -1,0 +1,223 @@
+// The inner solver K(P, AA, X, b, n_iter) of Algorithm 3, batched over the
+// active time steps of a sweep.
+//
+// One cycle of right-preconditioned flexible GMRES per step (the paper uses
+// PETSc GMRES, Sec. 4; the preconditioner apply is exact here, the flexible
+// form keeps Z = P^{-1} V explicitly for the update). The Arnoldi basis lives in
+// the equilibrated variables r~ = D^{-1/2} r, D = |diag AA|, so the minimised
+// norm weighs the displacement and pressure equations alike:
+//   v_0 = r~ / |r~|;  z_j = P^{-1} (D^{1/2} v_j);  w = D^{-1/2} AA z_j;
+//   classical Gram-Schmidt applied twice; Givens rotations on H;
+//   x <- x + Z_k y_k with R y = g.
+// Every reduction (dot products, norms) is a fixed two-level tree: per-block
+// partial sums, then a pass over the blocks in order. Results do not depend on
+// scheduling.
+#include "common.cuh"
+
+namespace biot {
+
+namespace {
+
+constexpr int kRecH = (kMaxIter + 1) * kMaxIter;              // H, row-major (kMaxIter+1) x kMaxIter
+constexpr int kRecG = kRecH;                                  // g[kMaxIter+1]
+constexpr int kRecCS = kRecG + kMaxIter + 1;                  // cs[kMaxIter]
+constexpr int kRecSN = kRecCS + kMaxIter;                     // sn[kMaxIter]
+constexpr int kRecY = kRecSN + kMaxIter;                      // y[kMaxIter]
+constexpr int kRec = kRecY + kMaxIter;
+
+// out[s][c] = sum over blocks of part[s][block][c], s < nslots, c in [c0, c0 + ncols).
+__global__ void k_reduce(const double* __restrict__ part, int nblocks, int nslots, int ld, int c0, int ncols,
+                         double* __restrict__ out, int ldo) {
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (c >= c0 + ncols || s >= nslots) return;
+  double acc = 0.0;
+  const double* p = part + (size_t)s * nblocks * ld + c;
+  for (int b = 0; b < nblocks; ++b) acc += p[(size_t)b * ld];
+  out[(size_t)s * ldo + c] = acc;
+}
+
+// Partial dot products part[i][block][c] = sum_{rows of block} V_i[r][c] * w[r][c].
+__global__ void __launch_bounds__(256)
+k_dots(const double* __restrict__ V, size_t vstride, const double* __restrict__ w, int nrows, int ld, int c0,
+       int ncols, double* __restrict__ part) {
+  __shared__ double sm[8][32];
+  const int i = blockIdx.y;
+  const double* Vi = V + (size_t)i * vstride;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = (nrows + gridDim.x - 1) / gridDim.x;
+  const int rb = blockIdx.x * per, re = min(nrows, rb + per);
+  for (int cb = 0; cb < ncols; cb += 32) {
+    const int c = c0 + cb + lane;
+    const bool cv = cb + lane < ncols;
+    double acc = 0.0;
+    if (cv)
+      for (int r = rb + warp; r < re; r += 8) acc += Vi[(size_t)r * ld + c] * w[(size_t)r * ld + c];
+    sm[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && cv) {
+      double s = 0.0;
+      for (int k = 0; k < 8; ++k) s += sm[k][lane];
+      part[((size_t)i * gridDim.x + blockIdx.x) * ld + c] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// w[r][c] -= sum_i h[i][c] V_i[r][c].
+__global__ void k_gs_axpy(const double* __restrict__ V, size_t vstride, int nvec, const double* __restrict__ h,
+                          double* __restrict__ w, int nrows, int ld, int c0, int ncols) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)nrows * ncols) return;
+  const int r = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
+  double acc = w[(size_t)r * ld + c];
+  for (int i = 0; i < nvec; ++i) acc -= h[(size_t)i * ld + c] * V[(size_t)i * vstride + (size_t)r * ld + c];
+  w[(size_t)r * ld + c] = acc;
+}
+
+// dst[r][c] = src[r][c] * scale[c].
+__global__ void k_scale_cols(const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ scale,
+                             int nrows, int ld, int c0, int ncols) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)nrows * ncols) return;
+  const int r = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
+  dst[(size_t)r * ld + c] = src[(size_t)r * ld + c] * scale[c];
+}
+
+__global__ void k_fgmres_init(double* __restrict__ cs, int ld, int c0, int ncols, double* __restrict__ rec,
+                              int32_t* __restrict__ kcol) {
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c0 + ncols) return;
+  const double beta0 = sqrt(cs[CS_RR * ld + c]);
+  double* R = rec + (size_t)c * kRec;
+  for (int k = 0; k < kRec; ++k) R[k] = 0.0;
+  R[kRecG] = beta0;
+  cs[CS_BETA0 * ld + c] = beta0;
+  const bool act = beta0 > 0.0;
+  cs[CS_ACTIVE * ld + c] = act ? 1.0 : 0.0;
+  cs[CS_INVH * ld + c] = act ? 1.0 / beta0 : 0.0;
+  kcol[c] = 0;
+}
+
+// Arnoldi step j of column c: store H[:, j], rotate, extend g, test breakdown.
+__global__ void k_givens(int j, double* __restrict__ cs, const double* __restrict__ h1, const double* __restrict__ h2,
+                         int ld, int c0, int ncols, double* __restrict__ rec, int32_t* __restrict__ kcol) {
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c0 + ncols) return;
+  if (cs[CS_ACTIVE * ld + c] == 0.0) {
+    cs[CS_INVH * ld + c] = 0.0;
+    return;
+  }
+  double* R = rec + (size_t)c * kRec;
+  double* H = R;
+  double* g = R + kRecG;
+  double* cc = R + kRecCS;
+  double* sn = R + kRecSN;
+  for (int i = 0; i <= j; ++i) H[i * kMaxIter + j] = h1[(size_t)i * ld + c] + h2[(size_t)i * ld + c];
+  const double hn = sqrt(cs[CS_WW * ld + c]);
+  const double wn0 = sqrt(cs[CS_WN0 * ld + c]);
+  H[(j + 1) * kMaxIter + j] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i * kMaxIter + j], b = H[(i + 1) * kMaxIter + j];
+    H[i * kMaxIter + j] = cc[i] * a + sn[i] * b;
+    H[(i + 1) * kMaxIter + j] = -sn[i] * a + cc[i] * b;
+  }
+  const double a = H[j * kMaxIter + j], b = H[(j + 1) * kMaxIter + j];
+  const double den = hypot(a, b);
+  if (den == 0.0) {
+    cc[j] = 1.0;
+    sn[j] = 0.0;
+  } else {
+    cc[j] = a / den;
+    sn[j] = b / den;
+  }
+  H[j * kMaxIter + j] = den;
+  H[(j + 1) * kMaxIter + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cc[j] * g[j];
+  kcol[c] = j + 1;
+  if (hn <= kBreakdownRtol * wn0) {
+    cs[CS_ACTIVE * ld + c] = 0.0;
+    cs[CS_INVH * ld + c] = 0.0;
+  } else {
+    cs[CS_INVH * ld + c] = 1.0 / hn;
+  }
+}
+
+// Back substitution R y = g for the k steps each column took.
+__global__ void k_backsolve(int ld, int c0, int ncols, double* __restrict__ rec, const int32_t* __restrict__ kcol) {
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c0 + ncols) return;
+  double* R = rec + (size_t)c * kRec;
+  const double* H = R;
+  const double* g = R + kRecG;
+  double* y = R + kRecY;
+  const int k = kcol[c];
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int m = i + 1; m < k; ++m) s -= H[i * kMaxIter + m] * y[m];
+    y[i] = s / H[i * kMaxIter + i];
+  }
+}
+
+// X[r][lo + c] += sum_{i < k_c} y_i[c] Z_i[r][c].
+__global__ void k_update_x(const double* __restrict__ Z, size_t zstride, const double* __restrict__ rec,
+                           const int32_t* __restrict__ kcol, double* __restrict__ X, int ldx, int lo, int nrows,
+                           int ld, int c0, int ncols) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)nrows * ncols) return;
+  const int r = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
+  const int k = kcol[c];
+  if (k == 0) return;
+  const double* y = rec + (size_t)c * kRec + kRecY;
+  double acc = 0.0;
+  for (int i = 0; i < k; ++i) acc += y[i] * Z[(size_t)i * zstride + (size_t)r * ld + c];
+  X[(size_t)r * ldx + lo + c] += acc;
+}
+
+}  // namespace
+
+int krylov_record_doubles() { return kRec; }
+
+void reduce_partials(biot_ctx* ctx, int nslots, int ncols, double* out, int ldo, int c0) {
+  dim3 grid(div_up(ncols, 128), nslots);
+  BIOT_LAUNCH(k_reduce, grid, 128, 0, ctx->stream, ctx->part, kRedBlocks, nslots, ctx->wcap, c0, ncols, out, ldo);
+}
+
+biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
+  if (ncols <= 0) return BIOT_OK;
+  cudaStream_t s = ctx->stream;
+  const int ld = ctx->wcap, nd = ctx->n_dof;
+  const size_t vs = (size_t)nd * ld;
+  double* cs = ctx->colscal;
+  double* h1 = ctx->hvec;
+  double* h2 = ctx->hvec + (size_t)(kMaxIter + 1) * ld;
+  const int cblk = div_up(ncols, 128);
+  const int eblk = div_up((long long)nd * ncols, 256);
+  BIOT_LAUNCH(k_fgmres_init, cblk, 128, 0, s, cs, ld, c0, ncols, ctx->H, ctx->kcol);
+  BIOT_LAUNCH(k_scale_cols, eblk, 256, 0, s, ctx->V, ctx->V, cs + CS_INVH * ld, nd, ld, c0, ncols);
+  for (int j = 0; j < ctx->n_iter; ++j) {
+    double* Vj = ctx->V + j * vs;
+    double* Zj = ctx->Z + j * vs;
+    precond_apply(ctx, Vj, Zj, c0, ncols);
+    launch_spmm_scaled(ctx, Zj, ctx->Wv, c0, ncols);
+    reduce_partials(ctx, 1, ncols, cs + CS_WN0 * ld, ld, c0);
+    for (int pass = 0; pass < 2; ++pass) {
+      double* h = pass == 0 ? h1 : h2;
+      BIOT_LAUNCH(k_dots, dim3(kRedBlocks, j + 1), 256, 0, s, ctx->V, vs, ctx->Wv, nd, ld, c0, ncols, ctx->part);
+      reduce_partials(ctx, j + 1, ncols, h, ld, c0);
+      BIOT_LAUNCH(k_gs_axpy, eblk, 256, 0, s, ctx->V, vs, j + 1, h, ctx->Wv, nd, ld, c0, ncols);
+    }
+    BIOT_LAUNCH(k_dots, dim3(kRedBlocks, 1), 256, 0, s, ctx->Wv, vs, ctx->Wv, nd, ld, c0, ncols, ctx->part);
+    reduce_partials(ctx, 1, ncols, cs + CS_WW * ld, ld, c0);
+    BIOT_LAUNCH(k_givens, cblk, 128, 0, s, j, cs, h1, h2, ld, c0, ncols, ctx->H, ctx->kcol);
+    if (j + 1 < ctx->n_iter)
+      BIOT_LAUNCH(k_scale_cols, eblk, 256, 0, s, ctx->Wv, ctx->V + (j + 1) * vs, cs + CS_INVH * ld, nd, ld, c0, ncols);
+  }
+  BIOT_LAUNCH(k_backsolve, cblk, 128, 0, s, ld, c0, ncols, ctx->H, ctx->kcol);
+  BIOT_LAUNCH(k_update_x, eblk, 256, 0, s, ctx->Z, vs, ctx->H, ctx->kcol, ctx->X, ctx->ldx, lo, nd, ld, c0, ncols);
+  BIOT_CU(ctx, cudaGetLastError());
+  return BIOT_OK;
+}
+
+}  // namespace biot
