@@ -1,0 +1,383 @@
+"""Benchmark of the parallel-in-time Biot sweep on GB300.
+
+Workload: the 256x256 Terzaghi column (66,049 nodes, 198,147 DOF), N_t = 256,
+tau = 1e-3, E = 1e4, nu = 0.3, alpha = 1, kappa = 1e-6, stabilised P1-P1,
+block-diagonal preconditioner P2, FGMRES(10) per step, FP64 (synthetic inputs
+shaped like the paper's test cases; see workloads/).
+
+One step = one outer iteration of the inverted time stepping (Alg. 3) over all
+N_t = 256 time steps at once: the fused window residual, one preconditioned
+FGMRES(10) cycle per time step (10 exact P2 applications by band triangular
+solves, 10 AA z products, CGS2) and the convergence norms. This is the work of
+one wave of the paper's N_thread = 256 threads.
+
+metric: DOF x timesteps x outer-iterations per second = n_dof * 256 / t_step,
+summed over replicas (one independent replica per GPU; the method has no
+exchange between independent solves).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DOF*timesteps*outer-iters/s"
+UNIT = "DOF*timesteps*outer-iters/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
+
+
+_SIZE = {}
+
+
+def workload():
+    import workloads as W
+    case = W.terzaghi_256("diag")
+    if _SIZE:
+        case = case.with_(n=_SIZE.get("n", case.n), n_t=_SIZE.get("n_t", case.n_t),
+                          name=f"terzaghi_{_SIZE.get('n', case.n)}x{_SIZE.get('n', case.n)}_nt{_SIZE.get('n_t', case.n_t)}")
+    return case
+
+
+def config_dict(case, window):
+    return {
+        "workload": f"{case.name} (Terzaghi column, stabilised P1-P1, P2 block-diagonal preconditioner)",
+        "n": case.n, "n_dof": case.n_dof, "n_t": case.n_t, "tau": case.tau, "E": case.E, "nu": case.nu,
+        "kappa": case.kappa, "precond": "P2", "n_iter": case.n_iter, "window": window,
+        "step": "one outer iteration (sweep) over all N_t time steps",
+        "l2": "no flush: working set ~12 GB >> 126 MB L2 (inputs larger than L2)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (the cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(case, budget_s, max_cols):
+    """Time oracle FGMRES(n_iter) cycles (exact LU block solves) on the first time
+    steps of a full-window sweep from the zero initial guess. Setup is untimed."""
+    import numpy as np
+    from oracle.solvers import BlockPreconditioner, fgmres_cycle, step_residual
+    from oracle.system import build_system
+    s = build_system(case)
+    P = BlockPreconditioner(s, case.precond)
+    d = s.dscale()
+    X = np.zeros((case.n_t + 1, s.n_dof))
+    X[0] = s.x0
+    times = []
+    t_start = time.perf_counter()
+    for n in range(1, min(case.n_t, max_cols) + 1):
+        t0 = time.perf_counter()
+        r, b = step_residual(s, X, n)
+        fgmres_cycle(s.AA, P, d, X[n], b, case.n_iter, r=r)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s:
+            break
+    return s.n_dof, times
+
+
+def cpu_baseline_subprocess(budget_s=15.0):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(budget_s)],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_cpu_sample(budget_s):
+    case = workload()
+    n_dof, times = oracle_sample(case, budget_s, case.n_t)
+    tot = sum(times)
+    print(json.dumps({
+        "value": n_dof * len(times) / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": f"{len(times)} of the {case.n_t} time steps of one full-window sweep at {case.n}x{case.n} "
+                  f"(oracle FGMRES({case.n_iter}) cycles with exact sparse-LU block solves, single thread, "
+                  f"{tot:.1f} s timed; assembly and factorisation untimed)",
+    }))
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (one independent replica per GPU)
+# ---------------------------------------------------------------------------
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline helpers
+# ---------------------------------------------------------------------------
+
+def band_solve_flops(info, ncols, precond):
+    """Algorithmic FP64 flops of the band triangular solves of one P apply
+    (forward + backward on A and on S): 2 flops per band entry per column."""
+    def tri(N, b):
+        return 2.0 * ncols * (N * b - b * (b + 1) / 2.0)
+    fa = tri(2 * info.n_nodes, info.band_u)
+    fs = tri(info.n_nodes, info.band_p)
+    return 2 * fa + 2 * fs, 4
+
+
+def profile_traffic(kernel_src):
+    """dram bytes per launch from a committed ncu summary whose source hash matches."""
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith(".md"):
+            continue
+        txt = open(os.path.join(pdir, fn)).read()
+        m1 = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", txt)
+        m2 = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+        if m1 and m2 and m1.group(1) == sha:
+            return float(m2.group(1))
+    return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2310_10430_gb300 import biot
+    from paper_2310_10430_gb300 import build as B
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if rank == 0:
+        B.build()
+    barrier(world)
+    if rank != 0:
+        B.build()
+    case = workload()
+    stream = torch.cuda.current_stream()
+    W_ = case.n_t
+    ctx = biot.Context(case, stream=stream, window=W_)
+    info = ctx.info
+    lo, hi = 1, case.n_t
+
+    for _ in range(args.warmup):
+        biot.biot_sweep(ctx.ctx, lo, hi, want_rel=False)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region -------------------------------------------------
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    biot.biot_timing_enable(ctx.ctx, True)
+    l0 = biot.biot_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        biot.biot_sweep(ctx.ctx, lo, hi, want_rel=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = biot.biot_launch_count() - l0 - 0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    band_ms, band_n = biot.biot_timing_read(ctx.ctx, biot.BIOT_KC_BAND_SOLVE)
+    res_ms, res_n = biot.biot_timing_read(ctx.ctx, biot.BIOT_KC_RESIDUAL)
+    spmm_ms, spmm_n = biot.biot_timing_read(ctx.ctx, biot.BIOT_KC_SPMM)
+    biot.biot_timing_enable(ctx.ctx, False)
+    barrier(world)
+    ms_max = allreduce_max(ms, world)
+    ms_per_step = ms_max / args.steps
+    units_per_step = case.n_dof * (hi - lo + 1)
+    value = world * units_per_step / (ms_per_step / 1e3)
+
+    # ---- end to end through the C ABI with pinned host buffers --------------
+    nd = case.n_dof
+    host_in = torch.empty((hi + 1, nd), dtype=torch.float64, pin_memory=True).numpy()
+    host_out = torch.empty((hi - lo + 1, nd), dtype=torch.float64, pin_memory=True).numpy()
+    biot.biot_get_state(ctx.ctx, 0, hi, host_in)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        biot.biot_set_state(ctx.ctx, 0, hi, host_in)
+        rel = biot.biot_sweep(ctx.ctx, lo, hi, want_rel=True)
+        biot.biot_get_state(ctx.ctx, lo, hi, host_out)
+    torch.cuda.synchronize()
+    e2e_s = allreduce_max(time.perf_counter() - t0, world) / args.steps
+    e2e_value = world * units_per_step / e2e_s
+    h2d = host_in.nbytes
+    d2h = host_out.nbytes + rel.nbytes
+
+    # ---- roofline of the dominant kernel (band triangular solves, FP64 ALU) --
+    flops_per_apply, launches_per_apply = band_solve_flops(info, hi - lo + 1, case.precond)
+    flops_per_launch = flops_per_apply / launches_per_apply
+    achieved = flops_per_launch / (band_ms / band_n / 1e3) / 1e12
+    traffic = profile_traffic(os.path.join(ROOT, "paper_2310_10430_gb300", "csrc", "band.cu"))
+    roofline = {"kernel": "k_band_solve (FP64 band triangular solves of the P2 block solves)",
+                "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (FP64 not in MEASURED_PEAKS.json)",
+                "traffic": traffic, "launches": band_n, "avg_launch_ms": band_ms / band_n,
+                "share_of_step": band_ms / ms}
+
+    out = None
+    if rank == 0:
+        cpu = cpu_baseline_subprocess(args.cpu_budget) if (world == 1 and not args.no_cpu) else None
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(case, W_),
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "kernels_ms_per_step": {"band_solve": band_ms / args.steps, "residual": res_ms / args.steps,
+                                    "spmm": spmm_ms / args.steps},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return None
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    case = workload()
+    n_dof, times = oracle_sample(case, budget_s=1e9, max_cols=args.warmup + args.steps)
+    timed = times[args.warmup:]
+    ms_per_step = 1e3 * sum(timed) / max(len(timed), 1)
+    value = n_dof / (ms_per_step / 1e3)
+    sample = (f"each step = one oracle FGMRES({case.n_iter}) cycle with exact sparse-LU block solves on one of "
+              f"the {case.n_t} time steps of a full-window sweep at {case.n}x{case.n}")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_dict(case, case.n_t),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-sample", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
+    ap.add_argument("--n", type=int, default=None, help="override the mesh size (profiling runs only)")
+    ap.add_argument("--nt", type=int, default=None, help="override N_t (profiling runs only)")
+    args = ap.parse_args()
+    if args.n:
+        _SIZE["n"] = args.n
+    if args.nt:
+        _SIZE["n_t"] = args.nt
+    if args.cpu_sample is not None:
+        run_cpu_sample(args.cpu_sample)
+        return
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

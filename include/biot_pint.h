@@ -190,6 +190,24 @@ biot_status biot_precond_apply(biot_ctx* ctx, int32_t ncols, const double* host_
 
 biot_status biot_get_info(const biot_ctx* ctx, biot_info* out);
 
+/* ---- measurement -------------------------------------------------------- */
+
+/* Kernel classes timed by biot_timing_read. */
+typedef enum {
+  BIOT_KC_RESIDUAL = 0,      /* fused window residual f^n + A' x_{n-1} - AA x_n */
+  BIOT_KC_SPMM = 1,          /* equilibrated AA z of the Arnoldi step */
+  BIOT_KC_BAND_SOLVE = 2,    /* band triangular solves of the P1/P2 block solves */
+  BIOT_KC_COUNT = 3
+} biot_kernel_class;
+
+/* enable != 0: clear previous records and bracket every later launch of the
+ * classes above with CUDA events on the context's stream; enable == 0: stop. */
+biot_status biot_timing_enable(biot_ctx* ctx, int32_t enable);
+
+/* Sum of the event-measured durations (ms) and number of launches recorded for
+ * one kernel class since biot_timing_enable. Synchronises the stream. */
+biot_status biot_timing_read(biot_ctx* ctx, int32_t kernel_class, double* total_ms, int64_t* launches);
+
 /* Kernel launches issued by this library since it was loaded (all contexts). */
 int64_t biot_launch_count(void);
 

@@ -24,6 +24,7 @@ BIOT_FP64, BIOT_FP32, BIOT_BF16VAL_FP32ACC = 0, 1, 2
 BIOT_TERZAGHI, BIOT_MMS_TRIG = 0, 1
 BIOT_BETA_H2, BIOT_BETA_H, BIOT_BETA_NONE = 0, 1, 2
 BIOT_SCHED_TOL, BIOT_SCHED_PAPER = 0, 1
+BIOT_KC_RESIDUAL, BIOT_KC_SPMM, BIOT_KC_BAND_SOLVE = 0, 1, 2
 
 
 class BiotParams(ctypes.Structure):
@@ -78,6 +79,8 @@ _SIGNATURES = {
     "biot_get_residual": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _D]),
     "biot_precond_apply": (ctypes.c_int, [_P, ctypes.c_int32, _D, _D]),
     "biot_get_info": (ctypes.c_int, [_P, ctypes.POINTER(BiotInfo)]),
+    "biot_timing_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "biot_timing_read": (ctypes.c_int, [_P, ctypes.c_int32, _D, _I64]),
     "biot_launch_count": (ctypes.c_int64, []),
     "biot_last_error": (ctypes.c_char_p, [_P]),
     "biot_destroy": (None, [_P]),
@@ -235,6 +238,18 @@ def biot_precond_apply(ctx, vin: np.ndarray) -> np.ndarray:
     out = np.zeros_like(vin)
     _check(lib().biot_precond_apply(ctx, vin.shape[0], _dptr(vin), _dptr(out)), ctx, "biot_precond_apply")
     return out
+
+
+def biot_timing_enable(ctx, enable: bool = True):
+    _check(lib().biot_timing_enable(ctx, 1 if enable else 0), ctx, "biot_timing_enable")
+
+
+def biot_timing_read(ctx, kernel_class: int):
+    """(total_ms, launches) recorded for one kernel class."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(lib().biot_timing_read(ctx, int(kernel_class), ctypes.byref(ms), ctypes.byref(n)), ctx, "biot_timing_read")
+    return ms.value, n.value
 
 
 def biot_launch_count() -> int:

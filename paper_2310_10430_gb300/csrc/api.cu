@@ -57,6 +57,29 @@ void dfree_all(biot_ctx* ctx) {
   ctx->device_bytes = 0;
 }
 
+static size_t next_event(biot_ctx* ctx) {
+  if (ctx->ev_used == ctx->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return (size_t)-1;
+    ctx->ev_pool.push_back(e);
+  }
+  return ctx->ev_used++;
+}
+
+KTimer::KTimer(biot_ctx* c, int k) : ctx(c), kc(k) {
+  if (!ctx->timing) return;
+  a = next_event(ctx);
+  if (a != (size_t)-1) cudaEventRecord(ctx->ev_pool[a], ctx->stream);
+}
+
+KTimer::~KTimer() {
+  if (!ctx->timing || a == (size_t)-1) return;
+  size_t b = next_event(ctx);
+  if (b == (size_t)-1) return;
+  cudaEventRecord(ctx->ev_pool[b], ctx->stream);
+  ctx->ev_marks[kc].emplace_back(a, b);
+}
+
 namespace {
 
 // Tiled transposes between the device layout [dof][ld] (time fastest) and the
@@ -528,6 +551,30 @@ biot_status biot_get_info(const biot_ctx* ctx, biot_info* out) {
   return BIOT_OK;
 }
 
+biot_status biot_timing_enable(biot_ctx* ctx, int32_t enable) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->timing = enable != 0;
+  ctx->ev_used = 0;
+  for (auto& m : ctx->ev_marks) m.clear();
+  return BIOT_OK;
+}
+
+biot_status biot_timing_read(biot_ctx* ctx, int32_t kc, double* total_ms, int64_t* launches) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  if (kc < 0 || kc >= BIOT_KC_COUNT || !total_ms || !launches) return fail(ctx, BIOT_E_INVALID, "kernel class");
+  BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  double sum = 0.0;
+  for (auto& pr : ctx->ev_marks[kc]) {
+    float ms = 0.f;
+    BIOT_CU(ctx, cudaEventElapsedTime(&ms, ctx->ev_pool[pr.first], ctx->ev_pool[pr.second]));
+    sum += ms;
+  }
+  *total_ms = sum;
+  *launches = (int64_t)ctx->ev_marks[kc].size();
+  return BIOT_OK;
+}
+
 int64_t biot_launch_count(void) { return g_launches.load(); }
 
 const char* biot_last_error(const biot_ctx* ctx) {
@@ -538,6 +585,7 @@ const char* biot_last_error(const biot_ctx* ctx) {
 void biot_destroy(biot_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   dfree_all(ctx);
   delete ctx;
 }

@@ -13,19 +13,26 @@
 // the transposed band Ub[i][q] = L[i + q][i] (diagonal at q = 0) serves the
 // backward solve with contiguous rows.
 //
-// The triangular solves run one CTA per active time step (column); the last b
-// solution values live in a shared-memory ring, the band row of the next row is
-// prefetched into registers while the current row is reduced.
+// The triangular solves are blocked by kNB rows. For a block of rows, the part of
+// each row's band that reaches into earlier blocks is a dense product with the
+// solution history (every FMA useful, K-split over 4 lanes); the part inside the
+// block is applied as the precomputed inverse of the block's triangle (a small
+// dense product instead of a serial substitution). A CTA owns kCols time steps
+// (columns); the last b + kNB solution rows live in a shared-memory ring. FP64
+// throughput on GB300 is 2 FMA/clk/SM, so the design spends FP64 issue slots only
+// on the band products: no per-row reduction trees, no divisions.
 #include "common.cuh"
+
+#include <algorithm>
 
 namespace biot {
 
 namespace {
 
 constexpr int kSolveThreads = 256;
-constexpr int kMaxQ = 9;          // band rows up to kMaxQ * 256 entries (n <= 1147)
-constexpr int kRing = 4096;       // power of two >= b + 1
-constexpr int kRhsChunk = 256;
+constexpr int kNB = 64;                         // rows per block of the triangular solves
+constexpr int kKSplit = kSolveThreads / kNB;    // lanes sharing one row's band product
+constexpr int kCols = 2;                        // time steps (columns) per CTA
 
 __global__ void k_band_extract_u(int nn, int bu, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                  const double* __restrict__ val, double* __restrict__ Lb) {
@@ -56,38 +63,69 @@ __global__ void k_band_extract_p(int nn, int bp, const int32_t* __restrict__ row
   }
 }
 
-// Column j of the right-looking band Cholesky: L_jj = sqrt(a_jj), L_ij = a_ij / L_jj.
-__global__ void k_chol_scale(int N, int b, int j, double* __restrict__ Lb, int32_t* __restrict__ status) {
-  if (*status != 0) return;
-  const double d = Lb[(size_t)j * (b + 1) + b];
-  if (!(d > 0.0)) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *status = j + 1;
-    return;
+// Blocked right-looking band Cholesky, panels of kPanel columns.
+// Panel kernel (one CTA): factors columns j0 .. j0 + np - 1 including the rows
+// below them inside the band: L_jj = sqrt(a_jj), L_ij = a_ij / L_jj, and the
+// rank-1 updates of the remaining panel columns.
+constexpr int kPanel = 32;
+
+__global__ void __launch_bounds__(256)
+k_chol_panel(int N, int b, int j0, int np, double* __restrict__ Lb, int32_t* __restrict__ status) {
+  __shared__ double sd;
+  __shared__ int bad;
+  const int t = threadIdx.x;
+  if (t == 0) bad = (*status != 0);
+  __syncthreads();
+  if (bad) return;
+  const size_t W = (size_t)b + 1;
+  for (int jj = 0; jj < np; ++jj) {
+    const int j = j0 + jj;
+    if (t == 0) {
+      const double d = Lb[(size_t)j * W + b];
+      if (!(d > 0.0)) {
+        *status = j + 1;
+        bad = 1;
+      } else {
+        sd = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (bad) return;
+    const int last = min(N - 1, j + b);
+    const double inv = 1.0 / sd;
+    for (int i = j + 1 + t; i <= last; i += blockDim.x) Lb[(size_t)i * W + (b - (i - j))] *= inv;
+    if (t == 0) Lb[(size_t)j * W + b] = sd;
+    __syncthreads();
+    for (int k = j + 1; k < j0 + np; ++k) {
+      const double lkj = Lb[(size_t)k * W + (b - (k - j))];
+      for (int i = k + t; i <= last; i += blockDim.x)
+        Lb[(size_t)i * W + (b - (i - k))] -= Lb[(size_t)i * W + (b - (i - j))] * lkj;
+    }
+    __syncthreads();
   }
-  const double s = sqrt(d);
-  const double inv = 1.0 / s;
-  const int last = min(N - 1, j + b);
-  for (int i = j + 1 + blockIdx.x * blockDim.x + threadIdx.x; i <= last; i += blockDim.x * gridDim.x)
-    Lb[(size_t)i * (b + 1) + (b - (i - j))] *= inv;
-  if (blockIdx.x == 0 && threadIdx.x == 0) Lb[(size_t)j * (b + 1) + b] = s;
 }
 
-// Trailing update a_ik -= L_ij L_kj for j < k <= i <= j + b.
-__global__ void k_chol_update(int N, int b, int j, double* __restrict__ Lb, const int32_t* __restrict__ status) {
+// Trailing update after a panel: a_ik -= sum_{j in panel} L_ij L_kj for
+// j1 <= k <= i <= min(N - 1, j1 - 1 + b), j1 = j0 + np.
+__global__ void k_chol_trailing(int N, int b, int j0, int np, double* __restrict__ Lb,
+                                const int32_t* __restrict__ status) {
   if (*status != 0) return;
-  const int last = min(N - 1, j + b);
-  const int m = last - j;  // rows j+1..last
+  const int j1 = j0 + np;
+  const int last = min(N - 1, j1 - 1 + b);
+  const int m = last - j1 + 1;
+  if (m <= 0) return;
+  const size_t W = (size_t)b + 1;
   const long long tri = (long long)m * (m + 1) / 2;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tri; t += (long long)blockDim.x * gridDim.x) {
-    // t -> (ii, kk), 0 <= kk <= ii < m
     int ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
     while ((long long)ii * (ii + 1) / 2 > t) --ii;
     while ((long long)(ii + 1) * (ii + 2) / 2 <= t) ++ii;
     const int kk = (int)(t - (long long)ii * (ii + 1) / 2);
-    const int i = j + 1 + ii, k = j + 1 + kk;
-    const double lij = Lb[(size_t)i * (b + 1) + (b - (i - j))];
-    const double lkj = Lb[(size_t)k * (b + 1) + (b - (k - j))];
-    Lb[(size_t)i * (b + 1) + (b - (i - k))] -= lij * lkj;
+    const int i = j1 + ii, k = j1 + kk;
+    const int jb = max(j0, i - b);
+    double acc = 0.0;
+    for (int j = jb; j < j1; ++j) acc += Lb[(size_t)i * W + (b - (i - j))] * Lb[(size_t)k * W + (b - (k - j))];
+    Lb[(size_t)i * W + (b - (i - k))] -= acc;
   }
 }
 
@@ -108,86 +146,155 @@ enum SolveMode {
 
 __device__ __forceinline__ int udof(int i) { return 3 * (i >> 1) + (i & 1); }
 
-// One band triangular solve per CTA (column c = c0 + blockIdx.x).
-// Forward: y_i = (rhs_i - sum_{q<b} Lb[i][q] y_{i-b+q}) / Lb[i][b], i ascending.
-// Backward: x_i = (rhs_i - sum_{q>=1} Ub[i][q] x_{i+q}) / Ub[i][0], i descending.
+// Inverse of every kNB x kNB diagonal block of L (lower triangular), row-major,
+// zero above the diagonal; rows past N are padded with the identity.
+__global__ void k_diag_inverse(int N, int b, const double* __restrict__ Lb, double* __restrict__ Dinv) {
+  __shared__ double Ld[kNB][kNB + 1];
+  const int I = blockIdx.x, i0 = I * kNB, t = threadIdx.x;
+  double* X = Dinv + (size_t)I * kNB * kNB;  // X[r * kNB + k]; column k written and read by thread k only
+  const size_t W = (size_t)b + 1;
+  for (int idx = t; idx < kNB * kNB; idx += blockDim.x) {
+    const int r = idx / kNB, c = idx % kNB;
+    double v = 0.0;
+    if (c <= r) {
+      if (i0 + r < N) {
+        if (r - c <= b) v = Lb[(size_t)(i0 + r) * W + (b - (r - c))];
+      } else {
+        v = (r == c) ? 1.0 : 0.0;
+      }
+    }
+    Ld[r][c] = v;
+  }
+  __syncthreads();
+  if (t < kNB) {
+    const int k = t;  // column k of the inverse: forward substitution on e_k
+    for (int r = 0; r < kNB; ++r) {
+      if (r < k) {
+        X[r * kNB + k] = 0.0;
+        continue;
+      }
+      double s = (r == k) ? 1.0 : 0.0;
+      for (int j = k; j < r; ++j) s -= Ld[r][j] * X[j * kNB + k];
+      X[r * kNB + k] = s / Ld[r][r];
+    }
+  }
+}
+
+// Blocked band triangular solve for kCols columns per CTA.
+// Forward (L y = rhs): blocks ascending; row i of block I gets
+//   s_i = sum_{j in [i-b, i0)} L[i][j] y_j,  y_I = Dinv_I (rhs_I - s_I).
+// Backward (L^T x = rhs, rows of L^T in Ub): blocks descending;
+//   s_i = sum_{j in (i0+kNB-1, i+b]} U[i][j] x_j,  x_I = Dinv_I^T (rhs_I - s_I).
 template <int MODE>
 __global__ void __launch_bounds__(kSolveThreads)
-k_band_solve(int N, int b, const double* __restrict__ band, const double* __restrict__ vin,
-             const double* __restrict__ dsc, double* __restrict__ ty, double* __restrict__ tp,
-             double* __restrict__ z, int ld, int c0) {
+k_band_solve(int N, int b, const double* __restrict__ band, const double* __restrict__ Dinv,
+             const double* __restrict__ vin, const double* __restrict__ dsc, double* __restrict__ ty,
+             double* __restrict__ tp, double* __restrict__ z, int ld, int c0, int ncols, int ring_mask) {
   constexpr bool kFwd = MODE <= FWD_P_FROM_V;
-  __shared__ double ring[kRing];
-  __shared__ double rhs[kRhsChunk];
-  __shared__ double red[kSolveThreads / 32];
-  __shared__ double sdiag;
-  const int c = c0 + blockIdx.x;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int W = b + 1;
-  // register prefetch of the band row for the next step
-  double lnext[kMaxQ];
-  auto row_of = [&](int step) { return kFwd ? step : (N - 1 - step); };
-  auto load_row = [&](int step, double* dst) {
-    const int i = row_of(step);
-    const double* rowp = band + (size_t)i * W;
-#pragma unroll
-    for (int u = 0; u < kMaxQ; ++u) {
-      const int q = t + u * kSolveThreads;
-      dst[u] = (q < W) ? rowp[q] : 0.0;
-    }
-  };
-  auto read_rhs = [&](int i) -> double {
-    if (MODE == FWD_U_FROM_V) { const int r = udof(i); return vin[(size_t)r * ld + c] / dsc[r]; }
+  extern __shared__ double smem[];
+  double* ring = smem;                                   // [(ring_mask + 1) * kCols]
+  double* tb = smem + (size_t)(ring_mask + 1) * kCols;   // [kNB * kCols]
+  const int cbase = c0 + blockIdx.x * kCols;
+  const int ncl = min(kCols, c0 + ncols - cbase);
+  const int t = threadIdx.x;
+  const int r = t / kKSplit, part = t % kKSplit;
+  const int nblk = (N + kNB - 1) / kNB;
+  const size_t W = (size_t)b + 1;
+
+  auto read_rhs = [&](int i, int c) -> double {
+    if (MODE == FWD_U_FROM_V) { const int rr = udof(i); return vin[(size_t)rr * ld + c] / dsc[rr]; }
     if (MODE == FWD_P_FROM_T) return tp[(size_t)i * ld + c];
-    if (MODE == FWD_P_FROM_V) { const int r = 3 * i + 2; return -vin[(size_t)r * ld + c] / dsc[r]; }
+    if (MODE == FWD_P_FROM_V) { const int rr = 3 * i + 2; return -vin[(size_t)rr * ld + c] / dsc[rr]; }
     if (MODE == BWD_U_TO_Z) return ty[(size_t)i * ld + c];
     return tp[(size_t)i * ld + c];
   };
-  auto write_out = [&](int i, double y) {
+  auto write_out = [&](int i, int c, double y) {
     if (MODE == FWD_U_FROM_V) ty[(size_t)i * ld + c] = y;
     else if (MODE == FWD_P_FROM_T || MODE == FWD_P_FROM_V) tp[(size_t)i * ld + c] = y;
     else if (MODE == BWD_U_TO_Z) z[(size_t)udof(i) * ld + c] = y;
     else z[(size_t)(3 * i + 2) * ld + c] = y;
   };
-  if (N > 0) load_row(0, lnext);
-  for (int step = 0; step < N; ++step) {
-    const int i = row_of(step);
-    if ((step % kRhsChunk) == 0) {
-      __syncthreads();
-      for (int u = t; u < kRhsChunk; u += kSolveThreads) {
-        const int s2 = step + u;
-        rhs[u] = (s2 < N) ? read_rhs(row_of(s2)) : 0.0;
-      }
-      __syncthreads();
+  auto block_of = [&](int bi) { return kFwd ? bi : (nblk - 1 - bi); };
+
+  // right-hand side of this thread's row, prefetched one block ahead
+  double rhs_next[kCols];
+  {
+    const int i = block_of(0) * kNB + r;
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) rhs_next[c] = (part == 0 && i < N && c < ncl) ? read_rhs(i, cbase + c) : 0.0;
+  }
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int I = block_of(bi);
+    const int i0 = I * kNB;
+    const int i = i0 + r;
+    double rhs[kCols];
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) rhs[c] = rhs_next[c];
+    if (bi + 1 < nblk) {
+      const int in = block_of(bi + 1) * kNB + r;
+#pragma unroll
+      for (int c = 0; c < kCols; ++c)
+        rhs_next[c] = (part == 0 && in < N && c < ncl) ? read_rhs(in, cbase + c) : 0.0;
     }
-    double lcur[kMaxQ];
+    // phase 1: band product with the rows outside this block
+    double acc[kCols];
 #pragma unroll
-    for (int u = 0; u < kMaxQ; ++u) lcur[u] = lnext[u];
-    if (step + 1 < N) load_row(step + 1, lnext);
-    double s = 0.0;
-#pragma unroll
-    for (int u = 0; u < kMaxQ; ++u) {
-      const int q = t + u * kSolveThreads;
+    for (int c = 0; c < kCols; ++c) acc[c] = 0.0;
+    if (i < N) {
+      const double* Lrow = band + (size_t)i * W;
+      int qs, qe;  // q in [qs, qe)
       if (kFwd) {
-        // entries q < b couple row i to row i - b + q (must exist: i - b + q >= 0)
-        if (q < b && i - b + q >= 0) s += lcur[u] * ring[(i - b + q) & (kRing - 1)];
+        qs = max(0, b - i);
+        qe = b - r;
       } else {
-        if (q >= 1 && q <= b && i + q < N) s += lcur[u] * ring[(i + q) & (kRing - 1)];
+        qs = kNB - r;
+        qe = min(b, N - 1 - i) + 1;
+      }
+#pragma unroll 4
+      for (int q = qs + part; q < qe; q += kKSplit) {
+        const double l = Lrow[q];
+        const int j = kFwd ? (i - b + q) : (i + q);
+        const double* yr = ring + (size_t)(j & ring_mask) * kCols;
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) acc[c] = fma(l, yr[c], acc[c]);
       }
     }
 #pragma unroll
-    for (int u = 0; u < kMaxQ; ++u)
-      if (t + u * kSolveThreads == (kFwd ? b : 0)) sdiag = lcur[u];
+    for (int c = 0; c < kCols; ++c)
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) red[warp] = s;
+      for (int off = 1; off < kKSplit; off <<= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+    if (part == 0)
+#pragma unroll
+      for (int c = 0; c < kCols; ++c) tb[r * kCols + c] = (i < N) ? rhs[c] - acc[c] : 0.0;
     __syncthreads();
-    if (t == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < kSolveThreads / 32; ++w) tot += red[w];
-      const double y = (rhs[step % kRhsChunk] - tot) / sdiag;
-      ring[i & (kRing - 1)] = y;
-      write_out(i, y);
+    // phase 2: apply the inverse of the diagonal block (4 lanes per row)
+    const double* D = Dinv + (size_t)I * kNB * kNB;
+    double y[kCols];
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) y[c] = 0.0;
+    if (kFwd) {
+      for (int k = part; k <= r; k += kKSplit) {
+        const double dv = D[r * kNB + k];
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) y[c] = fma(dv, tb[k * kCols + c], y[c]);
+      }
+    } else {
+      for (int k = r + part; k < kNB; k += kKSplit) {
+        const double dv = D[k * kNB + r];
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) y[c] = fma(dv, tb[k * kCols + c], y[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kCols; ++c)
+#pragma unroll
+      for (int off = 1; off < kKSplit; off <<= 1) y[c] += __shfl_xor_sync(0xffffffffu, y[c], off);
+    if (part == 0 && i < N) {
+#pragma unroll
+      for (int c = 0; c < kCols; ++c) {
+        ring[(size_t)(i & ring_mask) * kCols + c] = y[c];
+        if (c < ncl) write_out(i, cbase + c, y[c]);
+      }
     }
     __syncthreads();
   }
@@ -197,10 +304,11 @@ k_band_solve(int N, int b, const double* __restrict__ band, const double* __rest
 biot_status band_cholesky(biot_ctx* ctx, int N, int b, double* Lb) {
   BIOT_CU(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), ctx->stream));
   const long long tri = (long long)b * (b + 1) / 2;
-  const int ublocks = (int)((tri + 255) / 256 < 1024 ? (tri + 255) / 256 : 1024);
-  for (int j = 0; j < N; ++j) {
-    BIOT_LAUNCH(k_chol_scale, 1, 256, 0, ctx->stream, N, b, j, Lb, ctx->status);
-    if (j + 1 < N) BIOT_LAUNCH(k_chol_update, ublocks, 256, 0, ctx->stream, N, b, j, Lb, ctx->status);
+  const int ublocks = (int)std::min<long long>((tri + 255) / 256, 2048);
+  for (int j0 = 0; j0 < N; j0 += kPanel) {
+    const int np = std::min(kPanel, N - j0);
+    BIOT_LAUNCH(k_chol_panel, 1, 256, 0, ctx->stream, N, b, j0, np, Lb, ctx->status);
+    if (j0 + np < N) BIOT_LAUNCH(k_chol_trailing, ublocks, 256, 0, ctx->stream, N, b, j0, np, Lb, ctx->status);
   }
   BIOT_CU(ctx, cudaGetLastError());
   int32_t st = 0;
@@ -215,14 +323,16 @@ biot_status band_cholesky(biot_ctx* ctx, int N, int b, double* Lb) {
 biot_status band_setup(biot_ctx* ctx, int kind) {
   const int nn = ctx->n_nodes;
   const int bu = ctx->band_u, bp = ctx->band_p;
-  if (bu + 1 > kMaxQ * kSolveThreads || bu + 1 > kRing)
-    return fail(ctx, BIOT_E_INVALID, "mesh too large for the band solver (half-band %d)", bu);
+  if (bu + kNB > 8192) return fail(ctx, BIOT_E_INVALID, "mesh too large for the band solver (half-band %d)", bu);
   const size_t su = (size_t)2 * nn * (bu + 1), sp = (size_t)nn * (bp + 1);
   if (!ctx->Lu) {
     BIOT_TRY(dalloc(ctx, (void**)&ctx->Lu, sizeof(double) * su));
     BIOT_TRY(dalloc(ctx, (void**)&ctx->Uu, sizeof(double) * su));
     BIOT_TRY(dalloc(ctx, (void**)&ctx->Lp, sizeof(double) * sp));
     BIOT_TRY(dalloc(ctx, (void**)&ctx->Up, sizeof(double) * sp));
+    const size_t nbu = (size_t)div_up(2 * nn, kNB), nbp = (size_t)div_up(nn, kNB);
+    BIOT_TRY(dalloc(ctx, (void**)&ctx->Du, sizeof(double) * nbu * kNB * kNB));
+    BIOT_TRY(dalloc(ctx, (void**)&ctx->Dp, sizeof(double) * nbp * kNB * kNB));
   }
   cudaStream_t s = ctx->stream;
   BIOT_CU(ctx, cudaMemsetAsync(ctx->Lu, 0, sizeof(double) * su, s));
@@ -233,28 +343,45 @@ biot_status band_setup(biot_ctx* ctx, int kind) {
   BIOT_TRY(band_cholesky(ctx, nn, bp, ctx->Lp));
   BIOT_LAUNCH(k_band_transpose, div_up((long long)su, 256), 256, 0, s, 2 * nn, bu, ctx->Lu, ctx->Uu);
   BIOT_LAUNCH(k_band_transpose, div_up((long long)sp, 256), 256, 0, s, nn, bp, ctx->Lp, ctx->Up);
+  BIOT_LAUNCH(k_diag_inverse, div_up(2 * nn, kNB), 256, 0, s, 2 * nn, bu, ctx->Lu, ctx->Du);
+  BIOT_LAUNCH(k_diag_inverse, div_up(nn, kNB), 256, 0, s, nn, bp, ctx->Lp, ctx->Dp);
   BIOT_CU(ctx, cudaGetLastError());
   ctx->precond = kind;
   return BIOT_OK;
 }
 
+static int ring_rows(int b) {
+  int r = 1;
+  while (r < b + kNB + 1) r <<= 1;
+  return r;
+}
+
+template <int MODE>
+static void solve(biot_ctx* ctx, int N, int b, const double* band, const double* Dinv, const double* vin, double* z,
+                  int c0, int ncols) {
+  KTimer tm(ctx, BIOT_KC_BAND_SOLVE);
+  const int rr = ring_rows(b);
+  const size_t smem = sizeof(double) * ((size_t)rr * kCols + kNB * kCols);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_band_solve<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  BIOT_LAUNCH(k_band_solve<MODE>, div_up(ncols, kCols), kSolveThreads, smem, ctx->stream, N, b, band, Dinv, vin,
+              ctx->dsc, ctx->tu, ctx->tp, z, ctx->wcap, c0, ncols, rr - 1);
+}
+
 void precond_apply(biot_ctx* ctx, const double* vin, double* z, int c0, int ncols) {
-  const int nn = ctx->n_nodes, ld = ctx->wcap;
-  cudaStream_t s = ctx->stream;
-  BIOT_LAUNCH(k_band_solve<FWD_U_FROM_V>, ncols, kSolveThreads, 0, s, 2 * nn, ctx->band_u, ctx->Lu, vin, ctx->dsc,
-              ctx->tu, ctx->tp, z, ld, c0);
-  BIOT_LAUNCH(k_band_solve<BWD_U_TO_Z>, ncols, kSolveThreads, 0, s, 2 * nn, ctx->band_u, ctx->Uu, vin, ctx->dsc,
-              ctx->tu, ctx->tp, z, ld, c0);
+  const int nn = ctx->n_nodes;
+  solve<FWD_U_FROM_V>(ctx, 2 * nn, ctx->band_u, ctx->Lu, ctx->Du, vin, z, c0, ncols);
+  solve<BWD_U_TO_Z>(ctx, 2 * nn, ctx->band_u, ctx->Uu, ctx->Du, vin, z, c0, ncols);
   if (ctx->precond == BIOT_PRECOND_TRI) {
     launch_coupling(ctx, z, vin, ctx->tp, c0, ncols);
-    BIOT_LAUNCH(k_band_solve<FWD_P_FROM_T>, ncols, kSolveThreads, 0, s, nn, ctx->band_p, ctx->Lp, vin, ctx->dsc,
-                ctx->tu, ctx->tp, z, ld, c0);
+    solve<FWD_P_FROM_T>(ctx, nn, ctx->band_p, ctx->Lp, ctx->Dp, vin, z, c0, ncols);
   } else {
-    BIOT_LAUNCH(k_band_solve<FWD_P_FROM_V>, ncols, kSolveThreads, 0, s, nn, ctx->band_p, ctx->Lp, vin, ctx->dsc,
-                ctx->tu, ctx->tp, z, ld, c0);
+    solve<FWD_P_FROM_V>(ctx, nn, ctx->band_p, ctx->Lp, ctx->Dp, vin, z, c0, ncols);
   }
-  BIOT_LAUNCH(k_band_solve<BWD_P_TO_Z>, ncols, kSolveThreads, 0, s, nn, ctx->band_p, ctx->Up, vin, ctx->dsc, ctx->tu,
-              ctx->tp, z, ld, c0);
+  solve<BWD_P_TO_Z>(ctx, nn, ctx->band_p, ctx->Up, ctx->Dp, vin, z, c0, ncols);
 }
 
 }  // namespace biot

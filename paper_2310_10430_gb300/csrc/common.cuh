@@ -87,6 +87,8 @@ struct biot_ctx {
   double* Uu = nullptr;         // L^T band rows [2 n_nodes][band_u + 1]
   double* Lp = nullptr;         // S = L L^T, [n_nodes][band_p + 1]
   double* Up = nullptr;
+  double* Du = nullptr;         // inverses of the 64 x 64 diagonal blocks of L (A)
+  double* Dp = nullptr;         // same for S
   double* tu = nullptr;         // [2 n_nodes][wcap] forward-solve scratch (u)
   double* tp = nullptr;         // [n_nodes][wcap] coupling / forward scratch (p)
   int32_t* status = nullptr;    // device status word (factorisation pivots)
@@ -94,6 +96,11 @@ struct biot_ctx {
   biot_params prm{};
   double beta = 0.0;
   bool assembled = false;
+  // per-class event timing (biot_timing_enable / biot_timing_read)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<size_t, size_t>> ev_marks[BIOT_KC_COUNT];
   // bookkeeping
   int64_t device_bytes = 0;
   std::vector<void*> allocs;
@@ -101,6 +108,15 @@ struct biot_ctx {
 };
 
 namespace biot {
+
+// Brackets the launches issued in its scope with CUDA events when timing is on.
+struct KTimer {
+  biot_ctx* ctx;
+  int kc;
+  size_t a = 0;
+  KTimer(biot_ctx* c, int k);
+  ~KTimer();
+};
 
 // Error plumbing: every failing call stores a message in ctx->err.
 biot_status fail(biot_ctx* ctx, biot_status st, const char* fmt, ...);

@@ -146,11 +146,13 @@ __global__ void k_coupling(int nn, const int32_t* __restrict__ nodeptr, const in
 }  // namespace
 
 void launch_residual(biot_ctx* ctx, int lo, int ncols, double* out, int ldo) {
+  KTimer tm(ctx, BIOT_KC_RESIDUAL);
   BIOT_LAUNCH(k_residual, kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr, ctx->nbr, ctx->rowptr,
               ctx->val, ctx->apval, ctx->dsc, ctx->X, ctx->F, ctx->ldx, lo, ncols, out, ldo, ctx->part, ctx->wcap);
 }
 
 void launch_spmm_scaled(biot_ctx* ctx, const double* z, double* w, int c0, int ncols) {
+  KTimer tm(ctx, BIOT_KC_SPMM);
   BIOT_LAUNCH(k_spmm_scaled, kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr, ctx->nbr,
               ctx->rowptr, ctx->val, ctx->dsc, z, w, ctx->wcap, c0, ncols, ctx->part);
 }
