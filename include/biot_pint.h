@@ -208,6 +208,48 @@ biot_status biot_timing_enable(biot_ctx* ctx, int32_t enable);
  * one kernel class since biot_timing_enable. Synchronises the stream. */
 biot_status biot_timing_read(biot_ctx* ctx, int32_t kernel_class, double* total_ms, int64_t* launches);
 
+/* ---- allocation-free variant (the paper has no counterpart) ------------- */
+
+/* Largest window (columns) biot_residual_norms_noalloc accepts. */
+#define BIOT_NOALLOC_MAX_COLS 512
+
+/* Window residual norms for callers that cannot allocate device memory.
+ *
+ * Applications that give all of a GPU's memory to their own pool or arena
+ * (a framework's caching allocator, a service with a fixed memory budget) do
+ * not let libraries call cudaMalloc or cudaFree: those calls synchronise the
+ * device, bypass the pool's accounting and fragment it. This entry point
+ * computes exactly what biot_residual_norms computes, without allocating:
+ *
+ *   R[3v+f][c] = d[3v+f] * (f^n + A' x_{n-1} - AA x_n)[3v+f],  n = lo + c,
+ *   rel[c]     = |R[:, c]| / |d .* (f^n + A' x_{n-1})|,          c < ncols,
+ *
+ * with d = |diag AA|^{-1/2}. All pointers are device memory owned by the
+ * caller: the node adjacency (nodeptr[n_nodes+1], nbr[P]: node v's sorted
+ * neighbours incl. itself), the CSR of AA (rowptr, values in CSR order, as
+ * biot_get_csr returns them), the pressure-pressure entries of A' in
+ * node-pair order (ap_pp[P]), dscale[N_dof] = d, the state X and right-hand
+ * sides F ([N_dof][ldx], time fastest), and the outputs R ([N_dof][ldr]) and
+ * rel[ncols]. Work is ordered on cuda_stream; nothing is synchronised.
+ *
+ * Scratch: per-block partial sums live in one fixed file-scope device array
+ * of 2 x 304 x BIOT_NOALLOC_MAX_COLS doubles (2.5 MB), which every GPU that
+ * loads the library holds until the process exits. Every call overwrites the
+ * partials it reads, so nothing needs clearing, but all calls share the array:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. The first call on a device looks up the
+ * array's device address (once per device) and should therefore be made
+ * before any stream capture.
+ *
+ * Errors: BIOT_E_INVALID for a NULL buffer, n_nodes < 1, ncols outside
+ * 1..BIOT_NOALLOC_MAX_COLS, lo < 1, ldx < lo + ncols or ldr < ncols;
+ * BIOT_E_CUDA for a CUDA error. Messages: biot_last_error(NULL). */
+biot_status biot_residual_norms_noalloc(int32_t n_nodes, const int32_t* nodeptr, const int32_t* nbr,
+                                        const int32_t* rowptr, const double* val, const double* ap_pp,
+                                        const double* dscale, const double* X, const double* F, int32_t ldx,
+                                        int32_t lo, int32_t ncols, double* R, int32_t ldr, double* rel,
+                                        void* cuda_stream);
+
 /* Kernel launches issued by this library since it was loaded (all contexts). */
 int64_t biot_launch_count(void);
 

@@ -81,6 +81,8 @@ _SIGNATURES = {
     "biot_get_info": (ctypes.c_int, [_P, ctypes.POINTER(BiotInfo)]),
     "biot_timing_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "biot_timing_read": (ctypes.c_int, [_P, ctypes.c_int32, _D, _I64]),
+    "biot_residual_norms_noalloc": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32,
+                                                   ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P, _P]),
     "biot_launch_count": (ctypes.c_int64, []),
     "biot_last_error": (ctypes.c_char_p, [_P]),
     "biot_destroy": (None, [_P]),
@@ -250,6 +252,15 @@ def biot_timing_read(ctx, kernel_class: int):
     n = ctypes.c_int64(0)
     _check(lib().biot_timing_read(ctx, int(kernel_class), ctypes.byref(ms), ctypes.byref(n)), ctx, "biot_timing_read")
     return ms.value, n.value
+
+
+def biot_residual_norms_noalloc(n_nodes, nodeptr, nbr, rowptr, val, ap_pp, dscale, X, F, ldx, lo, ncols, R, ldr,
+                                rel, stream=None):
+    """Allocation-free window residual norms; every array argument is a device
+    pointer (int) owned by the caller, e.g. torch_tensor.data_ptr()."""
+    st = lib().biot_residual_norms_noalloc(int(n_nodes), nodeptr, nbr, rowptr, val, ap_pp, dscale, X, F, int(ldx),
+                                           int(lo), int(ncols), R, int(ldr), rel, _stream_handle(stream))
+    _check(st, None, "biot_residual_norms_noalloc")
 
 
 def biot_launch_count() -> int:

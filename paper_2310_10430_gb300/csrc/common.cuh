@@ -145,6 +145,11 @@ biot_status assemble_system(biot_ctx* ctx);
 // R-window residual: V0[:, c] = d .* (F[:, lo+c] + A' X[:, lo+c-1] - AA X[:, lo+c]) for c < ncols,
 // partials of |d r|^2 and |d b|^2 per column into part (slots 0 and 1).
 void launch_residual(biot_ctx* ctx, int lo, int ncols, double* out, int ldo);
+// The same kernel on caller-given buffers; partials to part[2][kRedBlocks][ldp].
+void launch_residual_raw(int n_nodes, const int32_t* nodeptr, const int32_t* nbr, const int32_t* rowptr,
+                         const double* val, const double* apval, const double* dsc, const double* X,
+                         const double* F, int ldx, int lo, int ncols, double* out, int ldo, double* part, int ldp,
+                         cudaStream_t stream);
 // w = d .* (AA z) for columns [c0, c0 + ncols) of z (ld wcap); partial |w|^2 into slot 0.
 void launch_spmm_scaled(biot_ctx* ctx, const double* z, double* w, int c0, int ncols);
 // t_p[v][c] = sum_m B^T[v][m] z_u[m][c] - v_p[v][c]/d (P1 coupling).

@@ -145,6 +145,14 @@ __global__ void k_coupling(int nn, const int32_t* __restrict__ nodeptr, const in
 
 }  // namespace
 
+void launch_residual_raw(int n_nodes, const int32_t* nodeptr, const int32_t* nbr, const int32_t* rowptr,
+                         const double* val, const double* apval, const double* dsc, const double* X,
+                         const double* F, int ldx, int lo, int ncols, double* out, int ldo, double* part, int ldp,
+                         cudaStream_t stream) {
+  BIOT_LAUNCH(k_residual, kRedBlocks, kWarps * 32, 0, stream, n_nodes, nodeptr, nbr, rowptr, val, apval, dsc, X, F,
+              ldx, lo, ncols, out, ldo, part, ldp);
+}
+
 void launch_residual(biot_ctx* ctx, int lo, int ncols, double* out, int ldo) {
   KTimer tm(ctx, BIOT_KC_RESIDUAL);
   BIOT_LAUNCH(k_residual, kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr, ctx->nbr, ctx->rowptr,
