@@ -83,8 +83,10 @@ KTimer::~KTimer() {
 namespace {
 
 // Tiled transposes between the device layout [dof][ld] (time fastest) and the
-// host layout [step][n_dof].
-__global__ void k_dof_to_step(const double* __restrict__ src, int lds, int col0, int ncols, int nrows,
+// host layout [step][n_dof] (FP64 staging). Optional row scale: divide on the way
+// out, multiply on the way in.
+template <typename S>
+__global__ void k_dof_to_step(const S* __restrict__ src, int lds, int col0, int ncols, int nrows,
                               const double* __restrict__ rowscale, double* __restrict__ dst) {
   __shared__ double tile[32][33];
   const int r0 = blockIdx.x * 32, cb = blockIdx.y * 32;
@@ -92,7 +94,7 @@ __global__ void k_dof_to_step(const double* __restrict__ src, int lds, int col0,
     const int r = r0 + k, c = cb + threadIdx.x;
     double v = 0.0;
     if (r < nrows && c < ncols) {
-      v = src[(size_t)r * lds + col0 + c];
+      v = (double)src[(size_t)r * lds + col0 + c];
       if (rowscale) v /= rowscale[r];
     }
     tile[k][threadIdx.x] = v;
@@ -104,8 +106,9 @@ __global__ void k_dof_to_step(const double* __restrict__ src, int lds, int col0,
   }
 }
 
+template <typename D>
 __global__ void k_step_to_dof(const double* __restrict__ src, int ncols, int nrows, const double* __restrict__ rowscale,
-                              double* __restrict__ dst, int ldd, int col0) {
+                              D* __restrict__ dst, int ldd, int col0) {
   __shared__ double tile[32][33];
   const int r0 = blockIdx.x * 32, cb = blockIdx.y * 32;
   for (int k = threadIdx.y; k < 32; k += 8) {
@@ -118,9 +121,27 @@ __global__ void k_step_to_dof(const double* __restrict__ src, int ncols, int nro
     if (r < nrows && c < ncols) {
       double v = tile[threadIdx.x][k];
       if (rowscale) v *= rowscale[r];
-      dst[(size_t)r * ldd + col0 + c] = v;
+      dst[(size_t)r * ldd + col0 + c] = (D)v;
     }
   }
+}
+
+__global__ void k_cvt_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    dst[k] = (float)src[k];
+}
+
+__global__ void k_cvt_bf16(const double* __restrict__ src, __nv_bfloat16* __restrict__ dst, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    dst[k] = __double2bfloat16(src[k]);
+}
+
+// X[r][n] += d[r][n] for n = 1..n_t (FP64 refinement update with the FP32 correction).
+__global__ void k_add_correction(double* __restrict__ X, const float* __restrict__ D, int nrows, int ldx, int n_t) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)nrows * n_t) return;
+  const int r = (int)(idx / n_t), n = 1 + (int)(idx % n_t);
+  X[(size_t)r * ldx + n] += (double)D[(size_t)r * ldx + n];
 }
 
 // |D^{-1/2} f_ST|^2 contributions per step n (f_ST = f^n, plus A' x0 for n = 1).
@@ -206,6 +227,65 @@ biot_status residual_window(biot_ctx* ctx, int lo, int ncols, double* rel_host) 
   return BIOT_OK;
 }
 
+// Reduced-precision window residual of the correction system (into lp.V) and relative norms.
+biot_status residual_window_lp(biot_ctx* ctx, int lo, int ncols, double* rel_host) {
+  launch_residual_lp(ctx, lo, ncols);
+  reduce_partials(ctx, 2, ncols, ctx->colscal + CS_RR * ctx->wcap, ctx->wcap, 0);
+  BIOT_CU(ctx, cudaGetLastError());
+  if (rel_host) {
+    std::vector<double> rb(2 * (size_t)ctx->wcap);
+    BIOT_CU(ctx, cudaMemcpyAsync(rb.data(), ctx->colscal, sizeof(double) * 2 * ctx->wcap, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < ncols; ++c) {
+      const double rr = std::sqrt(rb[c]), bb = std::sqrt(rb[ctx->wcap + c]);
+      rel_host[c] = bb > 0.0 ? rr / bb : (rr == 0.0 ? 0.0 : INFINITY);
+    }
+  }
+  return BIOT_OK;
+}
+
+// |D^{-1/2} f_ST|^2 summed over all steps.
+biot_status fst_norm2(biot_ctx* ctx, double* out);
+
+// FP64 true residual of every step: rounded into lp.F (the correction right-hand side),
+// lp.X cleared; *rr2 = |D^{-1/2}(F - calA X)|^2.
+biot_status form_correction(biot_ctx* ctx, double* rr2) {
+  double num = 0.0;
+  std::vector<double> rb(ctx->wcap);
+  for (int lo = 1; lo <= ctx->n_t; lo += ctx->wcap) {
+    const int nc = std::min(ctx->wcap, ctx->n_t - lo + 1);
+    launch_residual_to_f32(ctx, lo, nc);
+    reduce_partials(ctx, 1, nc, ctx->colscal + CS_RR * ctx->wcap, ctx->wcap, 0);
+    BIOT_CU(ctx, cudaMemcpyAsync(rb.data(), ctx->colscal + CS_RR * ctx->wcap, sizeof(double) * nc,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < nc; ++c) num += rb[c];
+  }
+  BIOT_CU(ctx, cudaMemsetAsync(ctx->lp.X, 0, sizeof(float) * (size_t)ctx->n_dof * ctx->ldx, ctx->stream));
+  // column 0 of the correction right-hand side is unused
+  ctx->lp.correction_ready = true;
+  *rr2 = num;
+  return BIOT_OK;
+}
+
+biot_status fst_norm2(biot_ctx* ctx, double* out) {
+  double den = 0.0;
+  std::vector<double> rb(ctx->wcap);
+  for (int lo = 1; lo <= ctx->n_t; lo += ctx->wcap) {
+    const int nc = std::min(ctx->wcap, ctx->n_t - lo + 1);
+    BIOT_LAUNCH(k_fst_norms, kRedBlocks, 256, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr, ctx->nbr, ctx->rowptr,
+                ctx->val, ctx->apval, ctx->dsc, ctx->X, ctx->F, ctx->ldx, lo, nc, ctx->part, ctx->wcap);
+    reduce_partials(ctx, 1, nc, ctx->colscal + CS_BB * ctx->wcap, ctx->wcap, 0);
+    BIOT_CU(ctx, cudaMemcpyAsync(rb.data(), ctx->colscal + CS_BB * ctx->wcap, sizeof(double) * nc,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < nc; ++c) den += rb[c];
+  }
+  *out = den;
+  return BIOT_OK;
+}
+
 biot_status spacetime_residual(biot_ctx* ctx, double* out) {
   double num = 0.0, den = 0.0;
   std::vector<double> rb(ctx->wcap);
@@ -217,47 +297,109 @@ biot_status spacetime_residual(biot_ctx* ctx, double* out) {
                                  cudaMemcpyDeviceToHost, ctx->stream));
     BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
     for (int c = 0; c < nc; ++c) num += rb[c];
-    BIOT_LAUNCH(k_fst_norms, kRedBlocks, 256, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr, ctx->nbr, ctx->rowptr,
-                ctx->val, ctx->apval, ctx->dsc, ctx->X, ctx->F, ctx->ldx, lo, nc, ctx->part, ctx->wcap);
-    reduce_partials(ctx, 1, nc, ctx->colscal + CS_BB * ctx->wcap, ctx->wcap, 0);
-    BIOT_CU(ctx, cudaMemcpyAsync(rb.data(), ctx->colscal + CS_BB * ctx->wcap, sizeof(double) * nc,
-                                 cudaMemcpyDeviceToHost, ctx->stream));
-    BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int c = 0; c < nc; ++c) den += rb[c];
   }
+  BIOT_TRY(fst_norm2(ctx, &den));
   *out = den > 0.0 ? std::sqrt(num / den) : std::sqrt(num);
   return BIOT_OK;
 }
 
+bool low_precision(const biot_ctx* ctx) { return ctx->prm.precision != BIOT_FP64; }
+
 biot_status sweep_impl(biot_ctx* ctx, int lo, int hi, double* rel_out) {
   const int ncols = hi - lo + 1;
+  if (low_precision(ctx)) {
+    if (!ctx->lp.correction_ready) {
+      double rr2 = 0.0;
+      BIOT_TRY(form_correction(ctx, &rr2));
+    }
+    BIOT_TRY(residual_window_lp(ctx, lo, ncols, rel_out));
+    return fgmres_cycle<float>(ctx, lo, 0, ncols);
+  }
   BIOT_TRY(residual_window(ctx, lo, ncols, rel_out));
-  BIOT_TRY(fgmres_cycle(ctx, lo, 0, ncols));
+  return fgmres_cycle<double>(ctx, lo, 0, ncols);
+}
+
+// Tol-schedule PinT solve (Alg. 3 as snapshot sweeps, reading A5) in the working
+// precision of T on the state X (FP64) or on the correction d (FP32). A step that
+// stays active for stall_cap sweeps retires as it is (used by the FP32 correction
+// solves, whose attainable residual is bounded by FP32 rounding).
+template <typename T>
+biot_status tol_schedule(biot_ctx* ctx, double tol, int max_sweeps, int stall_cap, int* sweeps, bool* converged) {
+  const int n_t = ctx->n_t;
+  std::vector<double> rel(ctx->wcap);
+  int lo = 1, w = 0, lo_since = 0;
+  double first = -1.0;
+  *converged = false;
+  while (lo <= n_t) {
+    if (w >= max_sweeps) {
+      *sweeps = w;
+      return BIOT_OK;
+    }
+    ++w;
+    const int hi = std::min(std::min(w, n_t), lo + ctx->wcap - 1);
+    const int nc = hi - lo + 1;
+    if (sizeof(T) == 8) BIOT_TRY(residual_window(ctx, lo, nc, rel.data()));
+    else BIOT_TRY(residual_window_lp(ctx, lo, nc, rel.data()));
+    for (int c = 0; c < nc; ++c)
+      if (!std::isfinite(rel[c]))
+        return fail(ctx, BIOT_E_DIVERGED, "non-finite residual at step %d, sweep %d", lo + c, w);
+    if (first < 0.0) first = rel[0];
+    if (first > 0.0 && rel[0] > 1e6 * std::max(first, 1.0))
+      return fail(ctx, BIOT_E_DIVERGED, "residual of step %d grew to %.3g", lo, rel[0]);
+    int k = 0;
+    while (k < nc && (rel[k] <= tol || (k == 0 && stall_cap > 0 && w - lo_since >= stall_cap))) ++k;
+    BIOT_TRY(fgmres_cycle<T>(ctx, lo, k, nc - k));
+    if (k > 0) lo_since = w;
+    lo += k;
+  }
+  *sweeps = w;
+  *converged = true;
   return BIOT_OK;
 }
 
-// Work buffers sized by N_t, the window capacity and n_iter.
+// Work buffers sized by N_t, the window capacity, n_iter and the precision.
 biot_status alloc_time_buffers(biot_ctx* ctx) {
-  const size_t nd = ctx->n_dof, wc = ctx->wcap, ld = ctx->ldx;
+  const size_t nd = ctx->n_dof, wc = ctx->wcap, ld = ctx->ldx, nn = ctx->n_nodes;
+  const bool lp = low_precision(ctx);
   BIOT_TRY(dalloc(ctx, (void**)&ctx->X, sizeof(double) * nd * ld));
   BIOT_TRY(dalloc(ctx, (void**)&ctx->F, sizeof(double) * nd * ld));
-  BIOT_TRY(dalloc(ctx, (void**)&ctx->V, sizeof(double) * nd * wc * (ctx->n_iter + 1)));
-  BIOT_TRY(dalloc(ctx, (void**)&ctx->Z, sizeof(double) * nd * wc * ctx->n_iter));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->V, sizeof(double) * nd * wc * (lp ? 1 : ctx->n_iter + 1)));
   BIOT_TRY(dalloc(ctx, (void**)&ctx->Wv, sizeof(double) * nd * wc));
   BIOT_TRY(dalloc(ctx, (void**)&ctx->part, sizeof(double) * kRedBlocks * (kMaxIter + 2) * wc));
   BIOT_TRY(dalloc(ctx, (void**)&ctx->colscal, sizeof(double) * kColScalars * wc));
   BIOT_TRY(dalloc(ctx, (void**)&ctx->H, sizeof(double) * krylov_record_doubles() * wc));
   BIOT_TRY(dalloc(ctx, (void**)&ctx->hvec, sizeof(double) * 2 * (kMaxIter + 1) * wc));
   BIOT_TRY(dalloc(ctx, (void**)&ctx->kcol, sizeof(int32_t) * wc));
-  BIOT_TRY(dalloc(ctx, (void**)&ctx->tu, sizeof(double) * 2 * ctx->n_nodes * wc));
-  BIOT_TRY(dalloc(ctx, (void**)&ctx->tp, sizeof(double) * ctx->n_nodes * wc));
+  if (!lp) {
+    BIOT_TRY(dalloc(ctx, (void**)&ctx->Z, sizeof(double) * nd * wc * ctx->n_iter));
+    BIOT_TRY(dalloc(ctx, (void**)&ctx->tu, sizeof(double) * 2 * nn * wc));
+    BIOT_TRY(dalloc(ctx, (void**)&ctx->tp, sizeof(double) * nn * wc));
+    return BIOT_OK;
+  }
+  LowPrec& L = ctx->lp;
+  BIOT_TRY(dalloc(ctx, (void**)&L.X, sizeof(float) * nd * ld));
+  BIOT_TRY(dalloc(ctx, (void**)&L.F, sizeof(float) * nd * ld));
+  BIOT_TRY(dalloc(ctx, (void**)&L.V, sizeof(float) * nd * wc * (ctx->n_iter + 1)));
+  BIOT_TRY(dalloc(ctx, (void**)&L.Z, sizeof(float) * nd * wc * ctx->n_iter));
+  BIOT_TRY(dalloc(ctx, (void**)&L.Wv, sizeof(float) * nd * wc));
+  BIOT_TRY(dalloc(ctx, (void**)&L.tu, sizeof(float) * 2 * nn * wc));
+  BIOT_TRY(dalloc(ctx, (void**)&L.tp, sizeof(float) * nn * wc));
+  BIOT_TRY(dalloc(ctx, (void**)&L.val, sizeof(float) * ctx->nnz));
+  BIOT_TRY(dalloc(ctx, (void**)&L.apval, sizeof(float) * ctx->n_pairs));
+  if (ctx->prm.precision == BIOT_BF16VAL_FP32ACC) {
+    BIOT_TRY(dalloc(ctx, (void**)&L.val_bf16, sizeof(__nv_bfloat16) * ctx->nnz));
+    BIOT_TRY(dalloc(ctx, (void**)&L.apval_bf16, sizeof(__nv_bfloat16) * ctx->n_pairs));
+  }
   return BIOT_OK;
 }
 
 void release_time_buffers(biot_ctx* ctx) {
-  void** bufs[] = {(void**)&ctx->X,       (void**)&ctx->F,    (void**)&ctx->V,    (void**)&ctx->Z,
-                   (void**)&ctx->Wv,      (void**)&ctx->part, (void**)&ctx->colscal, (void**)&ctx->H,
-                   (void**)&ctx->hvec,    (void**)&ctx->kcol, (void**)&ctx->tu,   (void**)&ctx->tp};
+  void** bufs[] = {(void**)&ctx->X,     (void**)&ctx->F,       (void**)&ctx->V,      (void**)&ctx->Z,
+                   (void**)&ctx->Wv,    (void**)&ctx->part,    (void**)&ctx->colscal, (void**)&ctx->H,
+                   (void**)&ctx->hvec,  (void**)&ctx->kcol,    (void**)&ctx->tu,     (void**)&ctx->tp,
+                   (void**)&ctx->lp.X,  (void**)&ctx->lp.F,    (void**)&ctx->lp.V,   (void**)&ctx->lp.Z,
+                   (void**)&ctx->lp.Wv, (void**)&ctx->lp.tu,   (void**)&ctx->lp.tp,  (void**)&ctx->lp.val,
+                   (void**)&ctx->lp.apval, (void**)&ctx->lp.val_bf16, (void**)&ctx->lp.apval_bf16};
   for (void** b : bufs) {
     if (!*b) continue;
     auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), *b);
@@ -274,7 +416,7 @@ biot_status copy_out_steps(biot_ctx* ctx, const double* src, int lds, int col0, 
   for (int c = 0; c < nc; c += ctx->wcap) {
     const int m = std::min(ctx->wcap, nc - c);
     dim3 grid(div_up(nd, 32), div_up(m, 32)), block(32, 8);
-    BIOT_LAUNCH(k_dof_to_step, grid, block, 0, ctx->stream, src, lds, col0 + c, m, nd, rowscale, ctx->Wv);
+    BIOT_LAUNCH(k_dof_to_step<double>, grid, block, 0, ctx->stream, src, lds, col0 + c, m, nd, rowscale, ctx->Wv);
     BIOT_CU(ctx, cudaGetLastError());
     BIOT_CU(ctx, cudaMemcpyAsync(host + (size_t)c * nd, ctx->Wv, sizeof(double) * nd * m, cudaMemcpyDeviceToHost,
                                  ctx->stream));
@@ -291,7 +433,7 @@ biot_status copy_in_steps(biot_ctx* ctx, const double* host, int nc, const doubl
     BIOT_CU(ctx, cudaMemcpyAsync(ctx->Wv, host + (size_t)c * nd, sizeof(double) * nd * m, cudaMemcpyHostToDevice,
                                  ctx->stream));
     dim3 grid(div_up(nd, 32), div_up(m, 32)), block(32, 8);
-    BIOT_LAUNCH(k_step_to_dof, grid, block, 0, ctx->stream, ctx->Wv, m, nd, rowscale, dst, ldd, col0 + c);
+    BIOT_LAUNCH(k_step_to_dof<double>, grid, block, 0, ctx->stream, ctx->Wv, m, nd, rowscale, dst, ldd, col0 + c);
     BIOT_CU(ctx, cudaGetLastError());
   }
   BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
@@ -353,7 +495,8 @@ biot_status biot_assemble(biot_ctx* ctx, const biot_params* p) {
   if (p->problem != BIOT_TERZAGHI && p->problem != BIOT_MMS_TRIG) return fail(ctx, BIOT_E_INVALID, "problem");
   if (p->beta_mode < BIOT_BETA_H2 || p->beta_mode > BIOT_BETA_NONE) return fail(ctx, BIOT_E_INVALID, "beta_mode");
   if (p->schedule != BIOT_SCHED_TOL && p->schedule != BIOT_SCHED_PAPER) return fail(ctx, BIOT_E_INVALID, "schedule");
-  if (p->precision != BIOT_FP64) return fail(ctx, BIOT_E_INVALID, "precision %d not available", p->precision);
+  if (p->precision < BIOT_FP64 || p->precision > BIOT_BF16VAL_FP32ACC)
+    return fail(ctx, BIOT_E_INVALID, "precision %d", p->precision);
   if (p->window < 0) return fail(ctx, BIOT_E_INVALID, "window must be >= 0");
   const size_t ne = 2 * (size_t)ctx->n * ctx->n;
   std::vector<double> kap(ne, p->kappa_const);
@@ -361,7 +504,8 @@ biot_status biot_assemble(biot_ctx* ctx, const biot_params* p) {
   for (double k : kap)
     if (!(k > 0.0) || !std::isfinite(k)) return fail(ctx, BIOT_E_INVALID, "permeability must be positive");
   const int wcap = std::max(1, std::min(p->n_t, p->window > 0 ? p->window : p->n_t));
-  if (ctx->X && (p->n_t != ctx->n_t || wcap != ctx->wcap || p->n_iter != ctx->n_iter)) {
+  if (ctx->X && (p->n_t != ctx->n_t || wcap != ctx->wcap || p->n_iter != ctx->n_iter ||
+                 p->precision != ctx->prm.precision)) {
     release_time_buffers(ctx);
     ctx->assembled = false;
   }
@@ -377,6 +521,16 @@ biot_status biot_assemble(biot_ctx* ctx, const biot_params* p) {
   }
   BIOT_CU(ctx, cudaMemcpyAsync(ctx->kappa, kap.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, ctx->stream));
   BIOT_TRY(assemble_system(ctx));
+  if (low_precision(ctx)) {
+    BIOT_LAUNCH(k_cvt_f32, 1024, 256, 0, ctx->stream, ctx->val, ctx->lp.val, (size_t)ctx->nnz);
+    BIOT_LAUNCH(k_cvt_f32, 256, 256, 0, ctx->stream, ctx->apval, ctx->lp.apval, (size_t)ctx->n_pairs);
+    if (ctx->prm.precision == BIOT_BF16VAL_FP32ACC) {
+      BIOT_LAUNCH(k_cvt_bf16, 1024, 256, 0, ctx->stream, ctx->val, ctx->lp.val_bf16, (size_t)ctx->nnz);
+      BIOT_LAUNCH(k_cvt_bf16, 256, 256, 0, ctx->stream, ctx->apval, ctx->lp.apval_bf16, (size_t)ctx->n_pairs);
+    }
+    BIOT_CU(ctx, cudaGetLastError());
+    ctx->lp.correction_ready = false;
+  }
   BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->assembled = true;
   return BIOT_OK;
@@ -414,12 +568,44 @@ biot_status biot_pint_solve(biot_ctx* ctx, double tol, int32_t max_outer, int32_
   if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
   BIOT_TRY(need_precond(ctx));
   if (max_outer < 1) return fail(ctx, BIOT_E_INVALID, "max_outer must be >= 1");
-  if (ctx->prm.schedule == BIOT_SCHED_TOL && !(tol >= 0.0)) return fail(ctx, BIOT_E_INVALID, "tol must be >= 0");
+  if ((ctx->prm.schedule == BIOT_SCHED_TOL || low_precision(ctx)) && !(tol >= 0.0))
+    return fail(ctx, BIOT_E_INVALID, "tol must be >= 0");
   const int n_t = ctx->n_t;
   int w = 0;
   biot_status result = BIOT_OK;
-  std::vector<double> rel(ctx->wcap);
-  if (ctx->prm.schedule == BIOT_SCHED_PAPER) {
+  if (low_precision(ctx)) {
+    // FP64 iterative refinement on the space-time system: true residual in FP64,
+    // correction d from the reduced-precision PinT sweep, x <- x + d.
+    const double tol_inner = 1e-5;
+    const int stall_cap = 25;
+    double fst2 = 0.0, prev = INFINITY;
+    BIOT_TRY(fst_norm2(ctx, &fst2));
+    for (int round = 0;; ++round) {
+      double rr2 = 0.0;
+      BIOT_TRY(form_correction(ctx, &rr2));
+      const double rel = fst2 > 0.0 ? std::sqrt(rr2 / fst2) : std::sqrt(rr2);
+      if (!std::isfinite(rel)) return fail(ctx, BIOT_E_DIVERGED, "non-finite FP64 residual in refinement");
+      if (rel <= tol) break;
+      if (w >= max_outer) {
+        result = fail(ctx, BIOT_E_NOT_CONVERGED, "refinement: residual %.3g after %d sweeps", rel, w);
+        break;
+      }
+      if (round > 0 && !(rel < 0.5 * prev)) {
+        result = fail(ctx, BIOT_E_NOT_CONVERGED, "refinement stagnated at residual %.3g (round %d)", rel, round);
+        break;
+      }
+      prev = rel;
+      int sw = 0;
+      bool conv = false;
+      BIOT_TRY(tol_schedule<float>(ctx, tol_inner, max_outer - w, stall_cap, &sw, &conv));
+      w += sw;
+      const long long tot = (long long)ctx->n_dof * n_t;
+      BIOT_LAUNCH(k_add_correction, div_up(tot, 256), 256, 0, ctx->stream, ctx->X, ctx->lp.X, ctx->n_dof, ctx->ldx,
+                  n_t);
+      BIOT_CU(ctx, cudaGetLastError());
+      ctx->lp.correction_ready = false;
+    }
+  } else if (ctx->prm.schedule == BIOT_SCHED_PAPER) {
     const int M = ctx->prm.window > 0 ? ctx->prm.window : n_t;
     if (M > ctx->wcap) return fail(ctx, BIOT_E_INVALID, "paper schedule needs window <= %d", ctx->wcap);
     const int total = n_t + M - 1;
@@ -434,29 +620,9 @@ biot_status biot_pint_solve(biot_ctx* ctx, double tol, int32_t max_outer, int32_
     }
     if (result == BIOT_OK) w = total;
   } else {
-    int lo = 1;
-    double first = -1.0;
-    while (lo <= n_t) {
-      if (w >= max_outer) {
-        result = fail(ctx, BIOT_E_NOT_CONVERGED, "tolerance %.3g not met after %d sweeps (step %d open)", tol,
-                      max_outer, lo);
-        break;
-      }
-      ++w;
-      const int hi = std::min(std::min(w, n_t), lo + ctx->wcap - 1);
-      const int nc = hi - lo + 1;
-      BIOT_TRY(residual_window(ctx, lo, nc, rel.data()));
-      for (int c = 0; c < nc; ++c)
-        if (!std::isfinite(rel[c]))
-          return fail(ctx, BIOT_E_DIVERGED, "non-finite residual at step %d, sweep %d", lo + c, w);
-      if (first < 0.0) first = rel[0];
-      if (first > 0.0 && rel[0] > 1e6 * std::max(first, 1.0))
-        return fail(ctx, BIOT_E_DIVERGED, "residual of step %d grew to %.3g", lo, rel[0]);
-      int k = 0;
-      while (k < nc && rel[k] <= tol) ++k;
-      BIOT_TRY(fgmres_cycle(ctx, lo, k, nc - k));
-      lo += k;
-    }
+    bool conv = false;
+    BIOT_TRY(tol_schedule<double>(ctx, tol, max_outer, 0, &w, &conv));
+    if (!conv) result = fail(ctx, BIOT_E_NOT_CONVERGED, "tolerance %.3g not met after %d sweeps", tol, max_outer);
   }
   if (sweeps_done) *sweeps_done = w;
   if (final_rel_res) BIOT_TRY(spacetime_residual(ctx, final_rel_res));
@@ -484,6 +650,7 @@ biot_status biot_set_state(biot_ctx* ctx, int32_t lo, int32_t hi, const double* 
   if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
   BIOT_TRY(need_assembled(ctx));
   if (!host || lo < 0 || hi > ctx->n_t || lo > hi) return fail(ctx, BIOT_E_INVALID, "bad state range");
+  ctx->lp.correction_ready = false;
   return copy_in_steps(ctx, host, hi - lo + 1, nullptr, ctx->X, ctx->ldx, lo);
 }
 
@@ -527,10 +694,24 @@ biot_status biot_precond_apply(biot_ctx* ctx, int32_t ncols, const double* host_
   if (ncols < 1 || ncols > ctx->wcap || !host_in || !host_out)
     return fail(ctx, BIOT_E_INVALID, "ncols must be in 1..%d and buffers non-NULL", ctx->wcap);
   // precond_apply computes P^{-1}(V ./ d); load V = d .* in.
-  BIOT_TRY(copy_in_steps(ctx, host_in, ncols, ctx->dsc, ctx->V, ctx->wcap, 0));
-  precond_apply(ctx, ctx->V, ctx->Z, 0, ncols);
+  if (!low_precision(ctx)) {
+    BIOT_TRY(copy_in_steps(ctx, host_in, ncols, ctx->dsc, ctx->V, ctx->wcap, 0));
+    precond_apply<double>(ctx, ctx->V, ctx->Z, 0, ncols);
+    BIOT_CU(ctx, cudaGetLastError());
+    return copy_out_steps(ctx, ctx->Z, ctx->wcap, 0, ncols, nullptr, host_out);
+  }
+  // reduced precision: the FP32 preconditioner of the correction sweep
+  const int nd = ctx->n_dof;
+  dim3 grid(div_up(nd, 32), div_up(ncols, 32)), block(32, 8);
+  BIOT_CU(ctx, cudaMemcpyAsync(ctx->Wv, host_in, sizeof(double) * nd * ncols, cudaMemcpyHostToDevice, ctx->stream));
+  BIOT_LAUNCH(k_step_to_dof<float>, grid, block, 0, ctx->stream, ctx->Wv, ncols, nd, ctx->dsc, ctx->lp.V, ctx->wcap,
+              0);
+  precond_apply<float>(ctx, ctx->lp.V, ctx->lp.Z, 0, ncols);
+  BIOT_LAUNCH(k_dof_to_step<float>, grid, block, 0, ctx->stream, ctx->lp.Z, ctx->wcap, 0, ncols, nd, nullptr, ctx->Wv);
   BIOT_CU(ctx, cudaGetLastError());
-  return copy_out_steps(ctx, ctx->Z, ctx->wcap, 0, ncols, nullptr, host_out);
+  BIOT_CU(ctx, cudaMemcpyAsync(host_out, ctx->Wv, sizeof(double) * nd * ncols, cudaMemcpyDeviceToHost, ctx->stream));
+  BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  return BIOT_OK;
 }
 
 biot_status biot_get_info(const biot_ctx* ctx, biot_info* out) {

@@ -185,15 +185,15 @@ __global__ void k_diag_inverse(int N, int b, const double* __restrict__ Lb, doub
 //   s_i = sum_{j in [i-b, i0)} L[i][j] y_j,  y_I = Dinv_I (rhs_I - s_I).
 // Backward (L^T x = rhs, rows of L^T in Ub): blocks descending;
 //   s_i = sum_{j in (i0+kNB-1, i+b]} U[i][j] x_j,  x_I = Dinv_I^T (rhs_I - s_I).
-template <int MODE>
+template <int MODE, typename T>
 __global__ void __launch_bounds__(kSolveThreads)
-k_band_solve(int N, int b, const double* __restrict__ band, const double* __restrict__ Dinv,
-             const double* __restrict__ vin, const double* __restrict__ dsc, double* __restrict__ ty,
-             double* __restrict__ tp, double* __restrict__ z, int ld, int c0, int ncols, int ring_mask) {
+k_band_solve(int N, int b, const T* __restrict__ band, const T* __restrict__ Dinv,
+             const T* __restrict__ vin, const double* __restrict__ dsc, T* __restrict__ ty,
+             T* __restrict__ tp, T* __restrict__ z, int ld, int c0, int ncols, int ring_mask) {
   constexpr bool kFwd = MODE <= FWD_P_FROM_V;
-  extern __shared__ double smem[];
-  double* ring = smem;                                   // [(ring_mask + 1) * kCols]
-  double* tb = smem + (size_t)(ring_mask + 1) * kCols;   // [kNB * kCols]
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = reinterpret_cast<T*>(smem_raw);              // [(ring_mask + 1) * kCols]
+  T* tb = ring + (size_t)(ring_mask + 1) * kCols;        // [kNB * kCols]
   const int cbase = c0 + blockIdx.x * kCols;
   const int ncl = min(kCols, c0 + ncols - cbase);
   const int t = threadIdx.x;
@@ -201,14 +201,14 @@ k_band_solve(int N, int b, const double* __restrict__ band, const double* __rest
   const int nblk = (N + kNB - 1) / kNB;
   const size_t W = (size_t)b + 1;
 
-  auto read_rhs = [&](int i, int c) -> double {
-    if (MODE == FWD_U_FROM_V) { const int rr = udof(i); return vin[(size_t)rr * ld + c] / dsc[rr]; }
+  auto read_rhs = [&](int i, int c) -> T {
+    if (MODE == FWD_U_FROM_V) { const int rr = udof(i); return vin[(size_t)rr * ld + c] / (T)dsc[rr]; }
     if (MODE == FWD_P_FROM_T) return tp[(size_t)i * ld + c];
-    if (MODE == FWD_P_FROM_V) { const int rr = 3 * i + 2; return -vin[(size_t)rr * ld + c] / dsc[rr]; }
+    if (MODE == FWD_P_FROM_V) { const int rr = 3 * i + 2; return -vin[(size_t)rr * ld + c] / (T)dsc[rr]; }
     if (MODE == BWD_U_TO_Z) return ty[(size_t)i * ld + c];
     return tp[(size_t)i * ld + c];
   };
-  auto write_out = [&](int i, int c, double y) {
+  auto write_out = [&](int i, int c, T y) {
     if (MODE == FWD_U_FROM_V) ty[(size_t)i * ld + c] = y;
     else if (MODE == FWD_P_FROM_T || MODE == FWD_P_FROM_V) tp[(size_t)i * ld + c] = y;
     else if (MODE == BWD_U_TO_Z) z[(size_t)udof(i) * ld + c] = y;
@@ -217,31 +217,31 @@ k_band_solve(int N, int b, const double* __restrict__ band, const double* __rest
   auto block_of = [&](int bi) { return kFwd ? bi : (nblk - 1 - bi); };
 
   // right-hand side of this thread's row, prefetched one block ahead
-  double rhs_next[kCols];
+  T rhs_next[kCols];
   {
     const int i = block_of(0) * kNB + r;
 #pragma unroll
-    for (int c = 0; c < kCols; ++c) rhs_next[c] = (part == 0 && i < N && c < ncl) ? read_rhs(i, cbase + c) : 0.0;
+    for (int c = 0; c < kCols; ++c) rhs_next[c] = (part == 0 && i < N && c < ncl) ? read_rhs(i, cbase + c) : T(0);
   }
   for (int bi = 0; bi < nblk; ++bi) {
     const int I = block_of(bi);
     const int i0 = I * kNB;
     const int i = i0 + r;
-    double rhs[kCols];
+    T rhs[kCols];
 #pragma unroll
     for (int c = 0; c < kCols; ++c) rhs[c] = rhs_next[c];
     if (bi + 1 < nblk) {
       const int in = block_of(bi + 1) * kNB + r;
 #pragma unroll
       for (int c = 0; c < kCols; ++c)
-        rhs_next[c] = (part == 0 && in < N && c < ncl) ? read_rhs(in, cbase + c) : 0.0;
+        rhs_next[c] = (part == 0 && in < N && c < ncl) ? read_rhs(in, cbase + c) : T(0);
     }
     // phase 1: band product with the rows outside this block
-    double acc[kCols];
+    T acc[kCols];
 #pragma unroll
-    for (int c = 0; c < kCols; ++c) acc[c] = 0.0;
+    for (int c = 0; c < kCols; ++c) acc[c] = T(0);
     if (i < N) {
-      const double* Lrow = band + (size_t)i * W;
+      const T* Lrow = band + (size_t)i * W;
       int qs, qe;  // q in [qs, qe)
       if (kFwd) {
         qs = max(0, b - i);
@@ -252,9 +252,9 @@ k_band_solve(int N, int b, const double* __restrict__ band, const double* __rest
       }
 #pragma unroll 4
       for (int q = qs + part; q < qe; q += kKSplit) {
-        const double l = Lrow[q];
+        const T l = Lrow[q];
         const int j = kFwd ? (i - b + q) : (i + q);
-        const double* yr = ring + (size_t)(j & ring_mask) * kCols;
+        const T* yr = ring + (size_t)(j & ring_mask) * kCols;
 #pragma unroll
         for (int c = 0; c < kCols; ++c) acc[c] = fma(l, yr[c], acc[c]);
       }
@@ -265,22 +265,22 @@ k_band_solve(int N, int b, const double* __restrict__ band, const double* __rest
       for (int off = 1; off < kKSplit; off <<= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
     if (part == 0)
 #pragma unroll
-      for (int c = 0; c < kCols; ++c) tb[r * kCols + c] = (i < N) ? rhs[c] - acc[c] : 0.0;
+      for (int c = 0; c < kCols; ++c) tb[r * kCols + c] = (i < N) ? rhs[c] - acc[c] : T(0);
     __syncthreads();
     // phase 2: apply the inverse of the diagonal block (4 lanes per row)
-    const double* D = Dinv + (size_t)I * kNB * kNB;
-    double y[kCols];
+    const T* D = Dinv + (size_t)I * kNB * kNB;
+    T y[kCols];
 #pragma unroll
-    for (int c = 0; c < kCols; ++c) y[c] = 0.0;
+    for (int c = 0; c < kCols; ++c) y[c] = T(0);
     if (kFwd) {
       for (int k = part; k <= r; k += kKSplit) {
-        const double dv = D[r * kNB + k];
+        const T dv = D[r * kNB + k];
 #pragma unroll
         for (int c = 0; c < kCols; ++c) y[c] = fma(dv, tb[k * kCols + c], y[c]);
       }
     } else {
       for (int k = r + part; k < kNB; k += kKSplit) {
-        const double dv = D[k * kNB + r];
+        const T dv = D[k * kNB + r];
 #pragma unroll
         for (int c = 0; c < kCols; ++c) y[c] = fma(dv, tb[k * kCols + c], y[c]);
       }
@@ -298,6 +298,11 @@ k_band_solve(int N, int b, const double* __restrict__ band, const double* __rest
     }
     __syncthreads();
   }
+}
+
+__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    dst[k] = (float)src[k];
 }
 
 // Full band Cholesky of an SPD band matrix held in Lb (in place).
@@ -345,6 +350,25 @@ biot_status band_setup(biot_ctx* ctx, int kind) {
   BIOT_LAUNCH(k_band_transpose, div_up((long long)sp, 256), 256, 0, s, nn, bp, ctx->Lp, ctx->Up);
   BIOT_LAUNCH(k_diag_inverse, div_up(2 * nn, kNB), 256, 0, s, 2 * nn, bu, ctx->Lu, ctx->Du);
   BIOT_LAUNCH(k_diag_inverse, div_up(nn, kNB), 256, 0, s, nn, bp, ctx->Lp, ctx->Dp);
+  if (ctx->prm.precision != BIOT_FP64) {
+    // reduced-precision sweep: the exact FP64 factors rounded to FP32
+    const size_t du = (size_t)div_up(2 * nn, kNB) * kNB * kNB, dp = (size_t)div_up(nn, kNB) * kNB * kNB;
+    if (!ctx->lp.Lu) {
+      BIOT_TRY(dalloc(ctx, (void**)&ctx->lp.Lu, sizeof(float) * su));
+      BIOT_TRY(dalloc(ctx, (void**)&ctx->lp.Uu, sizeof(float) * su));
+      BIOT_TRY(dalloc(ctx, (void**)&ctx->lp.Du, sizeof(float) * du));
+      BIOT_TRY(dalloc(ctx, (void**)&ctx->lp.Lp, sizeof(float) * sp));
+      BIOT_TRY(dalloc(ctx, (void**)&ctx->lp.Up, sizeof(float) * sp));
+      BIOT_TRY(dalloc(ctx, (void**)&ctx->lp.Dp, sizeof(float) * dp));
+    }
+    const int g = 1024;
+    BIOT_LAUNCH(k_to_f32, g, 256, 0, s, ctx->Lu, ctx->lp.Lu, su);
+    BIOT_LAUNCH(k_to_f32, g, 256, 0, s, ctx->Uu, ctx->lp.Uu, su);
+    BIOT_LAUNCH(k_to_f32, g, 256, 0, s, ctx->Du, ctx->lp.Du, du);
+    BIOT_LAUNCH(k_to_f32, g, 256, 0, s, ctx->Lp, ctx->lp.Lp, sp);
+    BIOT_LAUNCH(k_to_f32, g, 256, 0, s, ctx->Up, ctx->lp.Up, sp);
+    BIOT_LAUNCH(k_to_f32, g, 256, 0, s, ctx->Dp, ctx->lp.Dp, dp);
+  }
   BIOT_CU(ctx, cudaGetLastError());
   ctx->precond = kind;
   return BIOT_OK;
@@ -356,32 +380,58 @@ static int ring_rows(int b) {
   return r;
 }
 
-template <int MODE>
-static void solve(biot_ctx* ctx, int N, int b, const double* band, const double* Dinv, const double* vin, double* z,
-                  int c0, int ncols) {
+template <typename T> struct BandBufs;
+template <> struct BandBufs<double> {
+  static double* tu(biot_ctx* c) { return c->tu; }
+  static double* tp(biot_ctx* c) { return c->tp; }
+  static const double* Lu(biot_ctx* c) { return c->Lu; }
+  static const double* Uu(biot_ctx* c) { return c->Uu; }
+  static const double* Du(biot_ctx* c) { return c->Du; }
+  static const double* Lp(biot_ctx* c) { return c->Lp; }
+  static const double* Up(biot_ctx* c) { return c->Up; }
+  static const double* Dp(biot_ctx* c) { return c->Dp; }
+};
+template <> struct BandBufs<float> {
+  static float* tu(biot_ctx* c) { return c->lp.tu; }
+  static float* tp(biot_ctx* c) { return c->lp.tp; }
+  static const float* Lu(biot_ctx* c) { return c->lp.Lu; }
+  static const float* Uu(biot_ctx* c) { return c->lp.Uu; }
+  static const float* Du(biot_ctx* c) { return c->lp.Du; }
+  static const float* Lp(biot_ctx* c) { return c->lp.Lp; }
+  static const float* Up(biot_ctx* c) { return c->lp.Up; }
+  static const float* Dp(biot_ctx* c) { return c->lp.Dp; }
+};
+
+template <int MODE, typename T>
+static void solve(biot_ctx* ctx, int N, int b, const T* band, const T* Dinv, const T* vin, T* z, int c0, int ncols) {
   KTimer tm(ctx, BIOT_KC_BAND_SOLVE);
   const int rr = ring_rows(b);
-  const size_t smem = sizeof(double) * ((size_t)rr * kCols + kNB * kCols);
+  const size_t smem = sizeof(T) * ((size_t)rr * kCols + kNB * kCols);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_band_solve<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_band_solve<MODE, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  BIOT_LAUNCH(k_band_solve<MODE>, div_up(ncols, kCols), kSolveThreads, smem, ctx->stream, N, b, band, Dinv, vin,
-              ctx->dsc, ctx->tu, ctx->tp, z, ctx->wcap, c0, ncols, rr - 1);
+  BIOT_LAUNCH((k_band_solve<MODE, T>), div_up(ncols, kCols), kSolveThreads, smem, ctx->stream, N, b, band, Dinv, vin,
+              ctx->dsc, BandBufs<T>::tu(ctx), BandBufs<T>::tp(ctx), z, ctx->wcap, c0, ncols, rr - 1);
 }
 
-void precond_apply(biot_ctx* ctx, const double* vin, double* z, int c0, int ncols) {
+template <typename T>
+void precond_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols) {
+  using B = BandBufs<T>;
   const int nn = ctx->n_nodes;
-  solve<FWD_U_FROM_V>(ctx, 2 * nn, ctx->band_u, ctx->Lu, ctx->Du, vin, z, c0, ncols);
-  solve<BWD_U_TO_Z>(ctx, 2 * nn, ctx->band_u, ctx->Uu, ctx->Du, vin, z, c0, ncols);
+  solve<FWD_U_FROM_V, T>(ctx, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), vin, z, c0, ncols);
+  solve<BWD_U_TO_Z, T>(ctx, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), vin, z, c0, ncols);
   if (ctx->precond == BIOT_PRECOND_TRI) {
-    launch_coupling(ctx, z, vin, ctx->tp, c0, ncols);
-    solve<FWD_P_FROM_T>(ctx, nn, ctx->band_p, ctx->Lp, ctx->Dp, vin, z, c0, ncols);
+    launch_coupling<T>(ctx, z, vin, B::tp(ctx), c0, ncols);
+    solve<FWD_P_FROM_T, T>(ctx, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), vin, z, c0, ncols);
   } else {
-    solve<FWD_P_FROM_V>(ctx, nn, ctx->band_p, ctx->Lp, ctx->Dp, vin, z, c0, ncols);
+    solve<FWD_P_FROM_V, T>(ctx, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), vin, z, c0, ncols);
   }
-  solve<BWD_P_TO_Z>(ctx, nn, ctx->band_p, ctx->Up, ctx->Dp, vin, z, c0, ncols);
+  solve<BWD_P_TO_Z, T>(ctx, nn, ctx->band_p, B::Up(ctx), B::Dp(ctx), vin, z, c0, ncols);
 }
+
+template void precond_apply<double>(biot_ctx*, const double*, double*, int, int);
+template void precond_apply<float>(biot_ctx*, const float*, float*, int, int);
 
 }  // namespace biot

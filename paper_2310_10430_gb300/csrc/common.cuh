@@ -36,12 +36,27 @@ struct DeviceBuf {
   size_t bytes = 0;
 };
 
-// Per-precision copy of the matrix values used by the sweep kernels.
-struct Values32 {
-  float* val = nullptr;     // AA values, CSR order
-  float* apval = nullptr;   // A' pressure-pressure values, node-pair order
+// Buffers of the reduced-precision sweep (FP32 vectors; BF16 or FP32 matrix values):
+// the correction system AA d_n - A' d_{n-1} = r_n of the FP64 iterative refinement.
+struct LowPrec {
+  float* X = nullptr;            // correction iterate d [n_dof][ldx], column 0 zero
+  float* F = nullptr;            // FP64 true residual rounded to FP32 [n_dof][ldx]
+  float* V = nullptr;            // (n_iter + 1) x [n_dof][wcap]
+  float* Z = nullptr;            // n_iter x [n_dof][wcap]
+  float* Wv = nullptr;           // [n_dof][wcap]
+  float* tu = nullptr;           // [2 n_nodes][wcap]
+  float* tp = nullptr;           // [n_nodes][wcap]
+  float* val = nullptr;          // AA values (CSR order)
+  float* apval = nullptr;        // A' pressure-pressure values (node-pair order)
   __nv_bfloat16* val_bf16 = nullptr;
   __nv_bfloat16* apval_bf16 = nullptr;
+  float* Lu = nullptr;           // band factors rounded from the FP64 factorisation
+  float* Uu = nullptr;
+  float* Du = nullptr;
+  float* Lp = nullptr;
+  float* Up = nullptr;
+  float* Dp = nullptr;
+  bool correction_ready = false; // lp.F holds the residual of the current X
 };
 
 }  // namespace biot
@@ -92,6 +107,7 @@ struct biot_ctx {
   double* tu = nullptr;         // [2 n_nodes][wcap] forward-solve scratch (u)
   double* tp = nullptr;         // [n_nodes][wcap] coupling / forward scratch (p)
   int32_t* status = nullptr;    // device status word (factorisation pivots)
+  biot::LowPrec lp;             // reduced-precision sweep buffers (BIOT_FP32 / BIOT_BF16VAL_FP32ACC)
   // params
   biot_params prm{};
   double beta = 0.0;
@@ -142,7 +158,7 @@ biot_status build_pattern(biot_ctx* ctx);
 biot_status assemble_system(biot_ctx* ctx);
 
 // ---- spmm.cu ----
-// R-window residual: V0[:, c] = d .* (F[:, lo+c] + A' X[:, lo+c-1] - AA X[:, lo+c]) for c < ncols,
+// FP64 window residual: out[:, c] = d .* (F[:, lo+c] + A' X[:, lo+c-1] - AA X[:, lo+c]), c < ncols;
 // partials of |d r|^2 and |d b|^2 per column into part (slots 0 and 1).
 void launch_residual(biot_ctx* ctx, int lo, int ncols, double* out, int ldo);
 // The same kernel on caller-given buffers; partials to part[2][kRedBlocks][ldp].
@@ -150,19 +166,23 @@ void launch_residual_raw(int n_nodes, const int32_t* nodeptr, const int32_t* nbr
                          const double* val, const double* apval, const double* dsc, const double* X,
                          const double* F, int ldx, int lo, int ncols, double* out, int ldo, double* part, int ldp,
                          cudaStream_t stream);
-// w = d .* (AA z) for columns [c0, c0 + ncols) of z (ld wcap); partial |w|^2 into slot 0.
-void launch_spmm_scaled(biot_ctx* ctx, const double* z, double* w, int c0, int ncols);
+// FP64 residual of steps lo.. written unscaled into lp.F (correction right-hand side).
+void launch_residual_to_f32(biot_ctx* ctx, int lo, int ncols);
+// Reduced-precision residual of the correction system into lp.V (equilibrated).
+void launch_residual_lp(biot_ctx* ctx, int lo, int ncols);
+// w = d .* (AA z) for columns [c0, c0 + ncols); partial |w|^2 into slot 0.
+template <typename T> void launch_spmm_scaled(biot_ctx* ctx, const T* z, T* w, int c0, int ncols);
 // t_p[v][c] = sum_m B^T[v][m] z_u[m][c] - v_p[v][c]/d (P1 coupling).
-void launch_coupling(biot_ctx* ctx, const double* z, const double* vin, double* tp, int c0, int ncols);
+template <typename T> void launch_coupling(biot_ctx* ctx, const T* z, const T* vin, T* tp, int c0, int ncols);
 
 // ---- band.cu ----
 biot_status band_setup(biot_ctx* ctx, int kind);
 // z = P^{-1} (vin ./ d) for columns [c0, c0 + ncols); vin, z in [n_dof][wcap].
-void precond_apply(biot_ctx* ctx, const double* vin, double* z, int c0, int ncols);
+template <typename T> void precond_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols);
 
 // ---- krylov.cu ----
 enum ColScalar { CS_RR = 0, CS_BB, CS_BETA0, CS_WN0, CS_WW, CS_INVH, CS_ACTIVE, kColScalars };
 void reduce_partials(biot_ctx* ctx, int nslots, int ncols, double* out, int ldo, int c0);
-biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols);
+template <typename T> biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols);
 
 }  // namespace biot

@@ -37,23 +37,25 @@ __global__ void k_reduce(const double* __restrict__ part, int nblocks, int nslot
   out[(size_t)s * ldo + c] = acc;
 }
 
-// Partial dot products part[i][block][c] = sum_{rows of block} V_i[r][c] * w[r][c].
+// Partial dot products part[i][block][c] = sum_{rows of block} V_i[r][c] * w[r][c]
+// (products accumulated in T within a thread, combined in FP64 across threads and blocks).
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_dots(const double* __restrict__ V, size_t vstride, const double* __restrict__ w, int nrows, int ld, int c0,
+k_dots(const T* __restrict__ V, size_t vstride, const T* __restrict__ w, int nrows, int ld, int c0,
        int ncols, double* __restrict__ part) {
   __shared__ double sm[8][32];
   const int i = blockIdx.y;
-  const double* Vi = V + (size_t)i * vstride;
+  const T* Vi = V + (size_t)i * vstride;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per = (nrows + gridDim.x - 1) / gridDim.x;
   const int rb = blockIdx.x * per, re = min(nrows, rb + per);
   for (int cb = 0; cb < ncols; cb += 32) {
     const int c = c0 + cb + lane;
     const bool cv = cb + lane < ncols;
-    double acc = 0.0;
+    T acc = 0;
     if (cv)
       for (int r = rb + warp; r < re; r += 8) acc += Vi[(size_t)r * ld + c] * w[(size_t)r * ld + c];
-    sm[warp][lane] = acc;
+    sm[warp][lane] = (double)acc;
     __syncthreads();
     if (warp == 0 && cv) {
       double s = 0.0;
@@ -65,23 +67,25 @@ k_dots(const double* __restrict__ V, size_t vstride, const double* __restrict__ 
 }
 
 // w[r][c] -= sum_i h[i][c] V_i[r][c].
-__global__ void k_gs_axpy(const double* __restrict__ V, size_t vstride, int nvec, const double* __restrict__ h,
-                          double* __restrict__ w, int nrows, int ld, int c0, int ncols) {
+template <typename T>
+__global__ void k_gs_axpy(const T* __restrict__ V, size_t vstride, int nvec, const double* __restrict__ h,
+                          T* __restrict__ w, int nrows, int ld, int c0, int ncols) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)nrows * ncols) return;
   const int r = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
-  double acc = w[(size_t)r * ld + c];
-  for (int i = 0; i < nvec; ++i) acc -= h[(size_t)i * ld + c] * V[(size_t)i * vstride + (size_t)r * ld + c];
+  T acc = w[(size_t)r * ld + c];
+  for (int i = 0; i < nvec; ++i) acc -= (T)h[(size_t)i * ld + c] * V[(size_t)i * vstride + (size_t)r * ld + c];
   w[(size_t)r * ld + c] = acc;
 }
 
 // dst[r][c] = src[r][c] * scale[c].
-__global__ void k_scale_cols(const double* __restrict__ src, double* __restrict__ dst, const double* __restrict__ scale,
+template <typename T>
+__global__ void k_scale_cols(const T* __restrict__ src, T* __restrict__ dst, const double* __restrict__ scale,
                              int nrows, int ld, int c0, int ncols) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)nrows * ncols) return;
   const int r = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
-  dst[(size_t)r * ld + c] = src[(size_t)r * ld + c] * scale[c];
+  dst[(size_t)r * ld + c] = src[(size_t)r * ld + c] * (T)scale[c];
 }
 
 __global__ void k_fgmres_init(double* __restrict__ cs, int ld, int c0, int ncols, double* __restrict__ rec,
@@ -161,8 +165,9 @@ __global__ void k_backsolve(int ld, int c0, int ncols, double* __restrict__ rec,
 }
 
 // X[r][lo + c] += sum_{i < k_c} y_i[c] Z_i[r][c].
-__global__ void k_update_x(const double* __restrict__ Z, size_t zstride, const double* __restrict__ rec,
-                           const int32_t* __restrict__ kcol, double* __restrict__ X, int ldx, int lo, int nrows,
+template <typename T>
+__global__ void k_update_x(const T* __restrict__ Z, size_t zstride, const double* __restrict__ rec,
+                           const int32_t* __restrict__ kcol, T* __restrict__ X, int ldx, int lo, int nrows,
                            int ld, int c0, int ncols) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)nrows * ncols) return;
@@ -170,8 +175,8 @@ __global__ void k_update_x(const double* __restrict__ Z, size_t zstride, const d
   const int k = kcol[c];
   if (k == 0) return;
   const double* y = rec + (size_t)c * kRec + kRecY;
-  double acc = 0.0;
-  for (int i = 0; i < k; ++i) acc += y[i] * Z[(size_t)i * zstride + (size_t)r * ld + c];
+  T acc = 0;
+  for (int i = 0; i < k; ++i) acc += (T)y[i] * Z[(size_t)i * zstride + (size_t)r * ld + c];
   X[(size_t)r * ldx + lo + c] += acc;
 }
 
@@ -184,40 +189,62 @@ void reduce_partials(biot_ctx* ctx, int nslots, int ncols, double* out, int ldo,
   BIOT_LAUNCH(k_reduce, grid, 128, 0, ctx->stream, ctx->part, kRedBlocks, nslots, ctx->wcap, c0, ncols, out, ldo);
 }
 
+template <typename T> struct KBufs;
+template <> struct KBufs<double> {
+  static double* V(biot_ctx* c) { return c->V; }
+  static double* Z(biot_ctx* c) { return c->Z; }
+  static double* W(biot_ctx* c) { return c->Wv; }
+  static double* X(biot_ctx* c) { return c->X; }
+};
+template <> struct KBufs<float> {
+  static float* V(biot_ctx* c) { return c->lp.V; }
+  static float* Z(biot_ctx* c) { return c->lp.Z; }
+  static float* W(biot_ctx* c) { return c->lp.Wv; }
+  static float* X(biot_ctx* c) { return c->lp.X; }
+};
+
+template <typename T>
 biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
   if (ncols <= 0) return BIOT_OK;
   cudaStream_t s = ctx->stream;
   const int ld = ctx->wcap, nd = ctx->n_dof;
   const size_t vs = (size_t)nd * ld;
+  T* V = KBufs<T>::V(ctx);
+  T* Z = KBufs<T>::Z(ctx);
+  T* Wv = KBufs<T>::W(ctx);
   double* cs = ctx->colscal;
   double* h1 = ctx->hvec;
   double* h2 = ctx->hvec + (size_t)(kMaxIter + 1) * ld;
   const int cblk = div_up(ncols, 128);
   const int eblk = div_up((long long)nd * ncols, 256);
   BIOT_LAUNCH(k_fgmres_init, cblk, 128, 0, s, cs, ld, c0, ncols, ctx->H, ctx->kcol);
-  BIOT_LAUNCH(k_scale_cols, eblk, 256, 0, s, ctx->V, ctx->V, cs + CS_INVH * ld, nd, ld, c0, ncols);
+  BIOT_LAUNCH(k_scale_cols<T>, eblk, 256, 0, s, V, V, cs + CS_INVH * ld, nd, ld, c0, ncols);
   for (int j = 0; j < ctx->n_iter; ++j) {
-    double* Vj = ctx->V + j * vs;
-    double* Zj = ctx->Z + j * vs;
-    precond_apply(ctx, Vj, Zj, c0, ncols);
-    launch_spmm_scaled(ctx, Zj, ctx->Wv, c0, ncols);
+    T* Vj = V + j * vs;
+    T* Zj = Z + j * vs;
+    precond_apply<T>(ctx, Vj, Zj, c0, ncols);
+    launch_spmm_scaled<T>(ctx, Zj, Wv, c0, ncols);
     reduce_partials(ctx, 1, ncols, cs + CS_WN0 * ld, ld, c0);
     for (int pass = 0; pass < 2; ++pass) {
       double* h = pass == 0 ? h1 : h2;
-      BIOT_LAUNCH(k_dots, dim3(kRedBlocks, j + 1), 256, 0, s, ctx->V, vs, ctx->Wv, nd, ld, c0, ncols, ctx->part);
+      BIOT_LAUNCH(k_dots<T>, dim3(kRedBlocks, j + 1), 256, 0, s, V, vs, Wv, nd, ld, c0, ncols, ctx->part);
       reduce_partials(ctx, j + 1, ncols, h, ld, c0);
-      BIOT_LAUNCH(k_gs_axpy, eblk, 256, 0, s, ctx->V, vs, j + 1, h, ctx->Wv, nd, ld, c0, ncols);
+      BIOT_LAUNCH(k_gs_axpy<T>, eblk, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0, ncols);
     }
-    BIOT_LAUNCH(k_dots, dim3(kRedBlocks, 1), 256, 0, s, ctx->Wv, vs, ctx->Wv, nd, ld, c0, ncols, ctx->part);
+    BIOT_LAUNCH(k_dots<T>, dim3(kRedBlocks, 1), 256, 0, s, Wv, vs, Wv, nd, ld, c0, ncols, ctx->part);
     reduce_partials(ctx, 1, ncols, cs + CS_WW * ld, ld, c0);
     BIOT_LAUNCH(k_givens, cblk, 128, 0, s, j, cs, h1, h2, ld, c0, ncols, ctx->H, ctx->kcol);
     if (j + 1 < ctx->n_iter)
-      BIOT_LAUNCH(k_scale_cols, eblk, 256, 0, s, ctx->Wv, ctx->V + (j + 1) * vs, cs + CS_INVH * ld, nd, ld, c0, ncols);
+      BIOT_LAUNCH(k_scale_cols<T>, eblk, 256, 0, s, Wv, V + (j + 1) * vs, cs + CS_INVH * ld, nd, ld, c0, ncols);
   }
   BIOT_LAUNCH(k_backsolve, cblk, 128, 0, s, ld, c0, ncols, ctx->H, ctx->kcol);
-  BIOT_LAUNCH(k_update_x, eblk, 256, 0, s, ctx->Z, vs, ctx->H, ctx->kcol, ctx->X, ctx->ldx, lo, nd, ld, c0, ncols);
+  BIOT_LAUNCH(k_update_x<T>, eblk, 256, 0, s, Z, vs, ctx->H, ctx->kcol, KBufs<T>::X(ctx), ctx->ldx, lo, nd, ld, c0,
+              ncols);
   BIOT_CU(ctx, cudaGetLastError());
   return BIOT_OK;
 }
+
+template biot_status fgmres_cycle<double>(biot_ctx*, int, int, int);
+template biot_status fgmres_cycle<float>(biot_ctx*, int, int, int);
 
 }  // namespace biot
