@@ -149,6 +149,21 @@ biot_status biot_precond_setup(biot_ctx* ctx, int32_t kind);
 biot_status biot_pint_solve(biot_ctx* ctx, double tol, int32_t max_outer,
                             int32_t* sweeps_done, double* final_rel_res);
 
+/* Solve `count` independent instances together (batched form of biot_pint_solve).
+ * Each context is created, assembled (precision BIOT_FP32 or
+ * BIOT_BF16VAL_FP32ACC, window 0 = N_t; all with the same precision and n_iter)
+ * and set up (same preconditioner kind) on its own; meshes, material, K field
+ * and N_t may differ. Every sweep kernel processes all instances in one launch
+ * (device table of per-instance buffers and windows); with use_graph != 0 the
+ * FGMRES cycle of a sweep is captured once in a CUDA graph and replayed. The
+ * FP64 refinement and its tolerance are per instance, as in biot_pint_solve.
+ * Work runs on a private stream; the contexts' streams are synchronised first.
+ * sweeps_done[count] and final_rel_res[count] (host, nullable) receive each
+ * instance's FP32 sweeps and final relative space-time residual. Returns the
+ * first failing instance's status (BIOT_E_NOT_CONVERGED, BIOT_E_DIVERGED). */
+biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, double tol, int32_t max_outer,
+                             int32_t use_graph, int32_t* sweeps_done, double* final_rel_res);
+
 /* One outer iteration (sweep) over the window of steps lo..hi (1 <= lo <= hi <= N_t,
  * hi - lo + 1 <= window_cap): residuals from the current state, one cycle of
  * K = right-preconditioned FGMRES(n_iter) per step, state updated in place.

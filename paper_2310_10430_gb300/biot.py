@@ -70,6 +70,8 @@ _SIGNATURES = {
     "biot_precond_setup": (ctypes.c_int, [_P, ctypes.c_int32]),
     "biot_pint_solve": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int32, _I32, _D]),
     "biot_sweep": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _D]),
+    "biot_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                        ctypes.c_int32, _I32, _D]),
     "biot_residual_norms": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _D]),
     "biot_get_solution": (ctypes.c_int, [_P, ctypes.c_int32, _D]),
     "biot_get_state": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _D]),
@@ -170,6 +172,19 @@ def biot_pint_solve(ctx, tol: float, max_outer: int, allow_not_converged: bool =
     if not (st == BIOT_OK or (allow_not_converged and st == BIOT_E_NOT_CONVERGED)):
         _check(st, ctx, "biot_pint_solve")
     return st, sw.value, rr.value
+
+
+def biot_batch_solve(ctxs, tol: float, max_outer: int, use_graph: bool = True, allow_not_converged: bool = False):
+    """Returns (status, sweeps_done[count], final_rel_res[count])."""
+    count = len(ctxs)
+    arr = (_P * count)(*[c.value if isinstance(c, _P) else c for c in ctxs])
+    sw = np.zeros(count, dtype=np.int32)
+    rr = np.zeros(count)
+    st = lib().biot_batch_solve(arr, count, float(tol), int(max_outer), 1 if use_graph else 0,
+                                sw.ctypes.data_as(_I32), _dptr(rr))
+    if not (st == BIOT_OK or (allow_not_converged and st == BIOT_E_NOT_CONVERGED)):
+        _check(st, None, "biot_batch_solve")
+    return st, sw, rr
 
 
 def biot_sweep(ctx, lo: int, hi: int, want_rel: bool = True):

@@ -441,6 +441,9 @@ biot_status copy_in_steps(biot_ctx* ctx, const double* host, int nc, const doubl
 }
 
 }  // namespace
+
+biot_status fst_norm2_ctx(biot_ctx* ctx, double* out) { return fst_norm2(ctx, out); }
+
 }  // namespace biot
 
 using namespace biot;

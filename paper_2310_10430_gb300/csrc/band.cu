@@ -186,8 +186,7 @@ __global__ void k_diag_inverse(int N, int b, const double* __restrict__ Lb, doub
 // Backward (L^T x = rhs, rows of L^T in Ub): blocks descending;
 //   s_i = sum_{j in (i0+kNB-1, i+b]} U[i][j] x_j,  x_I = Dinv_I^T (rhs_I - s_I).
 template <int MODE, typename T>
-__global__ void __launch_bounds__(kSolveThreads)
-k_band_solve(int N, int b, const T* __restrict__ band, const T* __restrict__ Dinv,
+__device__ __forceinline__ void band_solve_body(int N, int b, const T* __restrict__ band, const T* __restrict__ Dinv,
              const T* __restrict__ vin, const double* __restrict__ dsc, T* __restrict__ ty,
              T* __restrict__ tp, T* __restrict__ z, int ld, int c0, int ncols, int ring_mask) {
   constexpr bool kFwd = MODE <= FWD_P_FROM_V;
@@ -300,6 +299,37 @@ k_band_solve(int N, int b, const T* __restrict__ band, const T* __restrict__ Din
   }
 }
 
+template <int MODE, typename T>
+__global__ void __launch_bounds__(kSolveThreads)
+k_band_solve(int N, int b, const T* __restrict__ band, const T* __restrict__ Dinv,
+             const T* __restrict__ vin, const double* __restrict__ dsc, T* __restrict__ ty,
+             T* __restrict__ tp, T* __restrict__ z, int ld, int c0, int ncols, int ring_mask) {
+  band_solve_body<MODE, T>(N, b, band, Dinv, vin, dsc, ty, tp, z, ld, c0, ncols, ring_mask);
+}
+
+__host__ __device__ inline int ring_rows(int b) {
+  int r = 1;
+  while (r < b + kNB + 1) r <<= 1;
+  return r;
+}
+
+// Batched FP32 band solve: instance blockIdx.z, column pair blockIdx.x of its window,
+// Krylov vector j (V_j in, Z_j out).
+template <int MODE>
+__global__ void __launch_bounds__(kSolveThreads) kb_band_solve(const InstDev* __restrict__ tab, int j) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active || I.nf <= 0 || (int)blockIdx.x * kCols >= I.nf) return;
+  const size_t vs = (size_t)I.n_dof * I.wcap;
+  const bool u = (MODE == FWD_U_FROM_V || MODE == BWD_U_TO_Z);
+  const int N = u ? 2 * I.n_nodes : I.n_nodes;
+  const int b = u ? I.band_u : I.band_p;
+  const float* band = (MODE == FWD_U_FROM_V) ? I.Lu : (MODE == BWD_U_TO_Z) ? I.Uu
+                    : (MODE == BWD_P_TO_Z) ? I.Up : I.Lp;
+  const float* Dinv = u ? I.Du : I.Dp;
+  band_solve_body<MODE, float>(N, b, band, Dinv, I.V + j * vs, I.dsc, I.tu, I.tp, I.Z + j * vs, I.wcap, I.c0, I.nf,
+                               ring_rows(b) - 1);
+}
+
 __global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
     dst[k] = (float)src[k];
@@ -374,12 +404,6 @@ biot_status band_setup(biot_ctx* ctx, int kind) {
   return BIOT_OK;
 }
 
-static int ring_rows(int b) {
-  int r = 1;
-  while (r < b + kNB + 1) r <<= 1;
-  return r;
-}
-
 template <typename T> struct BandBufs;
 template <> struct BandBufs<double> {
   static double* tu(biot_ctx* c) { return c->tu; }
@@ -432,6 +456,32 @@ void precond_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols) {
 }
 
 template void precond_apply<double>(biot_ctx*, const double*, double*, int, int);
+
+size_t batched_solve_smem(int max_band) { return sizeof(float) * ((size_t)ring_rows(max_band) * kCols + kNB * kCols); }
+
+void batched_precond_apply(const InstDev* tab, int count, int j, int max_wcap, int max_band, bool tri,
+                           cudaStream_t s) {
+  const dim3 grid(div_up(max_wcap, kCols), 1, count);
+  const size_t smem = batched_solve_smem(max_band);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kb_band_solve<FWD_U_FROM_V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(kb_band_solve<BWD_U_TO_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(kb_band_solve<FWD_P_FROM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(kb_band_solve<FWD_P_FROM_V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(kb_band_solve<BWD_P_TO_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  BIOT_LAUNCH(kb_band_solve<FWD_U_FROM_V>, grid, kSolveThreads, smem, s, tab, j);
+  BIOT_LAUNCH(kb_band_solve<BWD_U_TO_Z>, grid, kSolveThreads, smem, s, tab, j);
+  if (tri) {
+    launch_batched_coupling(tab, count, j, s);
+    BIOT_LAUNCH(kb_band_solve<FWD_P_FROM_T>, grid, kSolveThreads, smem, s, tab, j);
+  } else {
+    BIOT_LAUNCH(kb_band_solve<FWD_P_FROM_V>, grid, kSolveThreads, smem, s, tab, j);
+  }
+  BIOT_LAUNCH(kb_band_solve<BWD_P_TO_Z>, grid, kSolveThreads, smem, s, tab, j);
+}
 template void precond_apply<float>(biot_ctx*, const float*, float*, int, int);
 
 }  // namespace biot

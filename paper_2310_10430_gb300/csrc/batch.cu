@@ -1,0 +1,316 @@
+// Batched solve of many independent Biot instances (biot_batch_solve).
+//
+// Instances of uneven mesh size, permeability field and N_t are solved together:
+// every kernel of a sweep (FP32 correction residual, band solves, coupling,
+// AA z, CGS2, Givens, update) processes all instances in one launch, the
+// instance given by blockIdx.z and its buffers and window by a device-resident
+// table. Host decisions (retiring converged steps, moving windows, the FP64
+// refinement test) are taken once per sweep for all instances together; the
+// FGMRES cycle of a sweep has a launch sequence that depends only on n_iter,
+// so it is captured once in a CUDA graph and replayed every sweep after the
+// table is refreshed. There is no persistent kernel and no device-wide wait.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace biot {
+namespace {
+
+__global__ void kb_zero_correction(const InstDev* __restrict__ tab) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active) return;
+  const size_t tot = (size_t)I.n_dof * I.ldx;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < tot; k += (size_t)gridDim.x * blockDim.x)
+    I.X[k] = 0.0f;
+}
+
+__global__ void kb_add_correction(const InstDev* __restrict__ tab) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active) return;
+  const long long tot = (long long)I.n_dof * I.n_t;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / I.n_t), n = 1 + (int)(idx % I.n_t);
+    I.X64w[(size_t)r * I.ldx + n] += (double)I.X[(size_t)r * I.ldx + n];
+  }
+}
+
+// out[z][s][c] = colscal_z[(CS_RR + s) * wcap + c] for s < 2, c < wmax (zeros past the window).
+__global__ void kb_gather(const InstDev* __restrict__ tab, int wmax, int nslot, double* __restrict__ out) {
+  const InstDev& I = tab[blockIdx.z];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (c >= wmax || s >= nslot) return;
+  out[((size_t)blockIdx.z * nslot + s) * wmax + c] =
+      (I.active && c < I.wcap) ? I.colscal[(size_t)(CS_RR + s) * I.wcap + c] : 0.0;
+}
+
+struct BatchState {
+  int lo = 1, w = 0, lo_since = 0, total = 0;
+  bool done = false, inner_done = false;
+  double fst2 = 0.0, prev = INFINITY, rel = INFINITY;
+  biot_status st = BIOT_OK;
+};
+
+InstDev describe(biot_ctx* c) {
+  InstDev I{};
+  I.n_nodes = c->n_nodes;
+  I.n_dof = c->n_dof;
+  I.ldx = c->ldx;
+  I.wcap = c->wcap;
+  I.n_t = c->n_t;
+  I.band_u = c->band_u;
+  I.band_p = c->band_p;
+  I.nodeptr = c->nodeptr;
+  I.nbr = c->nbr;
+  I.rowptr = c->rowptr;
+  I.dsc = c->dsc;
+  I.val64 = c->val;
+  I.apval64 = c->apval;
+  I.X64 = c->X;
+  I.F64 = c->F;
+  I.X64w = c->X;
+  I.val = c->lp.val;
+  I.apval = c->lp.apval;
+  I.valbf = c->lp.val_bf16;
+  I.apvalbf = c->lp.apval_bf16;
+  I.X = c->lp.X;
+  I.F = c->lp.F;
+  I.V = c->lp.V;
+  I.Z = c->lp.Z;
+  I.Wv = c->lp.Wv;
+  I.tu = c->lp.tu;
+  I.tp = c->lp.tp;
+  I.Lu = c->lp.Lu;
+  I.Uu = c->lp.Uu;
+  I.Du = c->lp.Du;
+  I.Lp = c->lp.Lp;
+  I.Up = c->lp.Up;
+  I.Dp = c->lp.Dp;
+  I.part = c->part;
+  I.colscal = c->colscal;
+  I.H = c->H;
+  I.hvec = c->hvec;
+  I.kcol = c->kcol;
+  return I;
+}
+
+}  // namespace
+}  // namespace biot
+
+using namespace biot;
+
+extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, double tol, int32_t max_outer,
+                                        int32_t use_graph, int32_t* sweeps_done, double* final_rel_res) {
+  if (!ctxs || count < 1) return fail(nullptr, BIOT_E_INVALID, "biot_batch_solve: no contexts");
+  if (!(tol >= 0.0) || max_outer < 1) return fail(nullptr, BIOT_E_INVALID, "biot_batch_solve: tol >= 0, max_outer >= 1");
+  biot_ctx* c0 = ctxs[0];
+  for (int i = 0; i < count; ++i) {
+    biot_ctx* c = ctxs[i];
+    if (!c) return fail(nullptr, BIOT_E_INVALID, "biot_batch_solve: context %d is NULL", i);
+    if (!c->assembled || c->precond == 0)
+      return fail(c, BIOT_E_STATE, "biot_batch_solve: context %d not assembled and set up", i);
+    if (c->prm.precision == BIOT_FP64)
+      return fail(c, BIOT_E_INVALID, "biot_batch_solve: context %d must use BIOT_FP32 or BIOT_BF16VAL_FP32ACC", i);
+    if (c->prm.precision != c0->prm.precision || c->n_iter != c0->n_iter || c->precond != c0->precond)
+      return fail(c, BIOT_E_INVALID, "biot_batch_solve: contexts differ in precision, n_iter or preconditioner");
+    if (c->wcap != c->n_t) return fail(c, BIOT_E_INVALID, "biot_batch_solve: context %d needs window = N_t", i);
+  }
+  const bool bf16 = c0->prm.precision == BIOT_BF16VAL_FP32ACC;
+  const bool tri = c0->precond == BIOT_PRECOND_TRI;
+  const int n_iter = c0->n_iter;
+  int max_wcap = 0, max_ndof = 0, max_band = 0;
+  for (int i = 0; i < count; ++i) {
+    max_wcap = std::max(max_wcap, ctxs[i]->wcap);
+    max_ndof = std::max(max_ndof, ctxs[i]->n_dof);
+    max_band = std::max(max_band, std::max(ctxs[i]->band_u, ctxs[i]->band_p));
+  }
+  for (int i = 0; i < count; ++i) BIOT_CU(ctxs[i], cudaStreamSynchronize(ctxs[i]->stream));
+
+  cudaStream_t s = nullptr;
+  InstDev* tab_d = nullptr;
+  InstDev* tab_h = nullptr;
+  double* gat_d = nullptr;
+  double* gat_h = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  size_t graph_nodes = 0;
+  biot_status result = BIOT_OK;
+  std::vector<BatchState> B(count);
+  const double tol_inner = 1e-5;
+  const int stall_cap = 25;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (s) cudaStreamSynchronize(s);
+    if (tab_d) cudaFree(tab_d);
+    if (gat_d) cudaFree(gat_d);
+    if (tab_h) cudaFreeHost(tab_h);
+    if (gat_h) cudaFreeHost(gat_h);
+    if (s) cudaStreamDestroy(s);
+  };
+#define BATCH_CU(call)                                                                 \
+  do {                                                                                 \
+    cudaError_t _e = (call);                                                           \
+    if (_e != cudaSuccess) {                                                           \
+      result = fail(c0, BIOT_E_CUDA, "biot_batch_solve: %s: %s", #call, cudaGetErrorString(_e)); \
+      cleanup();                                                                       \
+      return result;                                                                   \
+    }                                                                                  \
+  } while (0)
+
+  BATCH_CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  BATCH_CU(cudaMalloc(&tab_d, sizeof(InstDev) * count));
+  BATCH_CU(cudaMalloc(&gat_d, sizeof(double) * count * 2 * max_wcap));
+  BATCH_CU(cudaMallocHost(&tab_h, sizeof(InstDev) * count));
+  BATCH_CU(cudaMallocHost(&gat_h, sizeof(double) * count * 2 * max_wcap));
+  for (int i = 0; i < count; ++i) {
+    tab_h[i] = describe(ctxs[i]);
+    biot_status st = fst_norm2_ctx(ctxs[i], &B[i].fst2);
+    if (st != BIOT_OK) {
+      cleanup();
+      return st;
+    }
+  }
+  auto upload = [&]() { return cudaMemcpyAsync(tab_d, tab_h, sizeof(InstDev) * count, cudaMemcpyHostToDevice, s); };
+  auto gather = [&](int nslot) -> cudaError_t {
+    BIOT_LAUNCH(kb_gather, dim3(div_up(max_wcap, 128), nslot, count), 128, 0, s, tab_d, max_wcap, nslot, gat_d);
+    cudaError_t e = cudaMemcpyAsync(gat_h, gat_d, sizeof(double) * count * nslot * max_wcap,
+                                    cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+  };
+  auto run_cycle = [&]() -> cudaError_t {
+    if (!use_graph) {
+      batched_fgmres_cycle(tab_d, count, n_iter, max_wcap, max_ndof, max_band, bf16, tri, s);
+      return cudaGetLastError();
+    }
+    if (!exec) {
+      cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return e;
+      const int64_t before = g_launches.load();
+      batched_fgmres_cycle(tab_d, count, n_iter, max_wcap, max_ndof, max_band, bf16, tri, s);
+      g_launches.store(before);  // captured, not launched
+      e = cudaStreamEndCapture(s, &graph);
+      if (e != cudaSuccess) return e;
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      if (e != cudaSuccess) return e;
+      cudaGraphGetNodes(graph, nullptr, &graph_nodes);
+    }
+    g_launches.fetch_add((int64_t)graph_nodes);
+    return cudaGraphLaunch(exec, s);
+  };
+
+  for (int round = 0;; ++round) {
+    // FP64 residual of every open instance -> FP32 correction right-hand side
+    for (int i = 0; i < count; ++i) tab_h[i].active = B[i].done ? 0 : 1;
+    BATCH_CU(upload());
+    launch_batched_residual_to_f32(tab_d, count, s);
+    batched_refine_reduce(tab_d, count, max_wcap, s);
+    BIOT_LAUNCH(kb_zero_correction, dim3(256, 1, count), 256, 0, s, tab_d);
+    BATCH_CU(cudaGetLastError());
+    BATCH_CU(gather(1));
+    bool any_open = false;
+    for (int i = 0; i < count; ++i) {
+      BatchState& S = B[i];
+      if (S.done) continue;
+      double rr2 = 0.0;
+      for (int c = 0; c < ctxs[i]->n_t; ++c) rr2 += gat_h[(size_t)i * max_wcap + c];
+      S.rel = S.fst2 > 0.0 ? std::sqrt(rr2 / S.fst2) : std::sqrt(rr2);
+      if (!std::isfinite(S.rel)) {
+        S.done = true;
+        S.st = BIOT_E_DIVERGED;
+      } else if (S.rel <= tol) {
+        S.done = true;
+      } else if (S.total >= max_outer || (round > 0 && !(S.rel < 0.5 * S.prev))) {
+        S.done = true;
+        S.st = BIOT_E_NOT_CONVERGED;
+      } else {
+        S.prev = S.rel;
+        S.lo = 1;
+        S.w = 0;
+        S.lo_since = 0;
+        S.inner_done = false;
+        any_open = true;
+      }
+    }
+    if (!any_open) break;
+    // inner FP32 PinT solves of all open instances, in lock step
+    for (;;) {
+      bool any = false;
+      for (int i = 0; i < count; ++i) {
+        BatchState& S = B[i];
+        InstDev& I = tab_h[i];
+        I.active = 0;
+        I.nres = I.nf = 0;
+        if (S.done || S.inner_done) continue;
+        if (S.lo > ctxs[i]->n_t || S.total >= max_outer) {
+          S.inner_done = true;
+          continue;
+        }
+        ++S.w;
+        ++S.total;
+        const int hi = std::min(std::min(S.w, ctxs[i]->n_t), S.lo + I.wcap - 1);
+        I.active = 1;
+        I.lo = S.lo;
+        I.nres = hi - S.lo + 1;
+        any = true;
+      }
+      if (!any) break;
+      BATCH_CU(upload());
+      launch_batched_residual_lp(tab_d, count, bf16, s);
+      batched_residual_reduce(tab_d, count, max_wcap, s);
+      BATCH_CU(cudaGetLastError());
+      BATCH_CU(gather(2));
+      for (int i = 0; i < count; ++i) {
+        InstDev& I = tab_h[i];
+        if (!I.active) continue;
+        BatchState& S = B[i];
+        const double* rr = gat_h + ((size_t)i * 2) * max_wcap;
+        const double* bb = rr + max_wcap;
+        int k = 0;
+        while (k < I.nres) {
+          const double r = std::sqrt(rr[k]), q = std::sqrt(bb[k]);
+          const double rel = q > 0.0 ? r / q : (r == 0.0 ? 0.0 : INFINITY);
+          if (!std::isfinite(rel)) {
+            S.st = BIOT_E_DIVERGED;
+            S.done = true;
+            break;
+          }
+          if (rel <= tol_inner || (k == 0 && S.w - S.lo_since >= stall_cap)) ++k;
+          else break;
+        }
+        if (S.done) {
+          I.active = 0;
+          continue;
+        }
+        I.c0 = k;
+        I.nf = I.nres - k;
+        if (k > 0) S.lo_since = S.w;
+        S.lo += k;
+      }
+      BATCH_CU(upload());
+      BATCH_CU(run_cycle());
+    }
+    // x <- x + d for every open instance
+    for (int i = 0; i < count; ++i) tab_h[i].active = B[i].done ? 0 : 1;
+    BATCH_CU(upload());
+    BIOT_LAUNCH(kb_add_correction, dim3(256, 1, count), 256, 0, s, tab_d);
+    BATCH_CU(cudaGetLastError());
+  }
+  BATCH_CU(cudaStreamSynchronize(s));
+  for (int i = 0; i < count; ++i) {
+    ctxs[i]->lp.correction_ready = false;
+    if (sweeps_done) sweeps_done[i] = B[i].total;
+    if (final_rel_res) final_rel_res[i] = B[i].rel;
+    if (B[i].st != BIOT_OK && result == BIOT_OK) {
+      result = fail(ctxs[i], B[i].st, "biot_batch_solve: instance %d ended with residual %.3g", i, B[i].rel);
+      fail(nullptr, B[i].st, "biot_batch_solve: instance %d ended with residual %.3g", i, B[i].rel);
+    }
+  }
+  cleanup();
+#undef BATCH_CU
+  return result;
+}

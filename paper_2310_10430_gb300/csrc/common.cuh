@@ -59,6 +59,45 @@ struct LowPrec {
   bool correction_ready = false; // lp.F holds the residual of the current X
 };
 
+// One instance of a batch, as the batched kernels see it (device-resident table).
+// Window: residual columns [0, nres) for steps lo .. lo + nres - 1; FGMRES on
+// columns [c0, c0 + nf).
+struct InstDev {
+  int n_nodes, n_dof, ldx, wcap, n_t, band_u, band_p;
+  int lo, nres, c0, nf, active;
+  const int32_t* nodeptr;
+  const int32_t* nbr;
+  const int32_t* rowptr;
+  const double* dsc;
+  const double* val64;
+  const double* apval64;
+  const double* X64;
+  const double* F64;
+  double* X64w;
+  const float* val;
+  const float* apval;
+  const __nv_bfloat16* valbf;
+  const __nv_bfloat16* apvalbf;
+  float* X;
+  float* F;
+  float* V;
+  float* Z;
+  float* Wv;
+  float* tu;
+  float* tp;
+  const float* Lu;
+  const float* Uu;
+  const float* Du;
+  const float* Lp;
+  const float* Up;
+  const float* Dp;
+  double* part;
+  double* colscal;
+  double* H;
+  double* hvec;
+  int32_t* kcol;
+};
+
 }  // namespace biot
 
 struct biot_ctx {
@@ -184,5 +223,18 @@ template <typename T> void precond_apply(biot_ctx* ctx, const T* vin, T* z, int 
 enum ColScalar { CS_RR = 0, CS_BB, CS_BETA0, CS_WN0, CS_WW, CS_INVH, CS_ACTIVE, kColScalars };
 void reduce_partials(biot_ctx* ctx, int nslots, int ncols, double* out, int ldo, int c0);
 template <typename T> biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols);
+
+// ---- batched launches (batch.cu drives them) ----
+void launch_batched_residual_lp(const InstDev* tab, int count, bool bf16, cudaStream_t s);
+void launch_batched_residual_to_f32(const InstDev* tab, int count, cudaStream_t s);
+void launch_batched_spmm(const InstDev* tab, int count, bool bf16, int j, cudaStream_t s);
+void launch_batched_coupling(const InstDev* tab, int count, int j, cudaStream_t s);
+void batched_precond_apply(const InstDev* tab, int count, int j, int max_wcap, int max_band, bool tri,
+                           cudaStream_t s);
+void batched_fgmres_cycle(const InstDev* tab, int count, int n_iter, int max_wcap, int max_ndof, int max_band,
+                          bool bf16, bool tri, cudaStream_t s);
+void batched_residual_reduce(const InstDev* tab, int count, int max_wcap, cudaStream_t s);
+void batched_refine_reduce(const InstDev* tab, int count, int max_wcap, cudaStream_t s);
+biot_status fst_norm2_ctx(biot_ctx* ctx, double* out);
 
 }  // namespace biot

@@ -14,6 +14,8 @@
 // scheduling.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace biot {
 
 namespace {
@@ -26,8 +28,8 @@ constexpr int kRecY = kRecSN + kMaxIter;                      // y[kMaxIter]
 constexpr int kRec = kRecY + kMaxIter;
 
 // out[s][c] = sum over blocks of part[s][block][c], s < nslots, c in [c0, c0 + ncols).
-__global__ void k_reduce(const double* __restrict__ part, int nblocks, int nslots, int ld, int c0, int ncols,
-                         double* __restrict__ out, int ldo) {
+__device__ __forceinline__ void reduce_body(const double* __restrict__ part, int nblocks, int nslots, int ld, int c0,
+                                            int ncols, double* __restrict__ out, int ldo) {
   const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blockIdx.y;
   if (c >= c0 + ncols || s >= nslots) return;
@@ -37,12 +39,16 @@ __global__ void k_reduce(const double* __restrict__ part, int nblocks, int nslot
   out[(size_t)s * ldo + c] = acc;
 }
 
+__global__ void k_reduce(const double* __restrict__ part, int nblocks, int nslots, int ld, int c0, int ncols,
+                         double* __restrict__ out, int ldo) {
+  reduce_body(part, nblocks, nslots, ld, c0, ncols, out, ldo);
+}
+
 // Partial dot products part[i][block][c] = sum_{rows of block} V_i[r][c] * w[r][c]
 // (products accumulated in T within a thread, combined in FP64 across threads and blocks).
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_dots(const T* __restrict__ V, size_t vstride, const T* __restrict__ w, int nrows, int ld, int c0,
-       int ncols, double* __restrict__ part) {
+__device__ __forceinline__ void dots_body(const T* __restrict__ V, size_t vstride, const T* __restrict__ w, int nrows,
+                                          int ld, int c0, int ncols, double* __restrict__ part) {
   __shared__ double sm[8][32];
   const int i = blockIdx.y;
   const T* Vi = V + (size_t)i * vstride;
@@ -66,30 +72,55 @@ k_dots(const T* __restrict__ V, size_t vstride, const T* __restrict__ w, int nro
   }
 }
 
-// w[r][c] -= sum_i h[i][c] V_i[r][c].
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_dots(const T* __restrict__ V, size_t vstride, const T* __restrict__ w, int nrows, int ld, int c0, int ncols,
+       double* __restrict__ part) {
+  dots_body<T>(V, vstride, w, nrows, ld, c0, ncols, part);
+}
+
+// w[r][c] -= sum_i h[i][c] V_i[r][c] (grid-stride over (r, c)).
+template <typename T>
+__device__ __forceinline__ void gs_axpy_body(const T* __restrict__ V, size_t vstride, int nvec,
+                                             const double* __restrict__ h, T* __restrict__ w, int nrows, int ld,
+                                             int c0, int ncols) {
+  const long long total = (long long)nrows * ncols;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
+    T acc = w[(size_t)r * ld + c];
+    for (int i = 0; i < nvec; ++i) acc -= (T)h[(size_t)i * ld + c] * V[(size_t)i * vstride + (size_t)r * ld + c];
+    w[(size_t)r * ld + c] = acc;
+  }
+}
+
 template <typename T>
 __global__ void k_gs_axpy(const T* __restrict__ V, size_t vstride, int nvec, const double* __restrict__ h,
                           T* __restrict__ w, int nrows, int ld, int c0, int ncols) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)nrows * ncols) return;
-  const int r = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
-  T acc = w[(size_t)r * ld + c];
-  for (int i = 0; i < nvec; ++i) acc -= (T)h[(size_t)i * ld + c] * V[(size_t)i * vstride + (size_t)r * ld + c];
-  w[(size_t)r * ld + c] = acc;
+  gs_axpy_body<T>(V, vstride, nvec, h, w, nrows, ld, c0, ncols);
 }
 
-// dst[r][c] = src[r][c] * scale[c].
+// dst[r][c] = src[r][c] * scale[c] (grid-stride).
+template <typename T>
+__device__ __forceinline__ void scale_cols_body(const T* __restrict__ src, T* __restrict__ dst,
+                                                const double* __restrict__ scale, int nrows, int ld, int c0,
+                                                int ncols) {
+  const long long total = (long long)nrows * ncols;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
+    dst[(size_t)r * ld + c] = src[(size_t)r * ld + c] * (T)scale[c];
+  }
+}
+
 template <typename T>
 __global__ void k_scale_cols(const T* __restrict__ src, T* __restrict__ dst, const double* __restrict__ scale,
                              int nrows, int ld, int c0, int ncols) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)nrows * ncols) return;
-  const int r = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
-  dst[(size_t)r * ld + c] = src[(size_t)r * ld + c] * (T)scale[c];
+  scale_cols_body<T>(src, dst, scale, nrows, ld, c0, ncols);
 }
 
-__global__ void k_fgmres_init(double* __restrict__ cs, int ld, int c0, int ncols, double* __restrict__ rec,
-                              int32_t* __restrict__ kcol) {
+__device__ __forceinline__ void fgmres_init_body(double* __restrict__ cs, int ld, int c0, int ncols,
+                                                 double* __restrict__ rec, int32_t* __restrict__ kcol) {
   const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= c0 + ncols) return;
   const double beta0 = sqrt(cs[CS_RR * ld + c]);
@@ -103,9 +134,15 @@ __global__ void k_fgmres_init(double* __restrict__ cs, int ld, int c0, int ncols
   kcol[c] = 0;
 }
 
+__global__ void k_fgmres_init(double* __restrict__ cs, int ld, int c0, int ncols, double* __restrict__ rec,
+                              int32_t* __restrict__ kcol) {
+  fgmres_init_body(cs, ld, c0, ncols, rec, kcol);
+}
+
 // Arnoldi step j of column c: store H[:, j], rotate, extend g, test breakdown.
-__global__ void k_givens(int j, double* __restrict__ cs, const double* __restrict__ h1, const double* __restrict__ h2,
-                         int ld, int c0, int ncols, double* __restrict__ rec, int32_t* __restrict__ kcol) {
+__device__ __forceinline__ void givens_body(int j, double* __restrict__ cs, const double* __restrict__ h1,
+                                            const double* __restrict__ h2, int ld, int c0, int ncols,
+                                            double* __restrict__ rec, int32_t* __restrict__ kcol) {
   const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= c0 + ncols) return;
   if (cs[CS_ACTIVE * ld + c] == 0.0) {
@@ -148,8 +185,14 @@ __global__ void k_givens(int j, double* __restrict__ cs, const double* __restric
   }
 }
 
+__global__ void k_givens(int j, double* __restrict__ cs, const double* __restrict__ h1, const double* __restrict__ h2,
+                         int ld, int c0, int ncols, double* __restrict__ rec, int32_t* __restrict__ kcol) {
+  givens_body(j, cs, h1, h2, ld, c0, ncols, rec, kcol);
+}
+
 // Back substitution R y = g for the k steps each column took.
-__global__ void k_backsolve(int ld, int c0, int ncols, double* __restrict__ rec, const int32_t* __restrict__ kcol) {
+__device__ __forceinline__ void backsolve_body(int ld, int c0, int ncols, double* __restrict__ rec,
+                                               const int32_t* __restrict__ kcol) {
   const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= c0 + ncols) return;
   double* R = rec + (size_t)c * kRec;
@@ -164,20 +207,111 @@ __global__ void k_backsolve(int ld, int c0, int ncols, double* __restrict__ rec,
   }
 }
 
-// X[r][lo + c] += sum_{i < k_c} y_i[c] Z_i[r][c].
+__global__ void k_backsolve(int ld, int c0, int ncols, double* __restrict__ rec, const int32_t* __restrict__ kcol) {
+  backsolve_body(ld, c0, ncols, rec, kcol);
+}
+
+// X[r][lo + c] += sum_{i < k_c} y_i[c] Z_i[r][c] (grid-stride).
+template <typename T>
+__device__ __forceinline__ void update_x_body(const T* __restrict__ Z, size_t zstride, const double* __restrict__ rec,
+                                              const int32_t* __restrict__ kcol, T* __restrict__ X, int ldx, int lo,
+                                              int nrows, int ld, int c0, int ncols) {
+  const long long total = (long long)nrows * ncols;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
+    const int k = kcol[c];
+    if (k == 0) continue;
+    const double* y = rec + (size_t)c * kRec + kRecY;
+    T acc = 0;
+    for (int i = 0; i < k; ++i) acc += (T)y[i] * Z[(size_t)i * zstride + (size_t)r * ld + c];
+    X[(size_t)r * ldx + lo + c] += acc;
+  }
+}
+
 template <typename T>
 __global__ void k_update_x(const T* __restrict__ Z, size_t zstride, const double* __restrict__ rec,
-                           const int32_t* __restrict__ kcol, T* __restrict__ X, int ldx, int lo, int nrows,
-                           int ld, int c0, int ncols) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)nrows * ncols) return;
-  const int r = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
-  const int k = kcol[c];
-  if (k == 0) return;
-  const double* y = rec + (size_t)c * kRec + kRecY;
-  T acc = 0;
-  for (int i = 0; i < k; ++i) acc += (T)y[i] * Z[(size_t)i * zstride + (size_t)r * ld + c];
-  X[(size_t)r * ldx + lo + c] += acc;
+                           const int32_t* __restrict__ kcol, T* __restrict__ X, int ldx, int lo, int nrows, int ld,
+                           int c0, int ncols) {
+  update_x_body<T>(Z, zstride, rec, kcol, X, ldx, lo, nrows, ld, c0, ncols);
+}
+
+// ---- batched variants: instance = blockIdx.z, arguments from the instance table ----
+
+enum RedDst { RD_RES = 0, RD_WN0, RD_H1, RD_H2, RD_WW };
+
+__global__ void kb_reduce(const InstDev* __restrict__ tab, int dst, int nslots) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active) return;
+  const int ld = I.wcap;
+  double* out = I.colscal;
+  int c0 = I.c0, nc = I.nf;
+  switch (dst) {
+    case RD_RES: out = I.colscal + CS_RR * ld; c0 = 0; nc = I.nres; break;
+    case RD_WN0: out = I.colscal + CS_WN0 * ld; break;
+    case RD_H1: out = I.hvec; break;
+    case RD_H2: out = I.hvec + (size_t)(kMaxIter + 1) * ld; break;
+    default: out = I.colscal + CS_WW * ld; break;
+  }
+  if (nc <= 0) return;
+  reduce_body(I.part, kRedBlocks, nslots, ld, c0, nc, out, ld);
+}
+
+// Full-range reduction of the refinement residual (slot 0 over all N_t steps).
+__global__ void kb_reduce_refine(const InstDev* __restrict__ tab) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active) return;
+  reduce_body(I.part, kRedBlocks, 1, I.wcap, 0, I.n_t, I.colscal + CS_RR * I.wcap, I.wcap);
+}
+
+__global__ void kb_fgmres_init(const InstDev* __restrict__ tab) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active || I.nf <= 0) return;
+  fgmres_init_body(I.colscal, I.wcap, I.c0, I.nf, I.H, I.kcol);
+}
+
+// V_{j} = src * invh; src = V_0 (j = 0, in place) or w.
+__global__ void kb_scale(const InstDev* __restrict__ tab, int j) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active || I.nf <= 0) return;
+  const size_t vs = (size_t)I.n_dof * I.wcap;
+  const float* src = j == 0 ? I.V : I.Wv;
+  scale_cols_body<float>(src, I.V + j * vs, I.colscal + CS_INVH * I.wcap, I.n_dof, I.wcap, I.c0, I.nf);
+}
+
+// blockIdx.y = basis vector index; nvec = 0 computes |w|^2.
+__global__ void __launch_bounds__(256) kb_dots(const InstDev* __restrict__ tab, int nvec) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active || I.nf <= 0) return;
+  const size_t vs = (size_t)I.n_dof * I.wcap;
+  if (nvec == 0) dots_body<float>(I.Wv, vs, I.Wv, I.n_dof, I.wcap, I.c0, I.nf, I.part);
+  else dots_body<float>(I.V, vs, I.Wv, I.n_dof, I.wcap, I.c0, I.nf, I.part);
+}
+
+__global__ void kb_gs_axpy(const InstDev* __restrict__ tab, int nvec, int pass) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active || I.nf <= 0) return;
+  const size_t vs = (size_t)I.n_dof * I.wcap;
+  const double* h = I.hvec + (pass == 0 ? 0 : (size_t)(kMaxIter + 1) * I.wcap);
+  gs_axpy_body<float>(I.V, vs, nvec, h, I.Wv, I.n_dof, I.wcap, I.c0, I.nf);
+}
+
+__global__ void kb_givens(const InstDev* __restrict__ tab, int j) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active || I.nf <= 0) return;
+  givens_body(j, I.colscal, I.hvec, I.hvec + (size_t)(kMaxIter + 1) * I.wcap, I.wcap, I.c0, I.nf, I.H, I.kcol);
+}
+
+__global__ void kb_backsolve(const InstDev* __restrict__ tab) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active || I.nf <= 0) return;
+  backsolve_body(I.wcap, I.c0, I.nf, I.H, I.kcol);
+}
+
+__global__ void kb_update_x(const InstDev* __restrict__ tab) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active || I.nf <= 0) return;
+  update_x_body<float>(I.Z, (size_t)I.n_dof * I.wcap, I.H, I.kcol, I.X, I.ldx, I.lo, I.n_dof, I.wcap, I.c0, I.nf);
 }
 
 }  // namespace
@@ -216,7 +350,7 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
   double* h1 = ctx->hvec;
   double* h2 = ctx->hvec + (size_t)(kMaxIter + 1) * ld;
   const int cblk = div_up(ncols, 128);
-  const int eblk = div_up((long long)nd * ncols, 256);
+  const int eblk = std::min(div_up((long long)nd * ncols, 256), 8192);
   BIOT_LAUNCH(k_fgmres_init, cblk, 128, 0, s, cs, ld, c0, ncols, ctx->H, ctx->kcol);
   BIOT_LAUNCH(k_scale_cols<T>, eblk, 256, 0, s, V, V, cs + CS_INVH * ld, nd, ld, c0, ncols);
   for (int j = 0; j < ctx->n_iter; ++j) {
@@ -245,6 +379,40 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
 }
 
 template biot_status fgmres_cycle<double>(biot_ctx*, int, int, int);
+
+// One FGMRES(n_iter) cycle for every instance of a batch (windows in the table).
+// The launch sequence depends only on n_iter, so it can be captured in a CUDA graph.
+void batched_fgmres_cycle(const InstDev* tab, int count, int n_iter, int max_wcap, int max_ndof, int max_band,
+                          bool bf16, bool tri, cudaStream_t s) {
+  const int cblk = div_up(max_wcap, 128);
+  const int eblk = std::min(div_up((long long)max_ndof * max_wcap, 256), 2048);
+  BIOT_LAUNCH(kb_fgmres_init, dim3(cblk, 1, count), 128, 0, s, tab);
+  BIOT_LAUNCH(kb_scale, dim3(eblk, 1, count), 256, 0, s, tab, 0);
+  for (int j = 0; j < n_iter; ++j) {
+    batched_precond_apply(tab, count, j, max_wcap, max_band, tri, s);
+    launch_batched_spmm(tab, count, bf16, j, s);
+    BIOT_LAUNCH(kb_reduce, dim3(cblk, 1, count), 128, 0, s, tab, (int)RD_WN0, 1);
+    for (int pass = 0; pass < 2; ++pass) {
+      BIOT_LAUNCH(kb_dots, dim3(kRedBlocks, j + 1, count), 256, 0, s, tab, j + 1);
+      BIOT_LAUNCH(kb_reduce, dim3(cblk, j + 1, count), 128, 0, s, tab, (int)(pass == 0 ? RD_H1 : RD_H2), j + 1);
+      BIOT_LAUNCH(kb_gs_axpy, dim3(eblk, 1, count), 256, 0, s, tab, j + 1, pass);
+    }
+    BIOT_LAUNCH(kb_dots, dim3(kRedBlocks, 1, count), 256, 0, s, tab, 0);
+    BIOT_LAUNCH(kb_reduce, dim3(cblk, 1, count), 128, 0, s, tab, (int)RD_WW, 1);
+    BIOT_LAUNCH(kb_givens, dim3(cblk, 1, count), 128, 0, s, tab, j);
+    if (j + 1 < n_iter) BIOT_LAUNCH(kb_scale, dim3(eblk, 1, count), 256, 0, s, tab, j + 1);
+  }
+  BIOT_LAUNCH(kb_backsolve, dim3(cblk, 1, count), 128, 0, s, tab);
+  BIOT_LAUNCH(kb_update_x, dim3(eblk, 1, count), 256, 0, s, tab);
+}
+
+void batched_residual_reduce(const InstDev* tab, int count, int max_wcap, cudaStream_t s) {
+  BIOT_LAUNCH(kb_reduce, dim3(div_up(max_wcap, 128), 2, count), 128, 0, s, tab, (int)RD_RES, 2);
+}
+
+void batched_refine_reduce(const InstDev* tab, int count, int max_wcap, cudaStream_t s) {
+  BIOT_LAUNCH(kb_reduce_refine, dim3(div_up(max_wcap, 128), 1, count), 128, 0, s, tab);
+}
 template biot_status fgmres_cycle<float>(biot_ctx*, int, int, int);
 
 }  // namespace biot

@@ -14,6 +14,8 @@
 // lanes and blocks.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace biot {
 
 namespace {
@@ -46,8 +48,7 @@ __device__ __forceinline__ void block_sum_to(double (*sm)[32], double val, doubl
 // out[3v+f][c] = (EQ ? d : 1) * (F + A' X_{n-1} - AA X_n)[3v+f], n = lo + c; partial |d r|^2 and
 // |d b|^2 in part slots 0 and 1.
 template <typename XT, typename VT, typename OT, bool EQ>
-__global__ void __launch_bounds__(kWarps * 32)
-k_residual(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
+__device__ __forceinline__ void residual_body(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
            const int32_t* __restrict__ rowptr, const VT* __restrict__ val, const VT* __restrict__ apval,
            const double* __restrict__ dsc, const XT* __restrict__ X, const XT* __restrict__ F, int ldx, int lo,
            int ncols, OT* __restrict__ out, int ldo, int ocol0, double* __restrict__ part, int ldp) {
@@ -102,10 +103,19 @@ k_residual(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restric
   }
 }
 
+template <typename XT, typename VT, typename OT, bool EQ>
+__global__ void __launch_bounds__(kWarps * 32)
+k_residual(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
+           const int32_t* __restrict__ rowptr, const VT* __restrict__ val, const VT* __restrict__ apval,
+           const double* __restrict__ dsc, const XT* __restrict__ X, const XT* __restrict__ F, int ldx, int lo,
+           int ncols, OT* __restrict__ out, int ldo, int ocol0, double* __restrict__ part, int ldp) {
+  residual_body<XT, VT, OT, EQ>(nn, nodeptr, nbr, rowptr, val, apval, dsc, X, F, ldx, lo, ncols, out, ldo, ocol0,
+                                part, ldp);
+}
+
 // w[:, c] = d .* (AA z[:, c]) for c in [c0, c0 + ncols); partial |w|^2 in slot 0.
 template <typename XT, typename VT>
-__global__ void __launch_bounds__(kWarps * 32)
-k_spmm_scaled(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
+__device__ __forceinline__ void spmm_body(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
               const int32_t* __restrict__ rowptr, const VT* __restrict__ val, const double* __restrict__ dsc,
               const XT* __restrict__ z, XT* __restrict__ w, int ld, int c0, int ncols, double* __restrict__ part) {
   using A = typename Acc<XT>::T;
@@ -146,26 +156,92 @@ k_spmm_scaled(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __rest
   }
 }
 
-// P1 coupling: tp[v][c] = (B^T z_u)[v][c] - vin[3v+2][c] / d[3v+2].
+template <typename XT, typename VT>
+__global__ void __launch_bounds__(kWarps * 32)
+k_spmm_scaled(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
+              const int32_t* __restrict__ rowptr, const VT* __restrict__ val, const double* __restrict__ dsc,
+              const XT* __restrict__ z, XT* __restrict__ w, int ld, int c0, int ncols, double* __restrict__ part) {
+  spmm_body<XT, VT>(nn, nodeptr, nbr, rowptr, val, dsc, z, w, ld, c0, ncols, part);
+}
+
+// P1 coupling: tp[v][c] = (B^T z_u)[v][c] - vin[3v+2][c] / d[3v+2] (grid-stride over (v, c)).
+template <typename XT, typename VT>
+__device__ __forceinline__ void coupling_body(int nn, const int32_t* __restrict__ nodeptr,
+                                              const int32_t* __restrict__ nbr, const int32_t* __restrict__ rowptr,
+                                              const VT* __restrict__ val, const double* __restrict__ dsc,
+                                              const XT* __restrict__ z, const XT* __restrict__ vin,
+                                              XT* __restrict__ tp, int ld, int c0, int ncols) {
+  using A = typename Acc<XT>::T;
+  const long long total = (long long)nn * ncols;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
+    const int32_t np = nodeptr[v];
+    const int deg = nodeptr[v + 1] - np;
+    const int32_t r2 = rowptr[3 * v] + 6 * deg;
+    A s = 0;
+    for (int k = 0; k < deg; ++k) {
+      const int m = nbr[np + k];
+      s += (A)to_acc(val[r2 + 3 * k]) * (A)z[(size_t)(3 * m) * ld + c] +
+           (A)to_acc(val[r2 + 3 * k + 1]) * (A)z[(size_t)(3 * m + 1) * ld + c];
+    }
+    tp[(size_t)v * ld + c] = (XT)(s - (A)vin[(size_t)(3 * v + 2) * ld + c] / (A)dsc[3 * v + 2]);
+  }
+}
+
 template <typename XT, typename VT>
 __global__ void k_coupling(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
                            const int32_t* __restrict__ rowptr, const VT* __restrict__ val,
                            const double* __restrict__ dsc, const XT* __restrict__ z, const XT* __restrict__ vin,
                            XT* __restrict__ tp, int ld, int c0, int ncols) {
-  using A = typename Acc<XT>::T;
-  const int c = c0 + (int)(threadIdx.x % 32) + 32 * (int)(blockIdx.y);
-  const int v = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  if (v >= nn || c >= c0 + ncols) return;
-  const int32_t np = nodeptr[v];
-  const int deg = nodeptr[v + 1] - np;
-  const int32_t r2 = rowptr[3 * v] + 6 * deg;
-  A s = 0;
-  for (int k = 0; k < deg; ++k) {
-    const int m = nbr[np + k];
-    s += (A)to_acc(val[r2 + 3 * k]) * (A)z[(size_t)(3 * m) * ld + c] +
-         (A)to_acc(val[r2 + 3 * k + 1]) * (A)z[(size_t)(3 * m + 1) * ld + c];
-  }
-  tp[(size_t)v * ld + c] = (XT)(s - (A)vin[(size_t)(3 * v + 2) * ld + c] / (A)dsc[3 * v + 2]);
+  coupling_body<XT, VT>(nn, nodeptr, nbr, rowptr, val, dsc, z, vin, tp, ld, c0, ncols);
+}
+
+// ---- batched variants: instance = blockIdx.z, arguments from the instance table ----
+
+template <typename VT> __device__ __forceinline__ const VT* inst_val(const InstDev& I);
+template <> __device__ __forceinline__ const float* inst_val<float>(const InstDev& I) { return I.val; }
+template <> __device__ __forceinline__ const __nv_bfloat16* inst_val<__nv_bfloat16>(const InstDev& I) {
+  return I.valbf;
+}
+template <typename VT> __device__ __forceinline__ const VT* inst_apval(const InstDev& I);
+template <> __device__ __forceinline__ const float* inst_apval<float>(const InstDev& I) { return I.apval; }
+template <> __device__ __forceinline__ const __nv_bfloat16* inst_apval<__nv_bfloat16>(const InstDev& I) {
+  return I.apvalbf;
+}
+
+// FP32 window residual of the correction system, columns [0, nres) of V_0.
+template <typename VT>
+__global__ void __launch_bounds__(kWarps * 32) kb_residual_lp(const InstDev* __restrict__ tab) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active || I.nres <= 0) return;
+  residual_body<float, VT, float, true>(I.n_nodes, I.nodeptr, I.nbr, I.rowptr, inst_val<VT>(I), inst_apval<VT>(I),
+                                        I.dsc, I.X, I.F, I.ldx, I.lo, I.nres, I.V, I.wcap, 0, I.part, I.wcap);
+}
+
+// FP64 true residual of all N_t steps into the FP32 correction right-hand side.
+__global__ void __launch_bounds__(kWarps * 32) kb_residual_to_f32(const InstDev* __restrict__ tab) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active) return;
+  residual_body<double, double, float, false>(I.n_nodes, I.nodeptr, I.nbr, I.rowptr, I.val64, I.apval64, I.dsc,
+                                              I.X64, I.F64, I.ldx, 1, I.n_t, I.F, I.ldx, 1, I.part, I.wcap);
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kWarps * 32) kb_spmm(const InstDev* __restrict__ tab, int j) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active || I.nf <= 0) return;
+  const size_t vs = (size_t)I.n_dof * I.wcap;
+  spmm_body<float, VT>(I.n_nodes, I.nodeptr, I.nbr, I.rowptr, inst_val<VT>(I), I.dsc, I.Z + j * vs, I.Wv, I.wcap,
+                       I.c0, I.nf, I.part);
+}
+
+__global__ void kb_coupling(const InstDev* __restrict__ tab, int j) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active || I.nf <= 0) return;
+  const size_t vs = (size_t)I.n_dof * I.wcap;
+  coupling_body<float, float>(I.n_nodes, I.nodeptr, I.nbr, I.rowptr, I.val, I.dsc, I.Z + j * vs, I.V + j * vs, I.tp,
+                              I.wcap, I.c0, I.nf);
 }
 
 }  // namespace
@@ -228,7 +304,7 @@ void launch_spmm_scaled<float>(biot_ctx* ctx, const float* z, float* w, int c0, 
 
 template <>
 void launch_coupling<double>(biot_ctx* ctx, const double* z, const double* vin, double* tp, int c0, int ncols) {
-  dim3 grid(div_up(ctx->n_nodes, 8), div_up(ncols, 32));
+  const int grid = std::min(div_up((long long)ctx->n_nodes * ncols, 256), 4096);
   BIOT_LAUNCH((k_coupling<double, double>), grid, 256, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr, ctx->nbr,
               ctx->rowptr, ctx->val, ctx->dsc, z, vin, tp, ctx->wcap, c0, ncols);
 }
@@ -236,9 +312,29 @@ void launch_coupling<double>(biot_ctx* ctx, const double* z, const double* vin, 
 template <>
 void launch_coupling<float>(biot_ctx* ctx, const float* z, const float* vin, float* tp, int c0, int ncols) {
   // the preconditioner's coupling block B^T runs in FP32 in both reduced-precision modes
-  dim3 grid(div_up(ctx->n_nodes, 8), div_up(ncols, 32));
+  const int grid = std::min(div_up((long long)ctx->n_nodes * ncols, 256), 4096);
   BIOT_LAUNCH((k_coupling<float, float>), grid, 256, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr, ctx->nbr,
               ctx->rowptr, ctx->lp.val, ctx->dsc, z, vin, tp, ctx->wcap, c0, ncols);
+}
+
+void launch_batched_residual_lp(const InstDev* tab, int count, bool bf16, cudaStream_t s) {
+  dim3 grid(kRedBlocks, 1, count);
+  if (bf16) BIOT_LAUNCH(kb_residual_lp<__nv_bfloat16>, grid, kWarps * 32, 0, s, tab);
+  else BIOT_LAUNCH(kb_residual_lp<float>, grid, kWarps * 32, 0, s, tab);
+}
+
+void launch_batched_residual_to_f32(const InstDev* tab, int count, cudaStream_t s) {
+  BIOT_LAUNCH(kb_residual_to_f32, dim3(kRedBlocks, 1, count), kWarps * 32, 0, s, tab);
+}
+
+void launch_batched_spmm(const InstDev* tab, int count, bool bf16, int j, cudaStream_t s) {
+  dim3 grid(kRedBlocks, 1, count);
+  if (bf16) BIOT_LAUNCH(kb_spmm<__nv_bfloat16>, grid, kWarps * 32, 0, s, tab, j);
+  else BIOT_LAUNCH(kb_spmm<float>, grid, kWarps * 32, 0, s, tab, j);
+}
+
+void launch_batched_coupling(const InstDev* tab, int count, int j, cudaStream_t s) {
+  BIOT_LAUNCH(kb_coupling, dim3(256, 1, count), 256, 0, s, tab, j);
 }
 
 }  // namespace biot
