@@ -265,6 +265,26 @@ biot_status biot_residual_norms_noalloc(int32_t n_nodes, const int32_t* nodeptr,
                                         int32_t lo, int32_t ncols, double* R, int32_t ldr, double* rel,
                                         void* cuda_stream);
 
+/* ---- autotuning ---------------------------------------------------------- */
+
+typedef struct {
+  int32_t variant_u, variant_p;         /* chosen band-solve variant for A and for S */
+  int32_t tma_u, nb_u, threads_u;       /* its shape: TMA-staged?, rows per block, CTA size */
+  int32_t tma_p, nb_p, threads_p;
+  double ms_u, ms_p;                    /* forward + backward solve pair, chosen variant */
+  double ms_u_default, ms_p_default;    /* same with the default variant */
+  int32_t from_cache;                   /* 1 if both choices came from the cache file */
+} biot_tuning;
+
+/* Pick the band triangular-solve kernel variant (register-streamed, or TMA-staged
+ * with 8/16/32-row blocks and 128/256 threads; those whose shared memory fits)
+ * for A and for S by timing a forward + backward solve pair of each candidate on
+ * this context's factors at full window width, in the context's precision.
+ * cache_path (nullable): JSON file of earlier choices keyed by precision, block
+ * size, half-band and window; read first, rewritten with the new choices.
+ * Requires biot_precond_setup. out (nullable) receives the choices and times. */
+biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out);
+
 /* Kernel launches issued by this library since it was loaded (all contexts). */
 int64_t biot_launch_count(void);
 

@@ -47,6 +47,20 @@ class BiotInfo(ctypes.Structure):
     ]
 
 
+class BiotTuning(ctypes.Structure):
+    _fields_ = [
+        ("variant_u", ctypes.c_int32), ("variant_p", ctypes.c_int32),
+        ("tma_u", ctypes.c_int32), ("nb_u", ctypes.c_int32), ("threads_u", ctypes.c_int32),
+        ("tma_p", ctypes.c_int32), ("nb_p", ctypes.c_int32), ("threads_p", ctypes.c_int32),
+        ("ms_u", ctypes.c_double), ("ms_p", ctypes.c_double),
+        ("ms_u_default", ctypes.c_double), ("ms_p_default", ctypes.c_double),
+        ("from_cache", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class BiotLibraryMissing(RuntimeError):
     pass
 
@@ -85,6 +99,7 @@ _SIGNATURES = {
     "biot_timing_read": (ctypes.c_int, [_P, ctypes.c_int32, _D, _I64]),
     "biot_residual_norms_noalloc": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32,
                                                    ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P, _P]),
+    "biot_tune": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(BiotTuning)]),
     "biot_launch_count": (ctypes.c_int64, []),
     "biot_last_error": (ctypes.c_char_p, [_P]),
     "biot_destroy": (None, [_P]),
@@ -276,6 +291,12 @@ def biot_residual_norms_noalloc(n_nodes, nodeptr, nbr, rowptr, val, ap_pp, dscal
     st = lib().biot_residual_norms_noalloc(int(n_nodes), nodeptr, nbr, rowptr, val, ap_pp, dscale, X, F, int(ldx),
                                            int(lo), int(ncols), R, int(ldr), rel, _stream_handle(stream))
     _check(st, None, "biot_residual_norms_noalloc")
+
+
+def biot_tune(ctx, cache_path: Optional[str] = None) -> BiotTuning:
+    out = BiotTuning()
+    _check(lib().biot_tune(ctx, cache_path.encode() if cache_path else None, ctypes.byref(out)), ctx, "biot_tune")
+    return out
 
 
 def biot_launch_count() -> int:

@@ -10,6 +10,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <new>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
 
 namespace biot {
 
@@ -304,6 +308,49 @@ biot_status spacetime_residual(biot_ctx* ctx, double* out) {
 }
 
 bool low_precision(const biot_ctx* ctx) { return ctx->prm.precision != BIOT_FP64; }
+
+std::map<std::string, int> read_tune_cache(const char* path) {
+  std::map<std::string, int> out;
+  if (!path) return out;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    const size_t k0 = line.find("\"key\": \"");
+    const size_t v0 = line.find("\"variant\": ");
+    if (k0 == std::string::npos || v0 == std::string::npos) continue;
+    const size_t ks = k0 + 8, ke = line.find('"', ks);
+    if (ke == std::string::npos) continue;
+    out[line.substr(ks, ke - ks)] = std::atoi(line.c_str() + v0 + 11);
+  }
+  return out;
+}
+
+void write_tune_cache(const char* path, const std::map<std::string, int>& m) {
+  if (!path) return;
+  std::ofstream f(path);
+  f << "{\"band_solve_variants\": [\n";
+  size_t k = 0;
+  for (const auto& kv : m)
+    f << "  {\"key\": \"" << kv.first << "\", \"variant\": " << kv.second << "}" << (++k < m.size() ? "," : "")
+      << "\n";
+  f << "]}\n";
+}
+
+std::string tune_key(bool fp64, int N, int b, int ncols) {
+  std::ostringstream o;
+  o << (fp64 ? "fp64" : "fp32") << ":N" << N << ":b" << b << ":w" << ncols;
+  return o.str();
+}
+
+biot_status device_status(biot_ctx* ctx) {
+  int32_t st = 0;
+  BIOT_CU(ctx, cudaMemcpyAsync(&st, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  if (st != 0) return fail(ctx, BIOT_E_TIMEOUT, "a bounded device wait ran out (band-row bulk copy)");
+  return BIOT_OK;
+}
+
+
 
 biot_status sweep_impl(biot_ctx* ctx, int lo, int hi, double* rel_out) {
   const int ncols = hi - lo + 1;
@@ -629,7 +676,7 @@ biot_status biot_pint_solve(biot_ctx* ctx, double tol, int32_t max_outer, int32_
   }
   if (sweeps_done) *sweeps_done = w;
   if (final_rel_res) BIOT_TRY(spacetime_residual(ctx, final_rel_res));
-  BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  BIOT_TRY(device_status(ctx));
   return result;
 }
 
@@ -756,6 +803,73 @@ biot_status biot_timing_read(biot_ctx* ctx, int32_t kc, double* total_ms, int64_
   }
   *total_ms = sum;
   *launches = (int64_t)ctx->ev_marks[kc].size();
+  return BIOT_OK;
+}
+
+biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_TRY(need_precond(ctx));
+  const bool fp64 = !low_precision(ctx);
+  const int pi = fp64 ? 0 : 1;
+  const int nc = ctx->wcap;
+  const int bu = ctx->band_u, bp = ctx->band_p;
+  const std::string ku = tune_key(fp64, 2 * ctx->n_nodes, bu, nc), kp = tune_key(fp64, ctx->n_nodes, bp, nc);
+  std::map<std::string, int> cache = read_tune_cache(cache_path);
+  biot_tuning res{};
+  res.from_cache = 0;
+  const int def_u = band_variant_default(fp64, bu), def_p = band_variant_default(fp64, bp);
+  // clean inputs for the timing runs
+  const size_t es = fp64 ? 8 : 4;
+  void* vin = fp64 ? (void*)ctx->V : (void*)ctx->lp.V;
+  void* z = fp64 ? (void*)ctx->Z : (void*)ctx->lp.Z;
+  BIOT_CU(ctx, cudaMemsetAsync(vin, 0, es * (size_t)ctx->n_dof * nc, ctx->stream));
+  auto time_pair = [&](bool u, int v) -> float {
+    return fp64 ? time_band_pair<double>(ctx, u, v, (const double*)vin, (double*)z, nc)
+                : time_band_pair<float>(ctx, u, v, (const float*)vin, (float*)z, nc);
+  };
+  bool hit_u = cache.count(ku) && band_variant_ok(cache[ku], fp64, bu);
+  bool hit_p = cache.count(kp) && band_variant_ok(cache[kp], fp64, bp);
+  for (int which = 0; which < 2; ++which) {
+    const bool u = which == 0;
+    const int b = u ? bu : bp;
+    int best = u ? def_u : def_p;
+    float tbest = time_pair(u, best);
+    (u ? res.ms_u_default : res.ms_p_default) = tbest;
+    if (u ? hit_u : hit_p) {
+      best = cache[u ? ku : kp];
+      tbest = time_pair(u, best);
+    } else {
+      for (int v = 0; v < kBandVariantCount; ++v) {
+        if (!band_variant_ok(v, fp64, b) || v == (u ? def_u : def_p)) continue;
+        const float t = time_pair(u, v);
+        if (t < tbest) {
+          tbest = t;
+          best = v;
+        }
+      }
+      cache[u ? ku : kp] = best;
+    }
+    BIOT_CU(ctx, cudaGetLastError());
+    if (u) {
+      ctx->band_var_u[pi] = best;
+      res.variant_u = best;
+      res.ms_u = tbest;
+    } else {
+      ctx->band_var_p[pi] = best;
+      res.variant_p = best;
+      res.ms_p = tbest;
+    }
+  }
+  BIOT_TRY(device_status(ctx));
+  res.from_cache = (hit_u && hit_p) ? 1 : 0;
+  res.tma_u = kBandVariants[res.variant_u].tma;
+  res.nb_u = kBandVariants[res.variant_u].nb;
+  res.threads_u = kBandVariants[res.variant_u].threads;
+  res.tma_p = kBandVariants[res.variant_p].tma;
+  res.nb_p = kBandVariants[res.variant_p].nb;
+  res.threads_p = kBandVariants[res.variant_p].threads;
+  if (!res.from_cache) write_tune_cache(cache_path, cache);
+  if (out) *out = res;
   return BIOT_OK;
 }
 

@@ -330,6 +330,209 @@ __global__ void __launch_bounds__(kSolveThreads) kb_band_solve(const InstDev* __
                                ring_rows(b) - 1);
 }
 
+// ---- TMA-staged variant --------------------------------------------------------
+// The band rows of the next block are copied into shared memory by the bulk-copy
+// engine (cp.async.bulk, completion on an mbarrier) while the current block is
+// processed: two buffers, so the FP pipes never wait on band loads from L2. The
+// band arrays are padded to a multiple of 64 rows, so every copy is one whole,
+// 16-byte aligned block of NB rows. The diagonal-block inverses of NB-row blocks
+// are the NB x NB diagonal sub-blocks of the 64-row inverses (the inverse of a
+// block lower-triangular matrix has the inverted diagonal blocks on its diagonal).
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of *bar for at most ~budget SM cycles; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long budget) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > budget) return false;
+  return true;
+}
+
+constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <typename T, int NB>
+__host__ __device__ inline size_t tma_smem_bytes(int b) {
+  return 64 + 2 * align16((size_t)NB * (b + 1) * sizeof(T)) + (size_t)ring_rows(b) * kCols * sizeof(T) +
+         (size_t)NB * kCols * sizeof(T);
+}
+
+template <int MODE, typename T, int NB, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__ Dinv64, const T* __restrict__ vin,
+                 const double* __restrict__ dsc, T* __restrict__ ty, T* __restrict__ tp, T* __restrict__ z, int ld,
+                 int c0, int ncols, int ring_mask, int32_t* __restrict__ err) {
+  constexpr bool kFwd = MODE <= FWD_P_FROM_V;
+  constexpr int KS = THREADS / NB;  // lanes sharing one row
+  static_assert(THREADS % NB == 0 && KS <= 32 && (KS & (KS - 1)) == 0, "bad split");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int W = b + 1;
+  const size_t bufb = align16((size_t)NB * W * sizeof(T));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  T* buf[2] = {reinterpret_cast<T*>(smem_raw + 64), reinterpret_cast<T*>(smem_raw + 64 + bufb)};
+  T* ring = reinterpret_cast<T*>(smem_raw + 64 + 2 * bufb);
+  T* tb = ring + (size_t)(ring_mask + 1) * kCols;
+  const int cbase = c0 + blockIdx.x * kCols;
+  const int ncl = min(kCols, c0 + ncols - cbase);
+  const int t = threadIdx.x;
+  const int r = t / KS, part = t % KS;
+  const int nblk = (N + NB - 1) / NB;
+  const uint32_t bytes = (uint32_t)((size_t)NB * W * sizeof(T));
+
+  auto read_rhs = [&](int i, int c) -> T {
+    if (MODE == FWD_U_FROM_V) { const int rr = udof(i); return vin[(size_t)rr * ld + c] / (T)dsc[rr]; }
+    if (MODE == FWD_P_FROM_T) return tp[(size_t)i * ld + c];
+    if (MODE == FWD_P_FROM_V) { const int rr = 3 * i + 2; return -vin[(size_t)rr * ld + c] / (T)dsc[rr]; }
+    if (MODE == BWD_U_TO_Z) return ty[(size_t)i * ld + c];
+    return tp[(size_t)i * ld + c];
+  };
+  auto write_out = [&](int i, int c, T y) {
+    if (MODE == FWD_U_FROM_V) ty[(size_t)i * ld + c] = y;
+    else if (MODE == FWD_P_FROM_T || MODE == FWD_P_FROM_V) tp[(size_t)i * ld + c] = y;
+    else if (MODE == BWD_U_TO_Z) z[(size_t)udof(i) * ld + c] = y;
+    else z[(size_t)(3 * i + 2) * ld + c] = y;
+  };
+  auto block_of = [&](int bi) { return kFwd ? bi : (nblk - 1 - bi); };
+  auto issue = [&](int bi) {
+    const int I = block_of(bi);
+    bulk_load(buf[bi & 1], band + (size_t)I * NB * W, bytes, &bar[bi & 1]);
+  };
+
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (t == 0) {
+    issue(0);
+    if (nblk > 1) issue(1);
+  }
+  T rhs_next[kCols];
+  {
+    const int i = block_of(0) * NB + r;
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) rhs_next[c] = (part == 0 && i < N && c < ncl) ? read_rhs(i, cbase + c) : T(0);
+  }
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int I = block_of(bi);
+    const int i0 = I * NB;
+    const int i = i0 + r;
+    T rhs[kCols];
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) rhs[c] = rhs_next[c];
+    if (bi + 1 < nblk) {
+      const int in = block_of(bi + 1) * NB + r;
+#pragma unroll
+      for (int c = 0; c < kCols; ++c)
+        rhs_next[c] = (part == 0 && in < N && c < ncl) ? read_rhs(in, cbase + c) : T(0);
+    }
+    // band rows of this block: wait for the bulk copy (bounded)
+    const bool ok = mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), kWaitBudget);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicExch(err, 1);
+        // let copies still in flight land before the CTA's shared memory is released
+        mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), kWaitBudget);
+        if (bi + 1 < nblk) mbar_wait_bounded(&bar[(bi + 1) & 1], (uint32_t)(((bi + 1) >> 1) & 1), kWaitBudget);
+      }
+      __syncthreads();
+      return;
+    }
+    const T* rows = buf[bi & 1];
+    T acc[kCols];
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) acc[c] = T(0);
+    if (i < N) {
+      const T* Lrow = rows + (size_t)r * W;
+      int qs, qe;
+      if (kFwd) {
+        qs = max(0, b - i);
+        qe = b - r;
+      } else {
+        qs = NB - r;
+        qe = min(b, N - 1 - i) + 1;
+      }
+#pragma unroll 4
+      for (int q = qs + part; q < qe; q += KS) {
+        const T l = Lrow[q];
+        const int j = kFwd ? (i - b + q) : (i + q);
+        const T* yr = ring + (size_t)(j & ring_mask) * kCols;
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) acc[c] = fma(l, yr[c], acc[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kCols; ++c)
+#pragma unroll
+      for (int off = 1; off < KS; off <<= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+    if (part == 0)
+#pragma unroll
+      for (int c = 0; c < kCols; ++c) tb[r * kCols + c] = (i < N) ? rhs[c] - acc[c] : T(0);
+    __syncthreads();
+    // buffer bi & 1 is free again: prefetch block bi + 2 into it
+    if (t == 0 && bi + 2 < nblk) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(bi + 2);
+    }
+    // diagonal block: NB x NB sub-block of the 64-row inverse
+    const int I64 = i0 / 64, o = i0 % 64;
+    const T* D = Dinv64 + (size_t)I64 * 64 * 64;
+    T y[kCols];
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) y[c] = T(0);
+    if (kFwd) {
+      for (int k = part; k <= r; k += KS) {
+        const T dv = D[(o + r) * 64 + o + k];
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) y[c] = fma(dv, tb[k * kCols + c], y[c]);
+      }
+    } else {
+      for (int k = r + part; k < NB; k += KS) {
+        const T dv = D[(o + k) * 64 + o + r];
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) y[c] = fma(dv, tb[k * kCols + c], y[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kCols; ++c)
+#pragma unroll
+      for (int off = 1; off < KS; off <<= 1) y[c] += __shfl_xor_sync(0xffffffffu, y[c], off);
+    if (part == 0 && i < N) {
+#pragma unroll
+      for (int c = 0; c < kCols; ++c) {
+        ring[(size_t)(i & ring_mask) * kCols + c] = y[c];
+        if (c < ncl) write_out(i, cbase + c, y[c]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
     dst[k] = (float)src[k];
@@ -359,7 +562,8 @@ biot_status band_setup(biot_ctx* ctx, int kind) {
   const int nn = ctx->n_nodes;
   const int bu = ctx->band_u, bp = ctx->band_p;
   if (bu + kNB > 8192) return fail(ctx, BIOT_E_INVALID, "mesh too large for the band solver (half-band %d)", bu);
-  const size_t su = (size_t)2 * nn * (bu + 1), sp = (size_t)nn * (bp + 1);
+  // band rows padded to a multiple of 64 (whole-block bulk copies), zero beyond N
+  const size_t su = (size_t)div_up(2 * nn, 64) * 64 * (bu + 1), sp = (size_t)div_up(nn, 64) * 64 * (bp + 1);
   if (!ctx->Lu) {
     BIOT_TRY(dalloc(ctx, (void**)&ctx->Lu, sizeof(double) * su));
     BIOT_TRY(dalloc(ctx, (void**)&ctx->Uu, sizeof(double) * su));
@@ -372,12 +576,14 @@ biot_status band_setup(biot_ctx* ctx, int kind) {
   cudaStream_t s = ctx->stream;
   BIOT_CU(ctx, cudaMemsetAsync(ctx->Lu, 0, sizeof(double) * su, s));
   BIOT_CU(ctx, cudaMemsetAsync(ctx->Lp, 0, sizeof(double) * sp, s));
+  BIOT_CU(ctx, cudaMemsetAsync(ctx->Uu, 0, sizeof(double) * su, s));
+  BIOT_CU(ctx, cudaMemsetAsync(ctx->Up, 0, sizeof(double) * sp, s));
   BIOT_LAUNCH(k_band_extract_u, div_up(2 * nn, 256), 256, 0, s, nn, bu, ctx->rowptr, ctx->col, ctx->val, ctx->Lu);
   BIOT_LAUNCH(k_band_extract_p, div_up(nn, 256), 256, 0, s, nn, bp, ctx->rowptr, ctx->col, ctx->val, ctx->Lp);
   BIOT_TRY(band_cholesky(ctx, 2 * nn, bu, ctx->Lu));
   BIOT_TRY(band_cholesky(ctx, nn, bp, ctx->Lp));
-  BIOT_LAUNCH(k_band_transpose, div_up((long long)su, 256), 256, 0, s, 2 * nn, bu, ctx->Lu, ctx->Uu);
-  BIOT_LAUNCH(k_band_transpose, div_up((long long)sp, 256), 256, 0, s, nn, bp, ctx->Lp, ctx->Up);
+  BIOT_LAUNCH(k_band_transpose, div_up((long long)2 * nn * (bu + 1), 256), 256, 0, s, 2 * nn, bu, ctx->Lu, ctx->Uu);
+  BIOT_LAUNCH(k_band_transpose, div_up((long long)nn * (bp + 1), 256), 256, 0, s, nn, bp, ctx->Lp, ctx->Up);
   BIOT_LAUNCH(k_diag_inverse, div_up(2 * nn, kNB), 256, 0, s, 2 * nn, bu, ctx->Lu, ctx->Du);
   BIOT_LAUNCH(k_diag_inverse, div_up(nn, kNB), 256, 0, s, nn, bp, ctx->Lp, ctx->Dp);
   if (ctx->prm.precision != BIOT_FP64) {
@@ -400,6 +606,10 @@ biot_status band_setup(biot_ctx* ctx, int kind) {
     BIOT_LAUNCH(k_to_f32, g, 256, 0, s, ctx->Dp, ctx->lp.Dp, dp);
   }
   BIOT_CU(ctx, cudaGetLastError());
+  for (int pi = 0; pi < 2; ++pi) {
+    ctx->band_var_u[pi] = band_variant_default(pi == 0, bu);
+    ctx->band_var_p[pi] = band_variant_default(pi == 0, bp);
+  }
   ctx->precond = kind;
   return BIOT_OK;
 }
@@ -426,9 +636,24 @@ template <> struct BandBufs<float> {
   static const float* Dp(biot_ctx* c) { return c->lp.Dp; }
 };
 
+template <int MODE, typename T, int NB, int THREADS>
+static void launch_tma(biot_ctx* ctx, int N, int b, const T* band, const T* Dinv, const T* vin, T* z, int c0,
+                       int ncols) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_band_solve_tma<MODE, T, NB, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr_set = true;
+  }
+  const int rr = ring_rows(b);
+  const size_t smem = tma_smem_bytes<T, NB>(b);
+  BIOT_LAUNCH((k_band_solve_tma<MODE, T, NB, THREADS>), div_up(ncols, kCols), THREADS, smem, ctx->stream, N, b, band, Dinv, vin, ctx->dsc, BandBufs<T>::tu(ctx), BandBufs<T>::tp(ctx), z, ctx->wcap,
+              c0, ncols, rr - 1, ctx->status);
+}
+
 template <int MODE, typename T>
-static void solve(biot_ctx* ctx, int N, int b, const T* band, const T* Dinv, const T* vin, T* z, int c0, int ncols) {
-  KTimer tm(ctx, BIOT_KC_BAND_SOLVE);
+static void launch_legacy(biot_ctx* ctx, int N, int b, const T* band, const T* Dinv, const T* vin, T* z, int c0,
+                          int ncols) {
   const int rr = ring_rows(b);
   const size_t smem = sizeof(T) * ((size_t)rr * kCols + kNB * kCols);
   static bool attr_set = false;
@@ -440,20 +665,96 @@ static void solve(biot_ctx* ctx, int N, int b, const T* band, const T* Dinv, con
               ctx->dsc, BandBufs<T>::tu(ctx), BandBufs<T>::tp(ctx), z, ctx->wcap, c0, ncols, rr - 1);
 }
 
+
+// Band-solve variants the tuner chooses from: the register-streaming kernel, and
+// TMA-staged kernels with NB-row blocks and THREADS threads.
+const BandVariant kBandVariants[kBandVariantCount] = {
+    {0, 64, 256}, {1, 16, 128}, {1, 16, 256}, {1, 32, 256}, {1, 8, 128}, {1, 32, 128}};
+
+size_t band_variant_smem(int v, bool fp64, int b) {
+  const BandVariant& V = kBandVariants[v];
+  const size_t es = fp64 ? 8 : 4;
+  if (!V.tma) return es * ((size_t)ring_rows(b) * kCols + kNB * kCols);
+  return 64 + 2 * align16((size_t)V.nb * (b + 1) * es) + (size_t)ring_rows(b) * kCols * es + (size_t)V.nb * kCols * es;
+}
+
+bool band_variant_ok(int v, bool fp64, int b) { return band_variant_smem(v, fp64, b) <= 227 * 1024; }
+
+int band_variant_default(bool fp64, int b) {
+  const int pref = fp64 ? 1 : 3;  // TMA NB=16 x 128 threads (FP64), NB=32 x 256 threads (FP32)
+  if (band_variant_ok(pref, fp64, b)) return pref;
+  for (int v = kBandVariantCount - 1; v > 0; --v)
+    if (band_variant_ok(v, fp64, b)) return v;
+  return 0;
+}
+
+
+template <int MODE, typename T>
+static void solve(biot_ctx* ctx, int variant, int N, int b, const T* band, const T* Dinv, const T* vin, T* z, int c0,
+                  int ncols) {
+  KTimer tm(ctx, BIOT_KC_BAND_SOLVE);
+  switch (variant) {
+    case 1: launch_tma<MODE, T, 16, 128>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
+    case 2: launch_tma<MODE, T, 16, 256>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
+    case 3: launch_tma<MODE, T, 32, 256>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
+    case 4: launch_tma<MODE, T, 8, 128>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
+    case 5: launch_tma<MODE, T, 32, 128>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
+    default: launch_legacy<MODE, T>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
+  }
+}
+
+
 template <typename T>
 void precond_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols) {
   using B = BandBufs<T>;
   const int nn = ctx->n_nodes;
-  solve<FWD_U_FROM_V, T>(ctx, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), vin, z, c0, ncols);
-  solve<BWD_U_TO_Z, T>(ctx, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), vin, z, c0, ncols);
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  const int vu = ctx->band_var_u[pi], vp = ctx->band_var_p[pi];
+  solve<FWD_U_FROM_V, T>(ctx, vu, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), vin, z, c0, ncols);
+  solve<BWD_U_TO_Z, T>(ctx, vu, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), vin, z, c0, ncols);
   if (ctx->precond == BIOT_PRECOND_TRI) {
     launch_coupling<T>(ctx, z, vin, B::tp(ctx), c0, ncols);
-    solve<FWD_P_FROM_T, T>(ctx, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), vin, z, c0, ncols);
+    solve<FWD_P_FROM_T, T>(ctx, vp, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), vin, z, c0, ncols);
   } else {
-    solve<FWD_P_FROM_V, T>(ctx, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), vin, z, c0, ncols);
+    solve<FWD_P_FROM_V, T>(ctx, vp, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), vin, z, c0, ncols);
   }
-  solve<BWD_P_TO_Z, T>(ctx, nn, ctx->band_p, B::Up(ctx), B::Dp(ctx), vin, z, c0, ncols);
+  solve<BWD_P_TO_Z, T>(ctx, vp, nn, ctx->band_p, B::Up(ctx), B::Dp(ctx), vin, z, c0, ncols);
 }
+
+// Time one forward + backward solve pair of block u (A) or p (S) with a variant.
+template <typename T>
+float time_band_pair(biot_ctx* ctx, bool u, int variant, const T* vin, T* z, int ncols) {
+  using B = BandBufs<T>;
+  const int nn = ctx->n_nodes;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bool was = ctx->timing;
+  ctx->timing = false;
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, ctx->stream);
+    if (u) {
+      solve<FWD_U_FROM_V, T>(ctx, variant, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), vin, z, 0, ncols);
+      solve<BWD_U_TO_Z, T>(ctx, variant, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), vin, z, 0, ncols);
+    } else {
+      solve<FWD_P_FROM_V, T>(ctx, variant, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), vin, z, 0, ncols);
+      solve<BWD_P_TO_Z, T>(ctx, variant, nn, ctx->band_p, B::Up(ctx), B::Dp(ctx), vin, z, 0, ncols);
+    }
+    cudaEventRecord(e1, ctx->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, ms);
+  }
+  ctx->timing = was;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+template float time_band_pair<double>(biot_ctx*, bool, int, const double*, double*, int);
+template float time_band_pair<float>(biot_ctx*, bool, int, const float*, float*, int);
 
 template void precond_apply<double>(biot_ctx*, const double*, double*, int, int);
 

@@ -147,6 +147,8 @@ struct biot_ctx {
   double* tp = nullptr;         // [n_nodes][wcap] coupling / forward scratch (p)
   int32_t* status = nullptr;    // device status word (factorisation pivots)
   biot::LowPrec lp;             // reduced-precision sweep buffers (BIOT_FP32 / BIOT_BF16VAL_FP32ACC)
+  int band_var_u[2] = {0, 0};   // band-solve variant for A, [FP64, FP32] (kBandVariants index)
+  int band_var_p[2] = {0, 0};   // same for S
   // params
   biot_params prm{};
   double beta = 0.0;
@@ -215,6 +217,17 @@ template <typename T> void launch_spmm_scaled(biot_ctx* ctx, const T* z, T* w, i
 template <typename T> void launch_coupling(biot_ctx* ctx, const T* z, const T* vin, T* tp, int c0, int ncols);
 
 // ---- band.cu ----
+struct BandVariant {
+  int tma;      // 1: band rows staged in shared memory by bulk copies
+  int nb;       // rows per block
+  int threads;  // CTA size
+};
+constexpr int kBandVariantCount = 6;
+extern const BandVariant kBandVariants[kBandVariantCount];
+size_t band_variant_smem(int v, bool fp64, int b);
+bool band_variant_ok(int v, bool fp64, int b);
+int band_variant_default(bool fp64, int b);
+template <typename T> float time_band_pair(biot_ctx* ctx, bool u, int variant, const T* vin, T* z, int ncols);
 biot_status band_setup(biot_ctx* ctx, int kind);
 // z = P^{-1} (vin ./ d) for columns [c0, c0 + ncols); vin, z in [n_dof][wcap].
 template <typename T> void precond_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols);

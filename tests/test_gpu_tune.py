@@ -1,0 +1,65 @@
+"""Every band-solve variant the tuner can pick gives the same preconditioner.
+
+A cache file naming one variant forces biot_tune to install it; the P^{-1} apply
+is then compared with the oracle's exact block solves (FP64: 1e-9, FP32: 1e-3,
+per field). A tuning run without a cache picks the fastest feasible variant and
+writes the cache.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.solvers import BlockPreconditioner, field_rel_errors
+from oracle.system import build_system
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2310_10430_gb300 import biot  # noqa: E402
+from paper_2310_10430_gb300 import build as B  # noqa: E402
+
+B.build()
+N_VARIANTS = 6
+
+
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-9), ("fp32", 1e-3)])
+@pytest.mark.parametrize("variant", list(range(N_VARIANTS)))
+def test_variant_matches_oracle(tmp_path, precision, bound, variant):
+    case = W.terzaghi_small().with_(n=20, n_t=5, precond="tri")
+    s = build_system(case)
+    P = BlockPreconditioner(s, "tri")
+    vin = np.random.default_rng(variant).standard_normal((5, s.n_dof))
+    with biot.Context(case, precision=precision) as c:
+        info = c.info
+        tag = "fp64" if precision == "fp64" else "fp32"
+        keys = [f"{tag}:N{2 * info.n_nodes}:b{info.band_u}:w{info.window_cap}",
+                f"{tag}:N{info.n_nodes}:b{info.band_p}:w{info.window_cap}"]
+        path = str(tmp_path / "tune.json")
+        with open(path, "w") as f:
+            f.write(json.dumps({"band_solve_variants": []})[:-2] + "\n")
+            f.write("".join(f'  {{"key": "{k}", "variant": {variant}}},\n' for k in keys) + "]}\n")
+        t = biot.biot_tune(c.ctx, path)
+        z = biot.biot_precond_apply(c.ctx, vin)
+    if t.from_cache:
+        assert t.variant_u == variant and t.variant_p == variant
+    for k in range(vin.shape[0]):
+        ref = P.apply(vin[k])
+        eu, ep = field_rel_errors(z[k][None].repeat(2, 0), ref[None].repeat(2, 0))
+        assert eu < bound and ep < bound, (variant, eu, ep)
+
+
+def test_tuning_writes_cache(tmp_path):
+    case = W.terzaghi_small().with_(n=24, n_t=8)
+    path = str(tmp_path / "tune.json")
+    with biot.Context(case) as c:
+        t = biot.biot_tune(c.ctx, path)
+    assert os.path.exists(path) and t.from_cache == 0
+    assert 0 <= t.variant_u < N_VARIANTS and t.ms_u <= t.ms_u_default * 1.05 + 1e-3
+    txt = open(path).read()
+    assert '"variant"' in txt and json.loads(txt)["band_solve_variants"]
