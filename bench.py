@@ -302,6 +302,13 @@ def run_ours(args):
                 "traffic": traffic, "launches": band_n, "avg_launch_ms": band_ms / band_n,
                 "share_of_step": band_ms / ms}
 
+    ctx.close()
+    extras = {}
+    if not args.no_extras:
+        extras["variants"] = {p: sweep_variant(case, p, max(2, args.steps // 2), 2, stream) for p in ("fp32", "bf16")}
+        extras["time_to_solution"] = time_to_solution(workload().with_(n=64, n_t=64, name="terzaghi_64x64_nt64"),
+                                                      stream)
+        extras["batched"] = batched_vs_sequential(stream)
     out = None
     if rank == 0:
         cpu = cpu_baseline_subprocess(args.cpu_budget) if (world == 1 and not args.no_cpu) else None
@@ -319,12 +326,119 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "tuning": tuning,
         }
+        out.update(extras)
         print(json.dumps(out))
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return out
+
+
+# ---------------------------------------------------------------------------
+# secondary measurements: reduced-precision sweeps, time to solution, batching
+# ---------------------------------------------------------------------------
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz
+
+
+def sweep_variant(case, precision, steps, warmup, stream):
+    """Time reduced-precision sweeps over all N_t steps at the bench workload (FP64 true
+    residual, FP32 FGMRES cycle on the correction, FP64 update); returns ms per sweep
+    and the band-solve roofline in FP32."""
+    import torch
+    from paper_2310_10430_gb300 import biot
+    with biot.Context(case, stream=stream, precision=precision) as c:
+        info = c.info
+        tuning = biot.biot_tune(c.ctx, None).as_dict()
+        for _ in range(warmup):
+            biot.biot_sweep(c.ctx, 1, case.n_t, want_rel=False)
+        torch.cuda.synchronize()
+        biot.biot_timing_enable(c.ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            biot.biot_sweep(c.ctx, 1, case.n_t, want_rel=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        band_ms, band_n = biot.biot_timing_read(c.ctx, biot.BIOT_KC_BAND_SOLVE)
+        biot.biot_timing_enable(c.ctx, False)
+        ms = e0.elapsed_time(e1) / steps
+        fl, per = band_solve_flops(info, case.n_t, case.precond)
+        ach = fl / per / (band_ms / band_n / 1e3) / 1e12
+        return {"ms_per_step": ms, "value": case.n_dof * case.n_t / (ms / 1e3), "unit": UNIT,
+                "band_solve": {"achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "bound": "alu",
+                               "frac": ach / FP32_PEAK_TFLOPS, "share_of_step": band_ms / steps / ms},
+                "tuning": {k: tuning[k] for k in ("variant_u", "variant_p", "nb_u", "threads_u", "tma_u")}}
+
+
+def time_to_solution(case, stream):
+    """Wall time of complete solves (setup excluded) to the same FP64 residual
+    tolerance 1e-10: plain FP64 PinT, and the FP32 / BF16-value sweeps with the FP64
+    residual and update (refinement per sweep), each checked against a FP64 solve
+    converged to 1e-13."""
+    import numpy as np
+    import torch
+    from paper_2310_10430_gb300 import biot
+    with biot.Context(case, stream=stream) as c:
+        biot.biot_pint_solve(c.ctx, 1e-13, 100000)
+        ref = biot.biot_get_state(c.ctx, 1, case.n_t)
+    out = {"workload": f"{case.name}: n={case.n}, N_t={case.n_t}, P2, setup (assembly, factorisation) excluded"}
+    for prec in ("fp64", "fp32", "bf16"):
+        with biot.Context(case, stream=stream, precision=prec) as c:
+            biot.biot_tune(c.ctx, None)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-10, 100000, allow_not_converged=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            X = biot.biot_get_state(c.ctx, 1, case.n_t)
+        eu = float(np.linalg.norm(X[:, 0::3] - ref[:, 0::3]) ** 2 + np.linalg.norm(X[:, 1::3] - ref[:, 1::3]) ** 2) ** 0.5
+        eu /= float(np.linalg.norm(ref[:, 0::3]) ** 2 + np.linalg.norm(ref[:, 1::3]) ** 2) ** 0.5
+        ep = float(np.linalg.norm(X[:, 2::3] - ref[:, 2::3]) / np.linalg.norm(ref[:, 2::3]))
+        out[prec] = {"seconds": dt, "sweeps": sweeps, "status": biot.STATUS_NAMES[st], "rel_residual": rel,
+                     "rel_err_u": eu, "rel_err_p": ep}
+    return out
+
+
+def batched_vs_sequential(stream, count=16):
+    """Config-4-shaped instances (uneven n, N_t, nu, lognormal kappa sigma 1.5), FP32
+    with FP64 refinement to 1e-10: one batched solve (CUDA graph) vs the same
+    instances solved one after another."""
+    import torch
+    import workloads as W
+    from paper_2310_10430_gb300 import biot
+    cases = []
+    for inst in W.batched_instances(count):
+        n = 32 + 8 * ((inst.n // 8) % 8)   # keep the bench bounded: n in [32, 88]
+        nt = 32 + inst.n_t % 64            # N_t in [32, 95]
+        cases.append(inst.with_(n=n, n_t=nt, kappa=W.lognormal_kappa(n, sigma=1.5, seed=int(inst.nu * 1e6))))
+    ctxs = [biot.Context(c, stream=stream, precision="fp32", precond="tri") for c in cases]
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, sweeps, rels = biot.biot_batch_solve([c.ctx for c in ctxs], 1e-10, 200000, use_graph=True,
+                                                 allow_not_converged=True)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+    finally:
+        for c in ctxs:
+            c.close()
+    ctxs = [biot.Context(c, stream=stream, precision="fp32", precond="tri") for c in cases]
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c in ctxs:
+            biot.biot_pint_solve(c.ctx, 1e-10, 200000, allow_not_converged=True)
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+    finally:
+        for c in ctxs:
+            c.close()
+    units = sum(c.n_dof * c.n_t for c in cases)
+    return {"instances": count, "n_range": [min(c.n for c in cases), max(c.n for c in cases)],
+            "n_t_range": [min(c.n_t for c in cases), max(c.n_t for c in cases)],
+            "dof_x_steps": units, "batched_seconds": t_batch, "sequential_seconds": t_seq,
+            "speedup": t_seq / t_batch, "max_rel_residual": float(max(rels)), "status": biot.STATUS_NAMES[st]}
 
 
 # ---------------------------------------------------------------------------
@@ -363,6 +477,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--cpu-sample", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the reduced-precision, time-to-solution and batched measurements")
     ap.add_argument("--n", type=int, default=None, help="override the mesh size (profiling runs only)")
     ap.add_argument("--nt", type=int, default=None, help="override N_t (profiling runs only)")
     args = ap.parse_args()

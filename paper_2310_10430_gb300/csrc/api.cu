@@ -140,14 +140,6 @@ __global__ void k_cvt_bf16(const double* __restrict__ src, __nv_bfloat16* __rest
     dst[k] = __double2bfloat16(src[k]);
 }
 
-// X[r][n] += d[r][n] for n = 1..n_t (FP64 refinement update with the FP32 correction).
-__global__ void k_add_correction(double* __restrict__ X, const float* __restrict__ D, int nrows, int ldx, int n_t) {
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)nrows * n_t) return;
-  const int r = (int)(idx / n_t), n = 1 + (int)(idx % n_t);
-  X[(size_t)r * ldx + n] += (double)D[(size_t)r * ldx + n];
-}
-
 // |D^{-1/2} f_ST|^2 contributions per step n (f_ST = f^n, plus A' x0 for n = 1).
 __global__ void k_fst_norms(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
                             const int32_t* __restrict__ rowptr, const double* __restrict__ val,
@@ -231,7 +223,7 @@ biot_status residual_window(biot_ctx* ctx, int lo, int ncols, double* rel_host) 
   return BIOT_OK;
 }
 
-// Reduced-precision window residual of the correction system (into lp.V) and relative norms.
+// Reduced-precision sweep: FP64 true residual of the window into the FP32 lp.V, FP64 relative norms.
 biot_status residual_window_lp(biot_ctx* ctx, int lo, int ncols, double* rel_host) {
   launch_residual_lp(ctx, lo, ncols);
   reduce_partials(ctx, 2, ncols, ctx->colscal + CS_RR * ctx->wcap, ctx->wcap, 0);
@@ -251,27 +243,6 @@ biot_status residual_window_lp(biot_ctx* ctx, int lo, int ncols, double* rel_hos
 
 // |D^{-1/2} f_ST|^2 summed over all steps.
 biot_status fst_norm2(biot_ctx* ctx, double* out);
-
-// FP64 true residual of every step: rounded into lp.F (the correction right-hand side),
-// lp.X cleared; *rr2 = |D^{-1/2}(F - calA X)|^2.
-biot_status form_correction(biot_ctx* ctx, double* rr2) {
-  double num = 0.0;
-  std::vector<double> rb(ctx->wcap);
-  for (int lo = 1; lo <= ctx->n_t; lo += ctx->wcap) {
-    const int nc = std::min(ctx->wcap, ctx->n_t - lo + 1);
-    launch_residual_to_f32(ctx, lo, nc);
-    reduce_partials(ctx, 1, nc, ctx->colscal + CS_RR * ctx->wcap, ctx->wcap, 0);
-    BIOT_CU(ctx, cudaMemcpyAsync(rb.data(), ctx->colscal + CS_RR * ctx->wcap, sizeof(double) * nc,
-                                 cudaMemcpyDeviceToHost, ctx->stream));
-    BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int c = 0; c < nc; ++c) num += rb[c];
-  }
-  BIOT_CU(ctx, cudaMemsetAsync(ctx->lp.X, 0, sizeof(float) * (size_t)ctx->n_dof * ctx->ldx, ctx->stream));
-  // column 0 of the correction right-hand side is unused
-  ctx->lp.correction_ready = true;
-  *rr2 = num;
-  return BIOT_OK;
-}
 
 biot_status fst_norm2(biot_ctx* ctx, double* out) {
   double den = 0.0;
@@ -355,10 +326,6 @@ biot_status device_status(biot_ctx* ctx) {
 biot_status sweep_impl(biot_ctx* ctx, int lo, int hi, double* rel_out) {
   const int ncols = hi - lo + 1;
   if (low_precision(ctx)) {
-    if (!ctx->lp.correction_ready) {
-      double rr2 = 0.0;
-      BIOT_TRY(form_correction(ctx, &rr2));
-    }
     BIOT_TRY(residual_window_lp(ctx, lo, ncols, rel_out));
     return fgmres_cycle<float>(ctx, lo, 0, ncols);
   }
@@ -366,10 +333,11 @@ biot_status sweep_impl(biot_ctx* ctx, int lo, int hi, double* rel_out) {
   return fgmres_cycle<double>(ctx, lo, 0, ncols);
 }
 
-// Tol-schedule PinT solve (Alg. 3 as snapshot sweeps, reading A5) in the working
-// precision of T on the state X (FP64) or on the correction d (FP32). A step that
-// stays active for stall_cap sweeps retires as it is (used by the FP32 correction
-// solves, whose attainable residual is bounded by FP32 rounding).
+// Tol-schedule PinT solve (Alg. 3 as snapshot sweeps, reading A5). T is the Krylov
+// precision: double (plain FP64), or float (the cycle runs in FP32 on the correction
+// of the FP64 residual and is added to the FP64 state). The residual and the
+// retirement test are FP64 in both. A step active for stall_cap sweeps (0: never)
+// retires as it is.
 template <typename T>
 biot_status tol_schedule(biot_ctx* ctx, double tol, int max_sweeps, int stall_cap, int* sweeps, bool* converged) {
   const int n_t = ctx->n_t;
@@ -424,8 +392,6 @@ biot_status alloc_time_buffers(biot_ctx* ctx) {
     return BIOT_OK;
   }
   LowPrec& L = ctx->lp;
-  BIOT_TRY(dalloc(ctx, (void**)&L.X, sizeof(float) * nd * ld));
-  BIOT_TRY(dalloc(ctx, (void**)&L.F, sizeof(float) * nd * ld));
   BIOT_TRY(dalloc(ctx, (void**)&L.V, sizeof(float) * nd * wc * (ctx->n_iter + 1)));
   BIOT_TRY(dalloc(ctx, (void**)&L.Z, sizeof(float) * nd * wc * ctx->n_iter));
   BIOT_TRY(dalloc(ctx, (void**)&L.Wv, sizeof(float) * nd * wc));
@@ -444,7 +410,7 @@ void release_time_buffers(biot_ctx* ctx) {
   void** bufs[] = {(void**)&ctx->X,     (void**)&ctx->F,       (void**)&ctx->V,      (void**)&ctx->Z,
                    (void**)&ctx->Wv,    (void**)&ctx->part,    (void**)&ctx->colscal, (void**)&ctx->H,
                    (void**)&ctx->hvec,  (void**)&ctx->kcol,    (void**)&ctx->tu,     (void**)&ctx->tp,
-                   (void**)&ctx->lp.X,  (void**)&ctx->lp.F,    (void**)&ctx->lp.V,   (void**)&ctx->lp.Z,
+                   (void**)&ctx->lp.V,   (void**)&ctx->lp.Z,
                    (void**)&ctx->lp.Wv, (void**)&ctx->lp.tu,   (void**)&ctx->lp.tp,  (void**)&ctx->lp.val,
                    (void**)&ctx->lp.apval, (void**)&ctx->lp.val_bf16, (void**)&ctx->lp.apval_bf16};
   for (void** b : bufs) {
@@ -490,6 +456,7 @@ biot_status copy_in_steps(biot_ctx* ctx, const double* host, int nc, const doubl
 }  // namespace
 
 biot_status fst_norm2_ctx(biot_ctx* ctx, double* out) { return fst_norm2(ctx, out); }
+biot_status spacetime_residual_ctx(biot_ctx* ctx, double* out) { return spacetime_residual(ctx, out); }
 
 }  // namespace biot
 
@@ -579,7 +546,6 @@ biot_status biot_assemble(biot_ctx* ctx, const biot_params* p) {
       BIOT_LAUNCH(k_cvt_bf16, 256, 256, 0, ctx->stream, ctx->apval, ctx->lp.apval_bf16, (size_t)ctx->n_pairs);
     }
     BIOT_CU(ctx, cudaGetLastError());
-    ctx->lp.correction_ready = false;
   }
   BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->assembled = true;
@@ -618,44 +584,12 @@ biot_status biot_pint_solve(biot_ctx* ctx, double tol, int32_t max_outer, int32_
   if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
   BIOT_TRY(need_precond(ctx));
   if (max_outer < 1) return fail(ctx, BIOT_E_INVALID, "max_outer must be >= 1");
-  if ((ctx->prm.schedule == BIOT_SCHED_TOL || low_precision(ctx)) && !(tol >= 0.0))
+  if (ctx->prm.schedule == BIOT_SCHED_TOL && !(tol >= 0.0))
     return fail(ctx, BIOT_E_INVALID, "tol must be >= 0");
   const int n_t = ctx->n_t;
   int w = 0;
   biot_status result = BIOT_OK;
-  if (low_precision(ctx)) {
-    // FP64 iterative refinement on the space-time system: true residual in FP64,
-    // correction d from the reduced-precision PinT sweep, x <- x + d.
-    const double tol_inner = 1e-5;
-    const int stall_cap = 25;
-    double fst2 = 0.0, prev = INFINITY;
-    BIOT_TRY(fst_norm2(ctx, &fst2));
-    for (int round = 0;; ++round) {
-      double rr2 = 0.0;
-      BIOT_TRY(form_correction(ctx, &rr2));
-      const double rel = fst2 > 0.0 ? std::sqrt(rr2 / fst2) : std::sqrt(rr2);
-      if (!std::isfinite(rel)) return fail(ctx, BIOT_E_DIVERGED, "non-finite FP64 residual in refinement");
-      if (rel <= tol) break;
-      if (w >= max_outer) {
-        result = fail(ctx, BIOT_E_NOT_CONVERGED, "refinement: residual %.3g after %d sweeps", rel, w);
-        break;
-      }
-      if (round > 0 && !(rel < 0.5 * prev)) {
-        result = fail(ctx, BIOT_E_NOT_CONVERGED, "refinement stagnated at residual %.3g (round %d)", rel, round);
-        break;
-      }
-      prev = rel;
-      int sw = 0;
-      bool conv = false;
-      BIOT_TRY(tol_schedule<float>(ctx, tol_inner, max_outer - w, stall_cap, &sw, &conv));
-      w += sw;
-      const long long tot = (long long)ctx->n_dof * n_t;
-      BIOT_LAUNCH(k_add_correction, div_up(tot, 256), 256, 0, ctx->stream, ctx->X, ctx->lp.X, ctx->n_dof, ctx->ldx,
-                  n_t);
-      BIOT_CU(ctx, cudaGetLastError());
-      ctx->lp.correction_ready = false;
-    }
-  } else if (ctx->prm.schedule == BIOT_SCHED_PAPER) {
+  if (ctx->prm.schedule == BIOT_SCHED_PAPER) {
     const int M = ctx->prm.window > 0 ? ctx->prm.window : n_t;
     if (M > ctx->wcap) return fail(ctx, BIOT_E_INVALID, "paper schedule needs window <= %d", ctx->wcap);
     const int total = n_t + M - 1;
@@ -671,7 +605,8 @@ biot_status biot_pint_solve(biot_ctx* ctx, double tol, int32_t max_outer, int32_
     if (result == BIOT_OK) w = total;
   } else {
     bool conv = false;
-    BIOT_TRY(tol_schedule<double>(ctx, tol, max_outer, 0, &w, &conv));
+    if (low_precision(ctx)) BIOT_TRY(tol_schedule<float>(ctx, tol, max_outer, 0, &w, &conv));
+    else BIOT_TRY(tol_schedule<double>(ctx, tol, max_outer, 0, &w, &conv));
     if (!conv) result = fail(ctx, BIOT_E_NOT_CONVERGED, "tolerance %.3g not met after %d sweeps", tol, max_outer);
   }
   if (sweeps_done) *sweeps_done = w;
@@ -700,7 +635,6 @@ biot_status biot_set_state(biot_ctx* ctx, int32_t lo, int32_t hi, const double* 
   if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
   BIOT_TRY(need_assembled(ctx));
   if (!host || lo < 0 || hi > ctx->n_t || lo > hi) return fail(ctx, BIOT_E_INVALID, "bad state range");
-  ctx->lp.correction_ready = false;
   return copy_in_steps(ctx, host, hi - lo + 1, nullptr, ctx->X, ctx->ldx, lo);
 }
 

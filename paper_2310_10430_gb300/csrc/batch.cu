@@ -1,14 +1,14 @@
 // Batched solve of many independent Biot instances (biot_batch_solve).
 //
 // Instances of uneven mesh size, permeability field and N_t are solved together:
-// every kernel of a sweep (FP32 correction residual, band solves, coupling,
-// AA z, CGS2, Givens, update) processes all instances in one launch, the
-// instance given by blockIdx.z and its buffers and window by a device-resident
-// table. Host decisions (retiring converged steps, moving windows, the FP64
-// refinement test) are taken once per sweep for all instances together; the
-// FGMRES cycle of a sweep has a launch sequence that depends only on n_iter,
-// so it is captured once in a CUDA graph and replayed every sweep after the
-// table is refreshed. There is no persistent kernel and no device-wide wait.
+// every kernel of a sweep (FP64 true residual, FP32 band solves, coupling, AA z,
+// CGS2, Givens, FP64 update) processes all instances in one launch, the instance
+// given by blockIdx.z and its buffers and window by a device-resident table. Host
+// decisions (retiring converged steps, moving windows) are taken once per sweep
+// for all instances together; the FGMRES cycle of a sweep has a launch sequence
+// that depends only on n_iter, so it is captured once in a CUDA graph and
+// replayed every sweep after the table is refreshed. There is no persistent
+// kernel and no device-wide wait.
 #include "common.cuh"
 
 #include <algorithm>
@@ -17,25 +17,6 @@
 
 namespace biot {
 namespace {
-
-__global__ void kb_zero_correction(const InstDev* __restrict__ tab) {
-  const InstDev& I = tab[blockIdx.z];
-  if (!I.active) return;
-  const size_t tot = (size_t)I.n_dof * I.ldx;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < tot; k += (size_t)gridDim.x * blockDim.x)
-    I.X[k] = 0.0f;
-}
-
-__global__ void kb_add_correction(const InstDev* __restrict__ tab) {
-  const InstDev& I = tab[blockIdx.z];
-  if (!I.active) return;
-  const long long tot = (long long)I.n_dof * I.n_t;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / I.n_t), n = 1 + (int)(idx % I.n_t);
-    I.X64w[(size_t)r * I.ldx + n] += (double)I.X[(size_t)r * I.ldx + n];
-  }
-}
 
 // out[z][s][c] = colscal_z[(CS_RR + s) * wcap + c] for s < 2, c < wmax (zeros past the window).
 __global__ void kb_gather(const InstDev* __restrict__ tab, int wmax, int nslot, double* __restrict__ out) {
@@ -48,9 +29,9 @@ __global__ void kb_gather(const InstDev* __restrict__ tab, int wmax, int nslot, 
 }
 
 struct BatchState {
-  int lo = 1, w = 0, lo_since = 0, total = 0;
-  bool done = false, inner_done = false;
-  double fst2 = 0.0, prev = INFINITY, rel = INFINITY;
+  int lo = 1, w = 0;
+  bool done = false;
+  double rel = INFINITY;
   biot_status st = BIOT_OK;
 };
 
@@ -76,8 +57,6 @@ InstDev describe(biot_ctx* c) {
   I.apval = c->lp.apval;
   I.valbf = c->lp.val_bf16;
   I.apvalbf = c->lp.apval_bf16;
-  I.X = c->lp.X;
-  I.F = c->lp.F;
   I.V = c->lp.V;
   I.Z = c->lp.Z;
   I.Wv = c->lp.Wv;
@@ -139,8 +118,6 @@ extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, do
   size_t graph_nodes = 0;
   biot_status result = BIOT_OK;
   std::vector<BatchState> B(count);
-  const double tol_inner = 1e-5;
-  const int stall_cap = 25;
   auto cleanup = [&]() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -166,14 +143,7 @@ extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, do
   BATCH_CU(cudaMalloc(&gat_d, sizeof(double) * count * 2 * max_wcap));
   BATCH_CU(cudaMallocHost(&tab_h, sizeof(InstDev) * count));
   BATCH_CU(cudaMallocHost(&gat_h, sizeof(double) * count * 2 * max_wcap));
-  for (int i = 0; i < count; ++i) {
-    tab_h[i] = describe(ctxs[i]);
-    biot_status st = fst_norm2_ctx(ctxs[i], &B[i].fst2);
-    if (st != BIOT_OK) {
-      cleanup();
-      return st;
-    }
-  }
+  for (int i = 0; i < count; ++i) tab_h[i] = describe(ctxs[i]);
   auto upload = [&]() { return cudaMemcpyAsync(tab_d, tab_h, sizeof(InstDev) * count, cudaMemcpyHostToDevice, s); };
   auto gather = [&](int nslot) -> cudaError_t {
     BIOT_LAUNCH(kb_gather, dim3(div_up(max_wcap, 128), nslot, count), 128, 0, s, tab_d, max_wcap, nslot, gat_d);
@@ -203,108 +173,79 @@ extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, do
     return cudaGraphLaunch(exec, s);
   };
 
-  for (int round = 0;; ++round) {
-    // FP64 residual of every open instance -> FP32 correction right-hand side
-    for (int i = 0; i < count; ++i) tab_h[i].active = B[i].done ? 0 : 1;
-    BATCH_CU(upload());
-    launch_batched_residual_to_f32(tab_d, count, s);
-    batched_refine_reduce(tab_d, count, max_wcap, s);
-    BIOT_LAUNCH(kb_zero_correction, dim3(256, 1, count), 256, 0, s, tab_d);
-    BATCH_CU(cudaGetLastError());
-    BATCH_CU(gather(1));
-    bool any_open = false;
+  // Tol-schedule sweeps of all instances in lock step (reading A5 per instance):
+  // FP64 true residual of every active window, retirement test in FP64, then one
+  // FP32 FGMRES cycle per active step whose correction is added to the FP64 state.
+  for (;;) {
+    bool any = false;
     for (int i = 0; i < count; ++i) {
       BatchState& S = B[i];
+      InstDev& I = tab_h[i];
+      I.active = 0;
+      I.nres = I.nf = 0;
       if (S.done) continue;
-      double rr2 = 0.0;
-      for (int c = 0; c < ctxs[i]->n_t; ++c) rr2 += gat_h[(size_t)i * max_wcap + c];
-      S.rel = S.fst2 > 0.0 ? std::sqrt(rr2 / S.fst2) : std::sqrt(rr2);
-      if (!std::isfinite(S.rel)) {
+      if (S.lo > ctxs[i]->n_t) {
         S.done = true;
-        S.st = BIOT_E_DIVERGED;
-      } else if (S.rel <= tol) {
-        S.done = true;
-      } else if (S.total >= max_outer || (round > 0 && !(S.rel < 0.5 * S.prev))) {
+        continue;
+      }
+      if (S.w >= max_outer) {
         S.done = true;
         S.st = BIOT_E_NOT_CONVERGED;
-      } else {
-        S.prev = S.rel;
-        S.lo = 1;
-        S.w = 0;
-        S.lo_since = 0;
-        S.inner_done = false;
-        any_open = true;
+        continue;
       }
+      ++S.w;
+      const int hi = std::min(std::min(S.w, ctxs[i]->n_t), S.lo + I.wcap - 1);
+      I.active = 1;
+      I.lo = S.lo;
+      I.nres = hi - S.lo + 1;
+      any = true;
     }
-    if (!any_open) break;
-    // inner FP32 PinT solves of all open instances, in lock step
-    for (;;) {
-      bool any = false;
-      for (int i = 0; i < count; ++i) {
-        BatchState& S = B[i];
-        InstDev& I = tab_h[i];
-        I.active = 0;
-        I.nres = I.nf = 0;
-        if (S.done || S.inner_done) continue;
-        if (S.lo > ctxs[i]->n_t || S.total >= max_outer) {
-          S.inner_done = true;
-          continue;
-        }
-        ++S.w;
-        ++S.total;
-        const int hi = std::min(std::min(S.w, ctxs[i]->n_t), S.lo + I.wcap - 1);
-        I.active = 1;
-        I.lo = S.lo;
-        I.nres = hi - S.lo + 1;
-        any = true;
-      }
-      if (!any) break;
-      BATCH_CU(upload());
-      launch_batched_residual_lp(tab_d, count, bf16, s);
-      batched_residual_reduce(tab_d, count, max_wcap, s);
-      BATCH_CU(cudaGetLastError());
-      BATCH_CU(gather(2));
-      for (int i = 0; i < count; ++i) {
-        InstDev& I = tab_h[i];
-        if (!I.active) continue;
-        BatchState& S = B[i];
-        const double* rr = gat_h + ((size_t)i * 2) * max_wcap;
-        const double* bb = rr + max_wcap;
-        int k = 0;
-        while (k < I.nres) {
-          const double r = std::sqrt(rr[k]), q = std::sqrt(bb[k]);
-          const double rel = q > 0.0 ? r / q : (r == 0.0 ? 0.0 : INFINITY);
-          if (!std::isfinite(rel)) {
-            S.st = BIOT_E_DIVERGED;
-            S.done = true;
-            break;
-          }
-          if (rel <= tol_inner || (k == 0 && S.w - S.lo_since >= stall_cap)) ++k;
-          else break;
-        }
-        if (S.done) {
-          I.active = 0;
-          continue;
-        }
-        I.c0 = k;
-        I.nf = I.nres - k;
-        if (k > 0) S.lo_since = S.w;
-        S.lo += k;
-      }
-      BATCH_CU(upload());
-      BATCH_CU(run_cycle());
-    }
-    // x <- x + d for every open instance
-    for (int i = 0; i < count; ++i) tab_h[i].active = B[i].done ? 0 : 1;
+    if (!any) break;
     BATCH_CU(upload());
-    BIOT_LAUNCH(kb_add_correction, dim3(256, 1, count), 256, 0, s, tab_d);
+    launch_batched_residual(tab_d, count, s);
+    batched_residual_reduce(tab_d, count, max_wcap, s);
     BATCH_CU(cudaGetLastError());
+    BATCH_CU(gather(2));
+    for (int i = 0; i < count; ++i) {
+      InstDev& I = tab_h[i];
+      if (!I.active) continue;
+      BatchState& S = B[i];
+      const double* rr = gat_h + ((size_t)i * 2) * max_wcap;
+      const double* bb = rr + max_wcap;
+      int k = 0;
+      while (k < I.nres) {
+        const double r = std::sqrt(rr[k]), q = std::sqrt(bb[k]);
+        const double rel = q > 0.0 ? r / q : (r == 0.0 ? 0.0 : INFINITY);
+        if (!std::isfinite(rel)) {
+          S.st = BIOT_E_DIVERGED;
+          S.done = true;
+          break;
+        }
+        if (rel <= tol) ++k;
+        else break;
+      }
+      if (S.done) {
+        I.active = 0;
+        continue;
+      }
+      I.c0 = k;
+      I.nf = I.nres - k;
+      S.lo += k;
+    }
+    BATCH_CU(upload());
+    BATCH_CU(run_cycle());
   }
   BATCH_CU(cudaStreamSynchronize(s));
   for (int i = 0; i < count; ++i) {
-    ctxs[i]->lp.correction_ready = false;
-    if (sweeps_done) sweeps_done[i] = B[i].total;
-    if (final_rel_res) final_rel_res[i] = B[i].rel;
+    if (final_rel_res) {
+      biot_status st = spacetime_residual_ctx(ctxs[i], &B[i].rel);
+      if (st != BIOT_OK) {
+        cleanup();
+        return st;
+      }
+      final_rel_res[i] = B[i].rel;
+    }
+    if (sweeps_done) sweeps_done[i] = B[i].w;
     if (B[i].st != BIOT_OK && result == BIOT_OK) {
       result = fail(ctxs[i], B[i].st, "biot_batch_solve: instance %d ended with residual %.3g", i, B[i].rel);
       fail(nullptr, B[i].st, "biot_batch_solve: instance %d ended with residual %.3g", i, B[i].rel);

@@ -36,11 +36,10 @@ struct DeviceBuf {
   size_t bytes = 0;
 };
 
-// Buffers of the reduced-precision sweep (FP32 vectors; BF16 or FP32 matrix values):
-// the correction system AA d_n - A' d_{n-1} = r_n of the FP64 iterative refinement.
+// Buffers of the reduced-precision sweep (FP32 Krylov vectors; BF16 or FP32 matrix
+// values): every sweep forms the true residual in FP64, runs the FGMRES cycle in FP32
+// on the correction and adds it to the FP64 state (iterative refinement per sweep).
 struct LowPrec {
-  float* X = nullptr;            // correction iterate d [n_dof][ldx], column 0 zero
-  float* F = nullptr;            // FP64 true residual rounded to FP32 [n_dof][ldx]
   float* V = nullptr;            // (n_iter + 1) x [n_dof][wcap]
   float* Z = nullptr;            // n_iter x [n_dof][wcap]
   float* Wv = nullptr;           // [n_dof][wcap]
@@ -56,7 +55,6 @@ struct LowPrec {
   float* Lp = nullptr;
   float* Up = nullptr;
   float* Dp = nullptr;
-  bool correction_ready = false; // lp.F holds the residual of the current X
 };
 
 // One instance of a batch, as the batched kernels see it (device-resident table).
@@ -78,8 +76,6 @@ struct InstDev {
   const float* apval;
   const __nv_bfloat16* valbf;
   const __nv_bfloat16* apvalbf;
-  float* X;
-  float* F;
   float* V;
   float* Z;
   float* Wv;
@@ -207,9 +203,7 @@ void launch_residual_raw(int n_nodes, const int32_t* nodeptr, const int32_t* nbr
                          const double* val, const double* apval, const double* dsc, const double* X,
                          const double* F, int ldx, int lo, int ncols, double* out, int ldo, double* part, int ldp,
                          cudaStream_t stream);
-// FP64 residual of steps lo.. written unscaled into lp.F (correction right-hand side).
-void launch_residual_to_f32(biot_ctx* ctx, int lo, int ncols);
-// Reduced-precision residual of the correction system into lp.V (equilibrated).
+// FP64 true residual of the window written equilibrated into the FP32 lp.V.
 void launch_residual_lp(biot_ctx* ctx, int lo, int ncols);
 // w = d .* (AA z) for columns [c0, c0 + ncols); partial |w|^2 into slot 0.
 template <typename T> void launch_spmm_scaled(biot_ctx* ctx, const T* z, T* w, int c0, int ncols);
@@ -238,8 +232,7 @@ void reduce_partials(biot_ctx* ctx, int nslots, int ncols, double* out, int ldo,
 template <typename T> biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols);
 
 // ---- batched launches (batch.cu drives them) ----
-void launch_batched_residual_lp(const InstDev* tab, int count, bool bf16, cudaStream_t s);
-void launch_batched_residual_to_f32(const InstDev* tab, int count, cudaStream_t s);
+void launch_batched_residual(const InstDev* tab, int count, cudaStream_t s);
 void launch_batched_spmm(const InstDev* tab, int count, bool bf16, int j, cudaStream_t s);
 void launch_batched_coupling(const InstDev* tab, int count, int j, cudaStream_t s);
 void batched_precond_apply(const InstDev* tab, int count, int j, int max_wcap, int max_band, bool tri,
@@ -247,7 +240,7 @@ void batched_precond_apply(const InstDev* tab, int count, int j, int max_wcap, i
 void batched_fgmres_cycle(const InstDev* tab, int count, int n_iter, int max_wcap, int max_ndof, int max_band,
                           bool bf16, bool tri, cudaStream_t s);
 void batched_residual_reduce(const InstDev* tab, int count, int max_wcap, cudaStream_t s);
-void batched_refine_reduce(const InstDev* tab, int count, int max_wcap, cudaStream_t s);
 biot_status fst_norm2_ctx(biot_ctx* ctx, double* out);
+biot_status spacetime_residual_ctx(biot_ctx* ctx, double* out);
 
 }  // namespace biot

@@ -236,6 +236,31 @@ __global__ void k_update_x(const T* __restrict__ Z, size_t zstride, const double
   update_x_body<T>(Z, zstride, rec, kcol, X, ldx, lo, nrows, ld, c0, ncols);
 }
 
+// Mixed precision: X64[r][lo + c] += sum_{i < k_c} y_i[c] Z_i[r][c], the correction
+// accumulated in FP32 and added to the FP64 state (iterative refinement per sweep).
+__device__ __forceinline__ void update_x_mixed_body(const float* __restrict__ Z, size_t zstride,
+                                                    const double* __restrict__ rec, const int32_t* __restrict__ kcol,
+                                                    double* __restrict__ X, int ldx, int lo, int nrows, int ld,
+                                                    int c0, int ncols) {
+  const long long total = (long long)nrows * ncols;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / ncols), c = c0 + (int)(idx % ncols);
+    const int k = kcol[c];
+    if (k == 0) continue;
+    const double* y = rec + (size_t)c * kRec + kRecY;
+    float acc = 0.f;
+    for (int i = 0; i < k; ++i) acc += (float)y[i] * Z[(size_t)i * zstride + (size_t)r * ld + c];
+    X[(size_t)r * ldx + lo + c] += (double)acc;
+  }
+}
+
+__global__ void k_update_x_mixed(const float* __restrict__ Z, size_t zstride, const double* __restrict__ rec,
+                                 const int32_t* __restrict__ kcol, double* __restrict__ X, int ldx, int lo, int nrows,
+                                 int ld, int c0, int ncols) {
+  update_x_mixed_body(Z, zstride, rec, kcol, X, ldx, lo, nrows, ld, c0, ncols);
+}
+
 // ---- batched variants: instance = blockIdx.z, arguments from the instance table ----
 
 enum RedDst { RD_RES = 0, RD_WN0, RD_H1, RD_H2, RD_WW };
@@ -255,13 +280,6 @@ __global__ void kb_reduce(const InstDev* __restrict__ tab, int dst, int nslots) 
   }
   if (nc <= 0) return;
   reduce_body(I.part, kRedBlocks, nslots, ld, c0, nc, out, ld);
-}
-
-// Full-range reduction of the refinement residual (slot 0 over all N_t steps).
-__global__ void kb_reduce_refine(const InstDev* __restrict__ tab) {
-  const InstDev& I = tab[blockIdx.z];
-  if (!I.active) return;
-  reduce_body(I.part, kRedBlocks, 1, I.wcap, 0, I.n_t, I.colscal + CS_RR * I.wcap, I.wcap);
 }
 
 __global__ void kb_fgmres_init(const InstDev* __restrict__ tab) {
@@ -311,7 +329,7 @@ __global__ void kb_backsolve(const InstDev* __restrict__ tab) {
 __global__ void kb_update_x(const InstDev* __restrict__ tab) {
   const InstDev& I = tab[blockIdx.z];
   if (!I.active || I.nf <= 0) return;
-  update_x_body<float>(I.Z, (size_t)I.n_dof * I.wcap, I.H, I.kcol, I.X, I.ldx, I.lo, I.n_dof, I.wcap, I.c0, I.nf);
+  update_x_mixed_body(I.Z, (size_t)I.n_dof * I.wcap, I.H, I.kcol, I.X64w, I.ldx, I.lo, I.n_dof, I.wcap, I.c0, I.nf);
 }
 
 }  // namespace
@@ -328,13 +346,11 @@ template <> struct KBufs<double> {
   static double* V(biot_ctx* c) { return c->V; }
   static double* Z(biot_ctx* c) { return c->Z; }
   static double* W(biot_ctx* c) { return c->Wv; }
-  static double* X(biot_ctx* c) { return c->X; }
 };
 template <> struct KBufs<float> {
   static float* V(biot_ctx* c) { return c->lp.V; }
   static float* Z(biot_ctx* c) { return c->lp.Z; }
   static float* W(biot_ctx* c) { return c->lp.Wv; }
-  static float* X(biot_ctx* c) { return c->lp.X; }
 };
 
 template <typename T>
@@ -372,8 +388,12 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
       BIOT_LAUNCH(k_scale_cols<T>, eblk, 256, 0, s, Wv, V + (j + 1) * vs, cs + CS_INVH * ld, nd, ld, c0, ncols);
   }
   BIOT_LAUNCH(k_backsolve, cblk, 128, 0, s, ld, c0, ncols, ctx->H, ctx->kcol);
-  BIOT_LAUNCH(k_update_x<T>, eblk, 256, 0, s, Z, vs, ctx->H, ctx->kcol, KBufs<T>::X(ctx), ctx->ldx, lo, nd, ld, c0,
-              ncols);
+  if (sizeof(T) == 8)
+    BIOT_LAUNCH(k_update_x<double>, eblk, 256, 0, s, (const double*)Z, vs, ctx->H, ctx->kcol, ctx->X, ctx->ldx, lo, nd,
+                ld, c0, ncols);
+  else
+    BIOT_LAUNCH(k_update_x_mixed, eblk, 256, 0, s, (const float*)Z, vs, ctx->H, ctx->kcol, ctx->X, ctx->ldx, lo, nd,
+                ld, c0, ncols);
   BIOT_CU(ctx, cudaGetLastError());
   return BIOT_OK;
 }
@@ -410,9 +430,7 @@ void batched_residual_reduce(const InstDev* tab, int count, int max_wcap, cudaSt
   BIOT_LAUNCH(kb_reduce, dim3(div_up(max_wcap, 128), 2, count), 128, 0, s, tab, (int)RD_RES, 2);
 }
 
-void batched_refine_reduce(const InstDev* tab, int count, int max_wcap, cudaStream_t s) {
-  BIOT_LAUNCH(kb_reduce_refine, dim3(div_up(max_wcap, 128), 1, count), 128, 0, s, tab);
-}
+
 template biot_status fgmres_cycle<float>(biot_ctx*, int, int, int);
 
 }  // namespace biot

@@ -210,21 +210,12 @@ template <> __device__ __forceinline__ const __nv_bfloat16* inst_apval<__nv_bflo
   return I.apvalbf;
 }
 
-// FP32 window residual of the correction system, columns [0, nres) of V_0.
-template <typename VT>
-__global__ void __launch_bounds__(kWarps * 32) kb_residual_lp(const InstDev* __restrict__ tab) {
+// True residual in FP64 of the window, columns [0, nres) of the FP32 V_0 (equilibrated).
+__global__ void __launch_bounds__(kWarps * 32) kb_residual(const InstDev* __restrict__ tab) {
   const InstDev& I = tab[blockIdx.z];
   if (!I.active || I.nres <= 0) return;
-  residual_body<float, VT, float, true>(I.n_nodes, I.nodeptr, I.nbr, I.rowptr, inst_val<VT>(I), inst_apval<VT>(I),
-                                        I.dsc, I.X, I.F, I.ldx, I.lo, I.nres, I.V, I.wcap, 0, I.part, I.wcap);
-}
-
-// FP64 true residual of all N_t steps into the FP32 correction right-hand side.
-__global__ void __launch_bounds__(kWarps * 32) kb_residual_to_f32(const InstDev* __restrict__ tab) {
-  const InstDev& I = tab[blockIdx.z];
-  if (!I.active) return;
-  residual_body<double, double, float, false>(I.n_nodes, I.nodeptr, I.nbr, I.rowptr, I.val64, I.apval64, I.dsc,
-                                              I.X64, I.F64, I.ldx, 1, I.n_t, I.F, I.ldx, 1, I.part, I.wcap);
+  residual_body<double, double, float, true>(I.n_nodes, I.nodeptr, I.nbr, I.rowptr, I.val64, I.apval64, I.dsc, I.X64,
+                                             I.F64, I.ldx, I.lo, I.nres, I.V, I.wcap, 0, I.part, I.wcap);
 }
 
 template <typename VT>
@@ -261,26 +252,13 @@ void launch_residual(biot_ctx* ctx, int lo, int ncols, double* out, int ldo) {
               ncols, out, ldo, 0, ctx->part, ctx->wcap);
 }
 
-// FP64 true residual of steps lo..lo+ncols-1 written (not equilibrated) as the FP32
-// right-hand side of the correction system: F32[:, lo + c] = r_{lo+c}.
-void launch_residual_to_f32(biot_ctx* ctx, int lo, int ncols) {
-  KTimer tm(ctx, BIOT_KC_RESIDUAL);
-  BIOT_LAUNCH((k_residual<double, double, float, false>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes,
-              ctx->nodeptr, ctx->nbr, ctx->rowptr, ctx->val, ctx->apval, ctx->dsc, ctx->X, ctx->F, ctx->ldx, lo,
-              ncols, ctx->lp.F, ctx->ldx, lo, ctx->part, ctx->wcap);
-}
-
-// Reduced-precision window residual of the correction system into V_0 (FP32).
+// Reduced-precision sweep: the true residual in FP64, written equilibrated into the
+// FP32 V_0 that starts the FP32 Krylov cycle on the correction.
 void launch_residual_lp(biot_ctx* ctx, int lo, int ncols) {
   KTimer tm(ctx, BIOT_KC_RESIDUAL);
-  if (ctx->prm.precision == BIOT_BF16VAL_FP32ACC)
-    BIOT_LAUNCH((k_residual<float, __nv_bfloat16, float, true>), kRedBlocks, kWarps * 32, 0, ctx->stream,
-                ctx->n_nodes, ctx->nodeptr, ctx->nbr, ctx->rowptr, ctx->lp.val_bf16, ctx->lp.apval_bf16, ctx->dsc,
-                ctx->lp.X, ctx->lp.F, ctx->ldx, lo, ncols, ctx->lp.V, ctx->wcap, 0, ctx->part, ctx->wcap);
-  else
-    BIOT_LAUNCH((k_residual<float, float, float, true>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes,
-                ctx->nodeptr, ctx->nbr, ctx->rowptr, ctx->lp.val, ctx->lp.apval, ctx->dsc, ctx->lp.X, ctx->lp.F,
-                ctx->ldx, lo, ncols, ctx->lp.V, ctx->wcap, 0, ctx->part, ctx->wcap);
+  BIOT_LAUNCH((k_residual<double, double, float, true>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes,
+              ctx->nodeptr, ctx->nbr, ctx->rowptr, ctx->val, ctx->apval, ctx->dsc, ctx->X, ctx->F, ctx->ldx, lo,
+              ncols, ctx->lp.V, ctx->wcap, 0, ctx->part, ctx->wcap);
 }
 
 template <>
@@ -317,14 +295,8 @@ void launch_coupling<float>(biot_ctx* ctx, const float* z, const float* vin, flo
               ctx->rowptr, ctx->lp.val, ctx->dsc, z, vin, tp, ctx->wcap, c0, ncols);
 }
 
-void launch_batched_residual_lp(const InstDev* tab, int count, bool bf16, cudaStream_t s) {
-  dim3 grid(kRedBlocks, 1, count);
-  if (bf16) BIOT_LAUNCH(kb_residual_lp<__nv_bfloat16>, grid, kWarps * 32, 0, s, tab);
-  else BIOT_LAUNCH(kb_residual_lp<float>, grid, kWarps * 32, 0, s, tab);
-}
-
-void launch_batched_residual_to_f32(const InstDev* tab, int count, cudaStream_t s) {
-  BIOT_LAUNCH(kb_residual_to_f32, dim3(kRedBlocks, 1, count), kWarps * 32, 0, s, tab);
+void launch_batched_residual(const InstDev* tab, int count, cudaStream_t s) {
+  BIOT_LAUNCH(kb_residual, dim3(kRedBlocks, 1, count), kWarps * 32, 0, s, tab);
 }
 
 void launch_batched_spmm(const InstDev* tab, int count, bool bf16, int j, cudaStream_t s) {
