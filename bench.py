@@ -127,7 +127,8 @@ def allreduce_max(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -236,7 +237,7 @@ def run_ours(args):
     case = workload()
     stream = torch.cuda.current_stream()
     W_ = case.n_t
-    ctx = biot.Context(case, stream=stream, window=W_)
+    ctx = biot.Context(case, stream=stream, window=W_, precision=args.precision)
     info = ctx.info
     lo, hi = 1, case.n_t
     tuning = biot.biot_tune(ctx.ctx, None).as_dict()
@@ -481,6 +482,8 @@ def main():
                     help="skip the reduced-precision, time-to-solution and batched measurements")
     ap.add_argument("--n", type=int, default=None, help="override the mesh size (profiling runs only)")
     ap.add_argument("--nt", type=int, default=None, help="override N_t (profiling runs only)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"],
+                    help="sweep precision of the timed line (profiling runs; the bench line is fp64)")
     args = ap.parse_args()
     if args.n:
         _SIZE["n"] = args.n

@@ -784,6 +784,7 @@ biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out) {
       cache[u ? ku : kp] = best;
     }
     BIOT_CU(ctx, cudaGetLastError());
+    BIOT_TRY(ensure_dnb(ctx, fp64, u, best));
     if (u) {
       ctx->band_var_u[pi] = best;
       res.variant_u = best;

@@ -345,9 +345,13 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+// One arrival that announces `bytes` of bulk-copy traffic for the current phase.
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
@@ -377,13 +381,26 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(siz
 
 template <typename T, int NB>
 __host__ __device__ inline size_t tma_smem_bytes(int b) {
-  return 64 + 2 * align16((size_t)NB * (b + 1) * sizeof(T)) + (size_t)ring_rows(b) * kCols * sizeof(T) +
-         (size_t)NB * kCols * sizeof(T);
+  return 64 + 2 * align16((size_t)NB * (b + 1) * sizeof(T)) + 2 * align16((size_t)NB * NB * sizeof(T)) +
+         (size_t)ring_rows(b) * kCols * sizeof(T) + (size_t)NB * kCols * sizeof(T);
+}
+
+// Compact inverses of the NB-row diagonal blocks, [block][NB][NB], taken from the
+// 64-row inverses (diagonal sub-blocks).
+template <typename T>
+__global__ void k_extract_dnb(const T* __restrict__ D64, int N, int nb, T* __restrict__ out) {
+  const int nblk = (N + nb - 1) / nb;
+  const long long tot = (long long)nblk * nb * nb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(t / (nb * nb)), rk = (int)(t % (nb * nb)), r = rk / nb, k = rk % nb;
+    const int i0 = I * nb, o = i0 % 64;
+    out[t] = D64[(size_t)(i0 / 64) * 64 * 64 + (size_t)(o + r) * 64 + o + k];
+  }
 }
 
 template <int MODE, typename T, int NB, int THREADS>
 __global__ void __launch_bounds__(THREADS)
-k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__ Dinv64, const T* __restrict__ vin,
+k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__ Dnb, const T* __restrict__ vin,
                  const double* __restrict__ dsc, T* __restrict__ ty, T* __restrict__ tp, T* __restrict__ z, int ld,
                  int c0, int ncols, int ring_mask, int32_t* __restrict__ err) {
   constexpr bool kFwd = MODE <= FWD_P_FROM_V;
@@ -392,9 +409,11 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int W = b + 1;
   const size_t bufb = align16((size_t)NB * W * sizeof(T));
+  constexpr size_t dbufb = align16((size_t)NB * NB * sizeof(T));
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   T* buf[2] = {reinterpret_cast<T*>(smem_raw + 64), reinterpret_cast<T*>(smem_raw + 64 + bufb)};
-  T* ring = reinterpret_cast<T*>(smem_raw + 64 + 2 * bufb);
+  T* dbuf[2] = {reinterpret_cast<T*>(smem_raw + 64 + 2 * bufb), reinterpret_cast<T*>(smem_raw + 64 + 2 * bufb + dbufb)};
+  T* ring = reinterpret_cast<T*>(smem_raw + 64 + 2 * bufb + 2 * dbufb);
   T* tb = ring + (size_t)(ring_mask + 1) * kCols;
   const int cbase = c0 + blockIdx.x * kCols;
   const int ncl = min(kCols, c0 + ncols - cbase);
@@ -402,6 +421,7 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
   const int r = t / KS, part = t % KS;
   const int nblk = (N + NB - 1) / NB;
   const uint32_t bytes = (uint32_t)((size_t)NB * W * sizeof(T));
+  constexpr uint32_t dbytes = (uint32_t)(NB * NB * sizeof(T));
 
   auto read_rhs = [&](int i, int c) -> T {
     if (MODE == FWD_U_FROM_V) { const int rr = udof(i); return vin[(size_t)rr * ld + c] / (T)dsc[rr]; }
@@ -419,7 +439,9 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
   auto block_of = [&](int bi) { return kFwd ? bi : (nblk - 1 - bi); };
   auto issue = [&](int bi) {
     const int I = block_of(bi);
-    bulk_load(buf[bi & 1], band + (size_t)I * NB * W, bytes, &bar[bi & 1]);
+    mbar_expect(&bar[bi & 1], bytes + dbytes);
+    bulk_copy(buf[bi & 1], band + (size_t)I * NB * W, bytes, &bar[bi & 1]);
+    bulk_copy(dbuf[bi & 1], Dnb + (size_t)I * NB * NB, dbytes, &bar[bi & 1]);
   };
 
   if (t == 0) {
@@ -494,26 +516,20 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
 #pragma unroll
       for (int c = 0; c < kCols; ++c) tb[r * kCols + c] = (i < N) ? rhs[c] - acc[c] : T(0);
     __syncthreads();
-    // buffer bi & 1 is free again: prefetch block bi + 2 into it
-    if (t == 0 && bi + 2 < nblk) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(bi + 2);
-    }
-    // diagonal block: NB x NB sub-block of the 64-row inverse
-    const int I64 = i0 / 64, o = i0 % 64;
-    const T* D = Dinv64 + (size_t)I64 * 64 * 64;
+    // diagonal block: its NB x NB inverse arrived with the band rows
+    const T* D = dbuf[bi & 1];
     T y[kCols];
 #pragma unroll
     for (int c = 0; c < kCols; ++c) y[c] = T(0);
     if (kFwd) {
       for (int k = part; k <= r; k += KS) {
-        const T dv = D[(o + r) * 64 + o + k];
+        const T dv = D[r * NB + k];
 #pragma unroll
         for (int c = 0; c < kCols; ++c) y[c] = fma(dv, tb[k * kCols + c], y[c]);
       }
     } else {
       for (int k = r + part; k < NB; k += KS) {
-        const T dv = D[(o + k) * 64 + o + r];
+        const T dv = D[k * NB + r];
 #pragma unroll
         for (int c = 0; c < kCols; ++c) y[c] = fma(dv, tb[k * kCols + c], y[c]);
       }
@@ -530,6 +546,11 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
       }
     }
     __syncthreads();
+    // both buffers of slot bi & 1 are free again: prefetch block bi + 2 into them
+    if (t == 0 && bi + 2 < nblk) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(bi + 2);
+    }
   }
 }
 
@@ -609,6 +630,10 @@ biot_status band_setup(biot_ctx* ctx, int kind) {
   for (int pi = 0; pi < 2; ++pi) {
     ctx->band_var_u[pi] = band_variant_default(pi == 0, bu);
     ctx->band_var_p[pi] = band_variant_default(pi == 0, bp);
+    ctx->dnb_nb_u[pi] = ctx->dnb_nb_p[pi] = 0;  // factors changed: rebuild the compact inverses
+    if (pi == 1 && ctx->prm.precision == BIOT_FP64) continue;
+    BIOT_TRY(ensure_dnb(ctx, pi == 0, true, ctx->band_var_u[pi]));
+    BIOT_TRY(ensure_dnb(ctx, pi == 0, false, ctx->band_var_p[pi]));
   }
   ctx->precond = kind;
   return BIOT_OK;
@@ -624,6 +649,8 @@ template <> struct BandBufs<double> {
   static const double* Lp(biot_ctx* c) { return c->Lp; }
   static const double* Up(biot_ctx* c) { return c->Up; }
   static const double* Dp(biot_ctx* c) { return c->Dp; }
+  static const double* Dnbu(biot_ctx* c) { return (const double*)c->dnb_u[0]; }
+  static const double* Dnbp(biot_ctx* c) { return (const double*)c->dnb_p[0]; }
 };
 template <> struct BandBufs<float> {
   static float* tu(biot_ctx* c) { return c->lp.tu; }
@@ -634,6 +661,8 @@ template <> struct BandBufs<float> {
   static const float* Lp(biot_ctx* c) { return c->lp.Lp; }
   static const float* Up(biot_ctx* c) { return c->lp.Up; }
   static const float* Dp(biot_ctx* c) { return c->lp.Dp; }
+  static const float* Dnbu(biot_ctx* c) { return (const float*)c->dnb_u[1]; }
+  static const float* Dnbp(biot_ctx* c) { return (const float*)c->dnb_p[1]; }
 };
 
 template <int MODE, typename T, int NB, int THREADS>
@@ -690,17 +719,38 @@ int band_variant_default(bool fp64, int b) {
 
 
 template <int MODE, typename T>
-static void solve(biot_ctx* ctx, int variant, int N, int b, const T* band, const T* Dinv, const T* vin, T* z, int c0,
-                  int ncols) {
+static void solve(biot_ctx* ctx, int variant, int N, int b, const T* band, const T* Dinv, const T* Dnb, const T* vin,
+                  T* z, int c0, int ncols) {
   KTimer tm(ctx, BIOT_KC_BAND_SOLVE);
   switch (variant) {
-    case 1: launch_tma<MODE, T, 16, 128>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
-    case 2: launch_tma<MODE, T, 16, 256>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
-    case 3: launch_tma<MODE, T, 32, 256>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
-    case 4: launch_tma<MODE, T, 8, 128>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
-    case 5: launch_tma<MODE, T, 32, 128>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
+    case 1: launch_tma<MODE, T, 16, 128>(ctx, N, b, band, Dnb, vin, z, c0, ncols); break;
+    case 2: launch_tma<MODE, T, 16, 256>(ctx, N, b, band, Dnb, vin, z, c0, ncols); break;
+    case 3: launch_tma<MODE, T, 32, 256>(ctx, N, b, band, Dnb, vin, z, c0, ncols); break;
+    case 4: launch_tma<MODE, T, 8, 128>(ctx, N, b, band, Dnb, vin, z, c0, ncols); break;
+    case 5: launch_tma<MODE, T, 32, 128>(ctx, N, b, band, Dnb, vin, z, c0, ncols); break;
     default: launch_legacy<MODE, T>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
   }
+}
+
+template <typename T>
+static biot_status build_dnb(biot_ctx* ctx, bool u, int nb) {
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  void*& dst = u ? ctx->dnb_u[pi] : ctx->dnb_p[pi];
+  int& have = u ? ctx->dnb_nb_u[pi] : ctx->dnb_nb_p[pi];
+  if (have == nb) return BIOT_OK;
+  const int N = u ? 2 * ctx->n_nodes : ctx->n_nodes;
+  if (!dst) BIOT_TRY(dalloc(ctx, &dst, sizeof(T) * ((size_t)N + 64) * 32));
+  const T* D64 = u ? BandBufs<T>::Du(ctx) : BandBufs<T>::Dp(ctx);
+  BIOT_LAUNCH(k_extract_dnb<T>, 512, 256, 0, ctx->stream, D64, N, nb, (T*)dst);
+  BIOT_CU(ctx, cudaGetLastError());
+  have = nb;
+  return BIOT_OK;
+}
+
+biot_status ensure_dnb(biot_ctx* ctx, bool fp64, bool u, int variant) {
+  if (!kBandVariants[variant].tma) return BIOT_OK;
+  return fp64 ? build_dnb<double>(ctx, u, kBandVariants[variant].nb)
+              : build_dnb<float>(ctx, u, kBandVariants[variant].nb);
 }
 
 
@@ -710,15 +760,15 @@ void precond_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols) {
   const int nn = ctx->n_nodes;
   const int pi = sizeof(T) == 8 ? 0 : 1;
   const int vu = ctx->band_var_u[pi], vp = ctx->band_var_p[pi];
-  solve<FWD_U_FROM_V, T>(ctx, vu, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), vin, z, c0, ncols);
-  solve<BWD_U_TO_Z, T>(ctx, vu, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), vin, z, c0, ncols);
+  solve<FWD_U_FROM_V, T>(ctx, vu, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, c0, ncols);
+  solve<BWD_U_TO_Z, T>(ctx, vu, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, c0, ncols);
   if (ctx->precond == BIOT_PRECOND_TRI) {
     launch_coupling<T>(ctx, z, vin, B::tp(ctx), c0, ncols);
-    solve<FWD_P_FROM_T, T>(ctx, vp, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), vin, z, c0, ncols);
+    solve<FWD_P_FROM_T, T>(ctx, vp, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
   } else {
-    solve<FWD_P_FROM_V, T>(ctx, vp, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), vin, z, c0, ncols);
+    solve<FWD_P_FROM_V, T>(ctx, vp, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
   }
-  solve<BWD_P_TO_Z, T>(ctx, vp, nn, ctx->band_p, B::Up(ctx), B::Dp(ctx), vin, z, c0, ncols);
+  solve<BWD_P_TO_Z, T>(ctx, vp, nn, ctx->band_p, B::Up(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
 }
 
 // Time one forward + backward solve pair of block u (A) or p (S) with a variant.
@@ -726,6 +776,7 @@ template <typename T>
 float time_band_pair(biot_ctx* ctx, bool u, int variant, const T* vin, T* z, int ncols) {
   using B = BandBufs<T>;
   const int nn = ctx->n_nodes;
+  if (ensure_dnb(ctx, sizeof(T) == 8, u, variant) != BIOT_OK) return 1e30f;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -735,11 +786,12 @@ float time_band_pair(biot_ctx* ctx, bool u, int variant, const T* vin, T* z, int
   for (int rep = 0; rep < 3; ++rep) {
     cudaEventRecord(e0, ctx->stream);
     if (u) {
-      solve<FWD_U_FROM_V, T>(ctx, variant, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), vin, z, 0, ncols);
-      solve<BWD_U_TO_Z, T>(ctx, variant, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), vin, z, 0, ncols);
+      solve<FWD_U_FROM_V, T>(ctx, variant, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, 0,
+                             ncols);
+      solve<BWD_U_TO_Z, T>(ctx, variant, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, 0, ncols);
     } else {
-      solve<FWD_P_FROM_V, T>(ctx, variant, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), vin, z, 0, ncols);
-      solve<BWD_P_TO_Z, T>(ctx, variant, nn, ctx->band_p, B::Up(ctx), B::Dp(ctx), vin, z, 0, ncols);
+      solve<FWD_P_FROM_V, T>(ctx, variant, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, 0, ncols);
+      solve<BWD_P_TO_Z, T>(ctx, variant, nn, ctx->band_p, B::Up(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, 0, ncols);
     }
     cudaEventRecord(e1, ctx->stream);
     cudaEventSynchronize(e1);

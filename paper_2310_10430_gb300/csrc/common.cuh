@@ -145,6 +145,10 @@ struct biot_ctx {
   biot::LowPrec lp;             // reduced-precision sweep buffers (BIOT_FP32 / BIOT_BF16VAL_FP32ACC)
   int band_var_u[2] = {0, 0};   // band-solve variant for A, [FP64, FP32] (kBandVariants index)
   int band_var_p[2] = {0, 0};   // same for S
+  void* dnb_u[2] = {nullptr, nullptr};  // compact NB x NB diagonal-block inverses of A, [FP64, FP32]
+  void* dnb_p[2] = {nullptr, nullptr};  // same for S
+  int dnb_nb_u[2] = {0, 0};     // NB they were built for (0: none)
+  int dnb_nb_p[2] = {0, 0};
   // params
   biot_params prm{};
   double beta = 0.0;
@@ -222,6 +226,8 @@ size_t band_variant_smem(int v, bool fp64, int b);
 bool band_variant_ok(int v, bool fp64, int b);
 int band_variant_default(bool fp64, int b);
 template <typename T> float time_band_pair(biot_ctx* ctx, bool u, int variant, const T* vin, T* z, int ncols);
+// Build the compact diagonal-block inverses a TMA variant needs (no-op if present).
+biot_status ensure_dnb(biot_ctx* ctx, bool fp64, bool u, int variant);
 biot_status band_setup(biot_ctx* ctx, int kind);
 // z = P^{-1} (vin ./ d) for columns [c0, c0 + ncols); vin, z in [n_dof][wcap].
 template <typename T> void precond_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols);
