@@ -34,6 +34,10 @@ constexpr int kNB = 64;                         // rows per block of the triangu
 constexpr int kKSplit = kSolveThreads / kNB;    // lanes sharing one row's band product
 constexpr int kCols = 2;                        // time steps (columns) per CTA
 
+// Leading dimension of the band rows: b + 1 entries padded to a multiple of 4, so every
+// row starts on a 16-byte boundary (vector loads, whole-block bulk copies).
+__host__ __device__ constexpr int band_ld(int b) { return (b + 1 + 3) & ~3; }
+
 __global__ void k_band_extract_u(int nn, int bu, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                  const double* __restrict__ val, double* __restrict__ Lb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // u-row 2 v + f
@@ -45,7 +49,7 @@ __global__ void k_band_extract_u(int nn, int bu, const int32_t* __restrict__ row
     if (g == 2) continue;
     const int j = 2 * (c / 3) + g;
     if (j > i || i - j > bu) continue;
-    Lb[(size_t)i * (bu + 1) + (bu - (i - j))] = val[e];
+    Lb[(size_t)i * band_ld(bu) + (bu - (i - j))] = val[e];
   }
 }
 
@@ -59,7 +63,7 @@ __global__ void k_band_extract_p(int nn, int bp, const int32_t* __restrict__ row
     if (c % 3 != 2) continue;
     const int j = c / 3;
     if (j > v || v - j > bp) continue;
-    Lb[(size_t)v * (bp + 1) + (bp - (v - j))] = -val[e];  // S = -AA_pp
+    Lb[(size_t)v * band_ld(bp) + (bp - (v - j))] = -val[e];  // S = -AA_pp
   }
 }
 
@@ -77,7 +81,7 @@ k_chol_panel(int N, int b, int j0, int np, double* __restrict__ Lb, int32_t* __r
   if (t == 0) bad = (*status != 0);
   __syncthreads();
   if (bad) return;
-  const size_t W = (size_t)b + 1;
+  const size_t W = (size_t)band_ld(b);
   for (int jj = 0; jj < np; ++jj) {
     const int j = j0 + jj;
     if (t == 0) {
@@ -114,7 +118,7 @@ __global__ void k_chol_trailing(int N, int b, int j0, int np, double* __restrict
   const int last = min(N - 1, j1 - 1 + b);
   const int m = last - j1 + 1;
   if (m <= 0) return;
-  const size_t W = (size_t)b + 1;
+  const size_t W = (size_t)band_ld(b);
   const long long tri = (long long)m * (m + 1) / 2;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tri; t += (long long)blockDim.x * gridDim.x) {
     int ii = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
@@ -133,7 +137,8 @@ __global__ void k_band_transpose(int N, int b, const double* __restrict__ Lb, do
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)N * (b + 1)) return;
   const int i = (int)(t / (b + 1)), q = (int)(t % (b + 1));
-  Ub[t] = (i + q < N) ? Lb[(size_t)(i + q) * (b + 1) + (b - q)] : 0.0;
+  const size_t ld = (size_t)band_ld(b);
+  Ub[(size_t)i * ld + q] = (i + q < N) ? Lb[(size_t)(i + q) * ld + (b - q)] : 0.0;
 }
 
 enum SolveMode {
@@ -152,7 +157,7 @@ __global__ void k_diag_inverse(int N, int b, const double* __restrict__ Lb, doub
   __shared__ double Ld[kNB][kNB + 1];
   const int I = blockIdx.x, i0 = I * kNB, t = threadIdx.x;
   double* X = Dinv + (size_t)I * kNB * kNB;  // X[r * kNB + k]; column k written and read by thread k only
-  const size_t W = (size_t)b + 1;
+  const size_t W = (size_t)band_ld(b);
   for (int idx = t; idx < kNB * kNB; idx += blockDim.x) {
     const int r = idx / kNB, c = idx % kNB;
     double v = 0.0;
@@ -198,7 +203,7 @@ __device__ __forceinline__ void band_solve_body(int N, int b, const T* __restric
   const int t = threadIdx.x;
   const int r = t / kKSplit, part = t % kKSplit;
   const int nblk = (N + kNB - 1) / kNB;
-  const size_t W = (size_t)b + 1;
+  const size_t W = (size_t)band_ld(b);
 
   auto read_rhs = [&](int i, int c) -> T {
     if (MODE == FWD_U_FROM_V) { const int rr = udof(i); return vin[(size_t)rr * ld + c] / (T)dsc[rr]; }
@@ -381,8 +386,8 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(siz
 
 template <typename T, int NB>
 __host__ __device__ inline size_t tma_smem_bytes(int b) {
-  return 64 + 2 * align16((size_t)NB * (b + 1) * sizeof(T)) + 2 * align16((size_t)NB * NB * sizeof(T)) +
-         (size_t)ring_rows(b) * kCols * sizeof(T) + (size_t)NB * kCols * sizeof(T);
+  return 64 + 2 * align16((size_t)NB * band_ld(b) * sizeof(T)) + 2 * align16((size_t)NB * NB * sizeof(T)) +
+         2 * (size_t)ring_rows(b) * kCols * sizeof(T) + (size_t)NB * kCols * sizeof(T);
 }
 
 // Compact inverses of the NB-row diagonal blocks, [block][NB][NB], taken from the
@@ -398,6 +403,18 @@ __global__ void k_extract_dnb(const T* __restrict__ D64, int N, int nb, T* __res
   }
 }
 
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using V = float4;
+  static constexpr int n = 4;
+  __device__ __forceinline__ static void get(const V& v, float* out) { out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w; }
+};
+template <> struct Vec16<double> {
+  using V = double2;
+  static constexpr int n = 2;
+  __device__ __forceinline__ static void get(const V& v, double* out) { out[0] = v.x; out[1] = v.y; }
+};
+
 template <int MODE, typename T, int NB, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__ Dnb, const T* __restrict__ vin,
@@ -405,22 +422,25 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
                  int c0, int ncols, int ring_mask, int32_t* __restrict__ err) {
   constexpr bool kFwd = MODE <= FWD_P_FROM_V;
   constexpr int KS = THREADS / NB;  // lanes sharing one row
+  constexpr int VQ = Vec16<T>::n;   // band entries per 16-byte load
   static_assert(THREADS % NB == 0 && KS <= 32 && (KS & (KS - 1)) == 0, "bad split");
+  static_assert(kCols == 2, "the ring rows are read as pairs");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int W = b + 1;
-  const size_t bufb = align16((size_t)NB * W * sizeof(T));
+  const int lb = band_ld(b);
+  const int R = ring_mask + 1;   // the ring holds every row twice: slots j mod R and j mod R + R
+  const size_t bufb = align16((size_t)NB * lb * sizeof(T));
   constexpr size_t dbufb = align16((size_t)NB * NB * sizeof(T));
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  T* buf[2] = {reinterpret_cast<T*>(smem_raw + 64), reinterpret_cast<T*>(smem_raw + 64 + bufb)};
-  T* dbuf[2] = {reinterpret_cast<T*>(smem_raw + 64 + 2 * bufb), reinterpret_cast<T*>(smem_raw + 64 + 2 * bufb + dbufb)};
-  T* ring = reinterpret_cast<T*>(smem_raw + 64 + 2 * bufb + 2 * dbufb);
-  T* tb = ring + (size_t)(ring_mask + 1) * kCols;
+  auto buf = [&](int slot) { return reinterpret_cast<T*>(smem_raw + 64 + slot * bufb); };
+  auto dbuf = [&](int slot) { return reinterpret_cast<T*>(smem_raw + 64 + 2 * bufb + slot * dbufb); };
+  T* ring = reinterpret_cast<T*>(smem_raw + 64 + 2 * bufb + 2 * dbufb);  // [2R][kCols]
+  T* tb = ring + (size_t)2 * R * kCols;
   const int cbase = c0 + blockIdx.x * kCols;
   const int ncl = min(kCols, c0 + ncols - cbase);
   const int t = threadIdx.x;
   const int r = t / KS, part = t % KS;
   const int nblk = (N + NB - 1) / NB;
-  const uint32_t bytes = (uint32_t)((size_t)NB * W * sizeof(T));
+  const uint32_t bytes = (uint32_t)((size_t)NB * lb * sizeof(T));
   constexpr uint32_t dbytes = (uint32_t)(NB * NB * sizeof(T));
 
   auto read_rhs = [&](int i, int c) -> T {
@@ -440,10 +460,12 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
   auto issue = [&](int bi) {
     const int I = block_of(bi);
     mbar_expect(&bar[bi & 1], bytes + dbytes);
-    bulk_copy(buf[bi & 1], band + (size_t)I * NB * W, bytes, &bar[bi & 1]);
-    bulk_copy(dbuf[bi & 1], Dnb + (size_t)I * NB * NB, dbytes, &bar[bi & 1]);
+    bulk_copy(buf(bi & 1), band + (size_t)I * NB * lb, bytes, &bar[bi & 1]);
+    bulk_copy(dbuf(bi & 1), Dnb + (size_t)I * NB * NB, dbytes, &bar[bi & 1]);
   };
 
+  // rows outside 0..N-1 read by the vectorised loop meet zero band entries: keep them finite
+  for (int k = t; k < 2 * R * kCols; k += THREADS) ring[k] = T(0);
   if (t == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -485,65 +507,77 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
       __syncthreads();
       return;
     }
-    const T* rows = buf[bi & 1];
-    T acc[kCols];
-#pragma unroll
-    for (int c = 0; c < kCols; ++c) acc[c] = T(0);
+    const T* rows = buf(bi & 1);
+    T acc0 = T(0), acc1 = T(0);
     if (i < N) {
-      const T* Lrow = rows + (size_t)r * W;
-      int qs, qe;
-      if (kFwd) {
-        qs = max(0, b - i);
-        qe = b - r;
-      } else {
-        qs = NB - r;
-        qe = min(b, N - 1 - i) + 1;
-      }
-#pragma unroll 4
-      for (int q = qs + part; q < qe; q += KS) {
-        const T l = Lrow[q];
-        const int j = kFwd ? (i - b + q) : (i + q);
-        const T* yr = ring + (size_t)(j & ring_mask) * kCols;
+      // off-block band entries q in [qs, qe): forward j = i - b + q < i0, backward j = i + q > i0 + NB - 1
+      const int qs = kFwd ? max(0, b - i) : NB - r;
+      const int qe = kFwd ? b - r : min(b, N - 1 - i) + 1;
+      if (qs < qe) {
+        const T* Lrow = rows + (size_t)r * lb;
+        const int qa = qs & ~(VQ - 1);  // 16-byte aligned start
+        int s0 = (kFwd ? (i - b + qa) : (i + qa)) % R;
+        if (s0 < 0) s0 += R;
+        // Forward: entries below qs are zero (rows j < 0), entries from qe on are inside the
+        // block and are masked. Backward: entries below qs are inside the block and masked,
+        // entries past qe are zero (rows j >= N, row padding).
+#pragma unroll 2
+        for (int q4 = qa + part * VQ; q4 < qe; q4 += KS * VQ) {
+          T l[VQ];
+          Vec16<T>::get(*reinterpret_cast<const typename Vec16<T>::V*>(Lrow + q4), l);
+          if (kFwd ? (q4 + VQ > qe) : (q4 < qs)) {
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) acc[c] = fma(l, yr[c], acc[c]);
+            for (int k = 0; k < VQ; ++k)
+              if (kFwd ? (q4 + k >= qe) : (q4 + k < qs)) l[k] = T(0);
+          }
+          const T* y = ring + (size_t)(s0 + (q4 - qa)) * kCols;
+#pragma unroll
+          for (int k = 0; k < VQ; ++k) {
+            acc0 = fma(l[k], y[2 * k], acc0);
+            acc1 = fma(l[k], y[2 * k + 1], acc1);
+          }
+        }
       }
     }
 #pragma unroll
-    for (int c = 0; c < kCols; ++c)
-#pragma unroll
-      for (int off = 1; off < KS; off <<= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
-    if (part == 0)
-#pragma unroll
-      for (int c = 0; c < kCols; ++c) tb[r * kCols + c] = (i < N) ? rhs[c] - acc[c] : T(0);
+    for (int off = 1; off < KS; off <<= 1) {
+      acc0 += __shfl_xor_sync(0xffffffffu, acc0, off);
+      acc1 += __shfl_xor_sync(0xffffffffu, acc1, off);
+    }
+    if (part == 0) {
+      tb[r * kCols + 0] = (i < N) ? rhs[0] - acc0 : T(0);
+      tb[r * kCols + 1] = (i < N) ? rhs[1] - acc1 : T(0);
+    }
     __syncthreads();
     // diagonal block: its NB x NB inverse arrived with the band rows
-    const T* D = dbuf[bi & 1];
-    T y[kCols];
-#pragma unroll
-    for (int c = 0; c < kCols; ++c) y[c] = T(0);
+    const T* D = dbuf(bi & 1);
+    T y0 = T(0), y1 = T(0);
     if (kFwd) {
       for (int k = part; k <= r; k += KS) {
         const T dv = D[r * NB + k];
-#pragma unroll
-        for (int c = 0; c < kCols; ++c) y[c] = fma(dv, tb[k * kCols + c], y[c]);
+        y0 = fma(dv, tb[k * kCols + 0], y0);
+        y1 = fma(dv, tb[k * kCols + 1], y1);
       }
     } else {
       for (int k = r + part; k < NB; k += KS) {
         const T dv = D[k * NB + r];
-#pragma unroll
-        for (int c = 0; c < kCols; ++c) y[c] = fma(dv, tb[k * kCols + c], y[c]);
+        y0 = fma(dv, tb[k * kCols + 0], y0);
+        y1 = fma(dv, tb[k * kCols + 1], y1);
       }
     }
 #pragma unroll
-    for (int c = 0; c < kCols; ++c)
-#pragma unroll
-      for (int off = 1; off < KS; off <<= 1) y[c] += __shfl_xor_sync(0xffffffffu, y[c], off);
+    for (int off = 1; off < KS; off <<= 1) {
+      y0 += __shfl_xor_sync(0xffffffffu, y0, off);
+      y1 += __shfl_xor_sync(0xffffffffu, y1, off);
+    }
     if (part == 0 && i < N) {
-#pragma unroll
-      for (int c = 0; c < kCols; ++c) {
-        ring[(size_t)(i & ring_mask) * kCols + c] = y[c];
-        if (c < ncl) write_out(i, cbase + c, y[c]);
-      }
+      const int sl = i % R;
+      ring[(size_t)sl * kCols + 0] = y0;
+      ring[(size_t)sl * kCols + 1] = y1;
+      ring[(size_t)(sl + R) * kCols + 0] = y0;
+      ring[(size_t)(sl + R) * kCols + 1] = y1;
+      if (0 < ncl) write_out(i, cbase + 0, y0);
+      if (1 < ncl) write_out(i, cbase + 1, y1);
     }
     __syncthreads();
     // both buffers of slot bi & 1 are free again: prefetch block bi + 2 into them
@@ -584,7 +618,7 @@ biot_status band_setup(biot_ctx* ctx, int kind) {
   const int bu = ctx->band_u, bp = ctx->band_p;
   if (bu + kNB > 8192) return fail(ctx, BIOT_E_INVALID, "mesh too large for the band solver (half-band %d)", bu);
   // band rows padded to a multiple of 64 (whole-block bulk copies), zero beyond N
-  const size_t su = (size_t)div_up(2 * nn, 64) * 64 * (bu + 1), sp = (size_t)div_up(nn, 64) * 64 * (bp + 1);
+  const size_t su = (size_t)div_up(2 * nn, 64) * 64 * band_ld(bu), sp = (size_t)div_up(nn, 64) * 64 * band_ld(bp);
   if (!ctx->Lu) {
     BIOT_TRY(dalloc(ctx, (void**)&ctx->Lu, sizeof(double) * su));
     BIOT_TRY(dalloc(ctx, (void**)&ctx->Uu, sizeof(double) * su));
@@ -704,7 +738,8 @@ size_t band_variant_smem(int v, bool fp64, int b) {
   const BandVariant& V = kBandVariants[v];
   const size_t es = fp64 ? 8 : 4;
   if (!V.tma) return es * ((size_t)ring_rows(b) * kCols + kNB * kCols);
-  return 64 + 2 * align16((size_t)V.nb * (b + 1) * es) + (size_t)ring_rows(b) * kCols * es + (size_t)V.nb * kCols * es;
+  return 64 + 2 * align16((size_t)V.nb * band_ld(b) * es) + 2 * align16((size_t)V.nb * V.nb * es) +
+         2 * (size_t)ring_rows(b) * kCols * es + (size_t)V.nb * kCols * es;
 }
 
 bool band_variant_ok(int v, bool fp64, int b) { return band_variant_smem(v, fp64, b) <= 227 * 1024; }
