@@ -487,6 +487,7 @@ biot_status biot_mesh_create(int32_t n, double Lx, double Ly, void* cuda_stream,
     if ((st = dalloc(ctx, (void**)&ctx->val, sizeof(double) * ctx->nnz)) != BIOT_OK) break;
     if ((st = dalloc(ctx, (void**)&ctx->apval, sizeof(double) * ctx->n_pairs)) != BIOT_OK) break;
     if ((st = dalloc(ctx, (void**)&ctx->dsc, sizeof(double) * ctx->n_dof)) != BIOT_OK) break;
+    if ((st = dalloc(ctx, (void**)&ctx->dsq, sizeof(double) * ctx->n_dof)) != BIOT_OK) break;
     if ((st = dalloc(ctx, (void**)&ctx->dmask, ctx->n_dof)) != BIOT_OK) break;
     if ((st = dalloc(ctx, (void**)&ctx->kappa, sizeof(double) * 2 * (size_t)n * n)) != BIOT_OK) break;
     if ((st = build_pattern(ctx)) != BIOT_OK) break;

@@ -350,13 +350,14 @@ __global__ void k_eliminate(int n_dof, const int32_t* __restrict__ rowptr, const
 }
 
 __global__ void k_dscale(int n_dof, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                         const double* __restrict__ val, double* __restrict__ dsc) {
+                         const double* __restrict__ val, double* __restrict__ dsc, double* __restrict__ dsq) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_dof) return;
   double d = 0.0;
   for (int32_t e = rowptr[r]; e < rowptr[r + 1]; ++e)
     if (col[e] == r) d = val[e];
   dsc[r] = 1.0 / sqrt(fabs(d));
+  dsq[r] = sqrt(fabs(d));
 }
 
 }  // namespace
@@ -425,7 +426,7 @@ biot_status assemble_system(biot_ctx* ctx) {
   BIOT_LAUNCH(k_init_state, div_up(nd, 128), 128, 0, s, n, nd, p.n_t, ctx->ldx, p.problem, hx, hy, ctx->X);
   BIOT_LAUNCH(k_eliminate, div_up(nd, 256), 256, 0, s, nd, ctx->rowptr, ctx->col, ctx->nodeptr, ctx->nbr, ctx->dmask,
               ctx->val, ctx->apval);
-  BIOT_LAUNCH(k_dscale, div_up(nd, 256), 256, 0, s, nd, ctx->rowptr, ctx->col, ctx->val, ctx->dsc);
+  BIOT_LAUNCH(k_dscale, div_up(nd, 256), 256, 0, s, nd, ctx->rowptr, ctx->col, ctx->val, ctx->dsc, ctx->dsq);
   BIOT_CU(ctx, cudaGetLastError());
   BIOT_CU(ctx, cudaFreeAsync(tmp, s));
   return BIOT_OK;

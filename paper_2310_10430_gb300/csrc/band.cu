@@ -415,10 +415,23 @@ template <> struct Vec16<double> {
   __device__ __forceinline__ static void get(const V& v, double* out) { out[0] = v.x; out[1] = v.y; }
 };
 
+// Sum of a and b over the KS lanes of a row group (KS a power of two, 2 <= KS <= 32),
+// transposed: lane `part` receives the sum of a when part is even and of b when odd,
+// with one add per lane per round instead of two.
+template <int KS, typename T>
+__device__ __forceinline__ T reduce_pair(T a, T b, int part) {
+  const bool odd = part & 1;
+  T keep = odd ? b : a;
+  keep += __shfl_xor_sync(0xffffffffu, odd ? a : b, 1);
+#pragma unroll
+  for (int off = 2; off < KS; off <<= 1) keep += __shfl_xor_sync(0xffffffffu, keep, off);
+  return keep;
+}
+
 template <int MODE, typename T, int NB, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__ Dnb, const T* __restrict__ vin,
-                 const double* __restrict__ dsc, T* __restrict__ ty, T* __restrict__ tp, T* __restrict__ z, int ld,
+                 const double* __restrict__ dsq, T* __restrict__ ty, T* __restrict__ tp, T* __restrict__ z, int ld,
                  int c0, int ncols, int ring_mask, int32_t* __restrict__ err) {
   constexpr bool kFwd = MODE <= FWD_P_FROM_V;
   constexpr int KS = THREADS / NB;  // lanes sharing one row
@@ -444,9 +457,9 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
   constexpr uint32_t dbytes = (uint32_t)(NB * NB * sizeof(T));
 
   auto read_rhs = [&](int i, int c) -> T {
-    if (MODE == FWD_U_FROM_V) { const int rr = udof(i); return vin[(size_t)rr * ld + c] / (T)dsc[rr]; }
+    if (MODE == FWD_U_FROM_V) { const int rr = udof(i); return vin[(size_t)rr * ld + c] * (T)dsq[rr]; }
     if (MODE == FWD_P_FROM_T) return tp[(size_t)i * ld + c];
-    if (MODE == FWD_P_FROM_V) { const int rr = 3 * i + 2; return -vin[(size_t)rr * ld + c] / (T)dsc[rr]; }
+    if (MODE == FWD_P_FROM_V) { const int rr = 3 * i + 2; return -vin[(size_t)rr * ld + c] * (T)dsq[rr]; }
     if (MODE == BWD_U_TO_Z) return ty[(size_t)i * ld + c];
     return tp[(size_t)i * ld + c];
   };
@@ -476,24 +489,20 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
     issue(0);
     if (nblk > 1) issue(1);
   }
-  T rhs_next[kCols];
+  // lane `part` of a row holds the right-hand side of column `part` (part < kCols)
+  T rhs_next;
   {
     const int i = block_of(0) * NB + r;
-#pragma unroll
-    for (int c = 0; c < kCols; ++c) rhs_next[c] = (part == 0 && i < N && c < ncl) ? read_rhs(i, cbase + c) : T(0);
+    rhs_next = (part < ncl && i < N) ? read_rhs(i, cbase + part) : T(0);
   }
   for (int bi = 0; bi < nblk; ++bi) {
     const int I = block_of(bi);
     const int i0 = I * NB;
     const int i = i0 + r;
-    T rhs[kCols];
-#pragma unroll
-    for (int c = 0; c < kCols; ++c) rhs[c] = rhs_next[c];
+    const T rhs = rhs_next;
     if (bi + 1 < nblk) {
       const int in = block_of(bi + 1) * NB + r;
-#pragma unroll
-      for (int c = 0; c < kCols; ++c)
-        rhs_next[c] = (part == 0 && in < N && c < ncl) ? read_rhs(in, cbase + c) : T(0);
+      rhs_next = (part < ncl && in < N) ? read_rhs(in, cbase + part) : T(0);
     }
     // band rows of this block: wait for the bulk copy (bounded)
     const bool ok = mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), kWaitBudget);
@@ -539,15 +548,9 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
         }
       }
     }
-#pragma unroll
-    for (int off = 1; off < KS; off <<= 1) {
-      acc0 += __shfl_xor_sync(0xffffffffu, acc0, off);
-      acc1 += __shfl_xor_sync(0xffffffffu, acc1, off);
-    }
-    if (part == 0) {
-      tb[r * kCols + 0] = (i < N) ? rhs[0] - acc0 : T(0);
-      tb[r * kCols + 1] = (i < N) ? rhs[1] - acc1 : T(0);
-    }
+    // transposed reduction over the row's KS lanes: lane `part` ends with column part & 1
+    const T s1 = reduce_pair<KS>(acc0, acc1, part);
+    if (part < kCols) tb[r * kCols + part] = (i < N) ? rhs - s1 : T(0);
     __syncthreads();
     // diagonal block: its NB x NB inverse arrived with the band rows
     const T* D = dbuf(bi & 1);
@@ -565,19 +568,12 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
         y1 = fma(dv, tb[k * kCols + 1], y1);
       }
     }
-#pragma unroll
-    for (int off = 1; off < KS; off <<= 1) {
-      y0 += __shfl_xor_sync(0xffffffffu, y0, off);
-      y1 += __shfl_xor_sync(0xffffffffu, y1, off);
-    }
-    if (part == 0 && i < N) {
+    const T y = reduce_pair<KS>(y0, y1, part);
+    if (part < kCols && i < N) {
       const int sl = i % R;
-      ring[(size_t)sl * kCols + 0] = y0;
-      ring[(size_t)sl * kCols + 1] = y1;
-      ring[(size_t)(sl + R) * kCols + 0] = y0;
-      ring[(size_t)(sl + R) * kCols + 1] = y1;
-      if (0 < ncl) write_out(i, cbase + 0, y0);
-      if (1 < ncl) write_out(i, cbase + 1, y1);
+      ring[(size_t)sl * kCols + part] = y;
+      ring[(size_t)(sl + R) * kCols + part] = y;
+      if (part < ncl) write_out(i, cbase + part, y);
     }
     __syncthreads();
     // both buffers of slot bi & 1 are free again: prefetch block bi + 2 into them
@@ -710,7 +706,7 @@ static void launch_tma(biot_ctx* ctx, int N, int b, const T* band, const T* Dinv
   }
   const int rr = ring_rows(b);
   const size_t smem = tma_smem_bytes<T, NB>(b);
-  BIOT_LAUNCH((k_band_solve_tma<MODE, T, NB, THREADS>), div_up(ncols, kCols), THREADS, smem, ctx->stream, N, b, band, Dinv, vin, ctx->dsc, BandBufs<T>::tu(ctx), BandBufs<T>::tp(ctx), z, ctx->wcap,
+  BIOT_LAUNCH((k_band_solve_tma<MODE, T, NB, THREADS>), div_up(ncols, kCols), THREADS, smem, ctx->stream, N, b, band, Dinv, vin, ctx->dsq, BandBufs<T>::tu(ctx), BandBufs<T>::tp(ctx), z, ctx->wcap,
               c0, ncols, rr - 1, ctx->status);
 }
 

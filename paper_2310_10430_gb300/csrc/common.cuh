@@ -112,6 +112,7 @@ struct biot_ctx {
   double* val = nullptr;        // AA after Dirichlet elimination, CSR order
   double* apval = nullptr;      // A'_pp after elimination, node-pair order
   double* dsc = nullptr;        // d = |diag AA|^{-1/2}
+  double* dsq = nullptr;        // |diag AA|^{1/2}: multiplies instead of dividing by dsc
   uint8_t* dmask = nullptr;     // 1 on Dirichlet DOFs
   double* kappa = nullptr;      // [2 n^2]
   // time data
