@@ -33,6 +33,7 @@ if ROOT not in sys.path:
 METRIC = "DOF*timesteps*outer-iters/s"
 UNIT = "DOF*timesteps*outer-iters/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz
 
 
 _SIZE = {}
@@ -199,6 +200,45 @@ def band_solve_flops(info, ncols, precond):
     return 2 * fa + 2 * fs, 4
 
 
+def _hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def streaming_kernels(info, ncols, precision, res_ms, res_n, spmm_ms, spmm_n):
+    """Algorithmic bytes and achieved bandwidth of the sparse sweep kernels.
+
+    Residual (one CSR pass over AA and A'): nnz*(s_v + 4) + P*s_v + 4*(N_dof + 1)
+    + N_dof*W*(s_x [X] + s_x [F] + s_o [R]) + N_dof*s_x [X column lo - 1]; the residual
+    is always formed in FP64 (s_v = s_x = 8) and written in the sweep's precision s_o.
+    SpMM (w = d .* AA z): the same without F and the extra column, in the sweep's
+    precision. Both also carry an FP64 ALU roof: 2*(nnz + P)*W flops for the residual,
+    2*nnz*W for the SpMM at the derived FP64 peak (FP32 one for the FP32 SpMM)."""
+    hbm, src = _hbm_peak()
+    nd, nnz, P = info.n_dof, info.nnz, info.n_pairs
+    s_o = 8 if precision == "fp64" else 4
+    s_z = 8 if precision == "fp64" else 4
+    s_val = {"fp64": 8, "fp32": 4, "bf16": 2}[precision]
+    res_bytes = nnz * (8 + 4) + P * 8 + 4 * (nd + 1) + nd * ncols * (8 + 8 + s_o) + nd * 8
+    spmm_bytes = nnz * (s_val + 4) + 4 * (nd + 1) + nd * ncols * 2 * s_z
+    out = {}
+    for name, ms, n, by, flops, alu in (
+            ("residual", res_ms, res_n, res_bytes, 2.0 * (nnz + P) * ncols, FP64_PEAK_TFLOPS),
+            ("spmm", spmm_ms, spmm_n, spmm_bytes, 2.0 * nnz * ncols,
+             FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS)):
+        if not n:
+            continue
+        t = ms / n / 1e3
+        out[name] = {"ms_per_launch": ms / n, "launches": n, "algorithmic_bytes": int(by),
+                     "achieved_gbs": by / t / 1e9, "hbm_peak_gbs": hbm, "hbm_frac": by / t / 1e9 / hbm,
+                     "peak_source": src, "alu_roof_ms": flops / (alu * 1e12) * 1e3,
+                     "alu_frac": flops / t / 1e12 / alu}
+    return out
+
+
 def profile_traffic(kernel_src):
     """dram bytes per launch from a committed ncu summary whose source hash matches."""
     sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
@@ -296,12 +336,17 @@ def run_ours(args):
     flops_per_launch = flops_per_apply / launches_per_apply
     achieved = flops_per_launch / (band_ms / band_n / 1e3) / 1e12
     traffic = profile_traffic(os.path.join(ROOT, "paper_2310_10430_gb300", "csrc", "band.cu"))
-    roofline = {"kernel": "k_band_solve* (FP64 band triangular solves of the P2 block solves)",
-                "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (FP64 not in MEASURED_PEAKS.json)",
+    fp64 = args.precision == "fp64"
+    peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+    roofline = {"kernel": "k_band_solve* (%s band triangular solves of the P2 block solves)" % ("FP64" if fp64 else "FP32"),
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (FP64 not in MEASURED_PEAKS.json)"
+                                if fp64 else "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz"),
                 "traffic": traffic, "launches": band_n, "avg_launch_ms": band_ms / band_n,
                 "share_of_step": band_ms / ms}
+
+    streaming = streaming_kernels(info, hi - lo + 1, args.precision, res_ms, res_n, spmm_ms, spmm_n)
 
     ctx.close()
     extras = {}
@@ -324,6 +369,7 @@ def run_ours(args):
             "roofline": roofline,
             "kernels_ms_per_step": {"band_solve": band_ms / args.steps, "residual": res_ms / args.steps,
                                     "spmm": spmm_ms / args.steps},
+            "streaming_kernels": streaming,
             "cpu_baseline": cpu,
             "tuning": tuning,
         }
@@ -339,7 +385,6 @@ def run_ours(args):
 # secondary measurements: reduced-precision sweeps, time to solution, batching
 # ---------------------------------------------------------------------------
 
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz
 
 
 def sweep_variant(case, precision, steps, warmup, stream):

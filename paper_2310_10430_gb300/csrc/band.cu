@@ -436,7 +436,8 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
   constexpr bool kFwd = MODE <= FWD_P_FROM_V;
   constexpr int KS = THREADS / NB;  // lanes sharing one row
   constexpr int VQ = Vec16<T>::n;   // band entries per 16-byte load
-  static_assert(THREADS % NB == 0 && KS <= 32 && (KS & (KS - 1)) == 0, "bad split");
+  static_assert(THREADS % NB == 0 && KS <= 32 && (KS & (KS - 1)) == 0 && KS >= 2, "bad split");
+  static_assert(THREADS >= 128 && NB % 4 == 0 && 64 % NB == 0, "phase 2 maps NB/4 rows to each of 4 warps");
   static_assert(kCols == 2, "the ring rows are read as pairs");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lb = band_ld(b);
@@ -552,28 +553,27 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
     const T s1 = reduce_pair<KS>(acc0, acc1, part);
     if (part < kCols) tb[r * kCols + part] = (i < N) ? rhs - s1 : T(0);
     __syncthreads();
-    // diagonal block: its NB x NB inverse arrived with the band rows
-    const T* D = dbuf(bi & 1);
-    T y0 = T(0), y1 = T(0);
-    if (kFwd) {
-      for (int k = part; k <= r; k += KS) {
-        const T dv = D[r * NB + k];
-        y0 = fma(dv, tb[k * kCols + 0], y0);
-        y1 = fma(dv, tb[k * kCols + 1], y1);
+    // diagonal block (its NB x NB inverse arrived with the band rows, zero outside the
+    // triangle) on warps 0..3, one per SM sub-partition: warp w owns rows w*NB/4 ..
+    // w*NB/4 + NB/4 - 1; lane = o * P2L + h, output o = (row, column), h splits the terms
+    if (t < 128) {
+      constexpr int P2L = 64 / NB;
+      const int w = t >> 5, lane = t & 31;
+      const int o = lane / P2L, h = lane % P2L;
+      const int r2 = w * (NB / 4) + (o >> 1), c2 = o & 1;
+      const T* D = dbuf(bi & 1);
+      T y = T(0);
+#pragma unroll
+      for (int k = h; k < NB; k += P2L) y = fma(kFwd ? D[r2 * NB + k] : D[k * NB + r2], tb[k * kCols + c2], y);
+#pragma unroll
+      for (int off = 1; off < P2L; off <<= 1) y += __shfl_xor_sync(0xffffffffu, y, off);
+      const int i2 = i0 + r2;
+      if (h == 0 && i2 < N) {
+        const int sl = i2 % R;
+        ring[(size_t)sl * kCols + c2] = y;
+        ring[(size_t)(sl + R) * kCols + c2] = y;
+        if (c2 < ncl) write_out(i2, cbase + c2, y);
       }
-    } else {
-      for (int k = r + part; k < NB; k += KS) {
-        const T dv = D[k * NB + r];
-        y0 = fma(dv, tb[k * kCols + 0], y0);
-        y1 = fma(dv, tb[k * kCols + 1], y1);
-      }
-    }
-    const T y = reduce_pair<KS>(y0, y1, part);
-    if (part < kCols && i < N) {
-      const int sl = i % R;
-      ring[(size_t)sl * kCols + part] = y;
-      ring[(size_t)(sl + R) * kCols + part] = y;
-      if (part < ncl) write_out(i, cbase + part, y);
     }
     __syncthreads();
     // both buffers of slot bi & 1 are free again: prefetch block bi + 2 into them
@@ -657,6 +657,7 @@ biot_status band_setup(biot_ctx* ctx, int kind) {
     BIOT_LAUNCH(k_to_f32, g, 256, 0, s, ctx->Dp, ctx->lp.Dp, dp);
   }
   BIOT_CU(ctx, cudaGetLastError());
+  ctx->lp.tile_ok[0] = ctx->lp.tile_ok[1] = 0;  // factors changed: rebuild the tiles on demand
   for (int pi = 0; pi < 2; ++pi) {
     ctx->band_var_u[pi] = band_variant_default(pi == 0, bu);
     ctx->band_var_p[pi] = band_variant_default(pi == 0, bp);
@@ -710,6 +711,230 @@ static void launch_tma(biot_ctx* ctx, int N, int b, const T* band, const T* Dinv
               c0, ncols, rr - 1, ctx->status);
 }
 
+// ---- FP32 band solves on skewed block tiles ----
+//
+// For block I (rows i0 .. i0 + NB - 1) the band entries that couple it to rows already
+// solved are stored as one dense NB x W tile, W = band_ld(b), aligned on the solution
+// index j = o + jj:
+//   forward  (L):   o = i0 - b rounded down to even, T[r][jj] = L[i0 + r][j] for
+//                   i0 + r - b <= j < i0, j >= 0;
+//   backward (L^T): o = i0 + NB, T[r][jj] = L^T[i0 + r][j] for j <= i0 + r + b, j < N;
+// every other entry (outside the band, inside the diagonal block, past the matrix) is an
+// explicit zero. The product of a tile with the solution window then needs no masks, and
+// a lane's 16-byte chunk of the window (four solution rows, both columns) serves four tile
+// rows at once, cutting the shared-memory reads per multiply-add to a quarter of the
+// row-by-row kernel's.
+constexpr int kTileNB = 32;
+constexpr int kTileThreads = 256;
+
+__host__ __device__ inline long long tile_origin(bool fwd, int i0, int b) {
+  return fwd ? (long long)((i0 - b) & ~1) : (long long)i0 + kTileNB;
+}
+
+__global__ void k_band_to_tiles(const float* __restrict__ band, int N, int b, bool fwd, float* __restrict__ tiles) {
+  const int W = band_ld(b);
+  const long long per = (long long)kTileNB * W;
+  const long long tot = (long long)((N + kTileNB - 1) / kTileNB) * per;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(t / per), rem = (int)(t % per);
+    const int r = rem / W, jj = rem % W;
+    const int i0 = I * kTileNB, i = i0 + r;
+    const long long j = tile_origin(fwd, i0, b) + jj;
+    float v = 0.f;
+    if (i < N && j >= 0 && j < N) {
+      if (fwd) {
+        if (j >= (long long)i - b && j < i0) v = band[(size_t)i * W + (size_t)(j - (i - b))];
+      } else {
+        if (j <= (long long)i + b && j >= i0 + kTileNB) v = band[(size_t)i * W + (size_t)(j - i)];
+      }
+    }
+    tiles[t] = v;
+  }
+}
+
+// Sum over a warp's 32 lanes of eight values per lane, transposed: lane l ends with the
+// sum of value (l >> 2) & 7 after 4 + 2 + 1 + 1 + 1 adds.
+__device__ __forceinline__ float reduce8(const float (&v)[8], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+  float u4[4], u2[2];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    u4[k] = (h16 ? v[k + 4] : v[k]) + __shfl_xor_sync(0xffffffffu, h16 ? v[k] : v[k + 4], 16);
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    u2[k] = (h8 ? u4[k + 2] : u4[k]) + __shfl_xor_sync(0xffffffffu, h8 ? u4[k] : u4[k + 2], 8);
+  float u1 = (h4 ? u2[1] : u2[0]) + __shfl_xor_sync(0xffffffffu, h4 ? u2[0] : u2[1], 4);
+  u1 += __shfl_xor_sync(0xffffffffu, u1, 2);
+  u1 += __shfl_xor_sync(0xffffffffu, u1, 1);
+  return u1;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTileThreads)
+k_band_solve_tile(int N, int b, const float* __restrict__ tiles, const float* __restrict__ Dnb,
+                  const float* __restrict__ vin, const double* __restrict__ dsq, float* __restrict__ ty,
+                  float* __restrict__ tp, float* __restrict__ z, int ld, int c0, int ncols, int ring_mask,
+                  int32_t* __restrict__ err) {
+  constexpr bool kFwd = MODE <= FWD_P_FROM_V;
+  constexpr int NB = kTileNB;
+  constexpr int RB = NB / (kTileThreads / 32);  // tile rows per warp
+  static_assert(RB == 4 && kCols == 2, "reduce8 sums 4 rows x 2 columns per warp");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int W = band_ld(b);
+  const int R = ring_mask + 1;  // the ring holds every row twice: slots j mod R and j mod R + R
+  const size_t tbytes_al = align16((size_t)NB * W * sizeof(float));
+  constexpr size_t dbytes_al = align16((size_t)NB * NB * sizeof(float));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  auto tbuf = [&](int slot) { return reinterpret_cast<const float*>(smem_raw + 64 + slot * tbytes_al); };
+  auto dbuf = [&](int slot) { return reinterpret_cast<const float*>(smem_raw + 64 + 2 * tbytes_al + slot * dbytes_al); };
+  auto tdst = [&](int slot) { return reinterpret_cast<float*>(smem_raw + 64 + slot * tbytes_al); };
+  auto ddst = [&](int slot) { return reinterpret_cast<float*>(smem_raw + 64 + 2 * tbytes_al + slot * dbytes_al); };
+  float* ring = reinterpret_cast<float*>(smem_raw + 64 + 2 * tbytes_al + 2 * dbytes_al);  // [2R][kCols]
+  float* tb = ring + (size_t)2 * R * kCols;                                               // [NB][kCols]
+  const int cbase = c0 + blockIdx.x * kCols;
+  const int ncl = min(kCols, c0 + ncols - cbase);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int nblk = (N + NB - 1) / NB;
+  const uint32_t tbytes = (uint32_t)((size_t)NB * W * sizeof(float));
+  constexpr uint32_t dbytes = (uint32_t)(NB * NB * sizeof(float));
+  // after the reductions lane `lane` holds row orow, column ocol (four lanes per output)
+  const int oidx = (lane >> 2) & 7;
+  const int orow = warp * RB + (oidx >> 1), ocol = oidx & 1;
+  const bool owner = (lane & 3) == 0;
+
+  auto read_rhs = [&](int i, int c) -> float {
+    if (MODE == FWD_U_FROM_V) { const int rr = udof(i); return vin[(size_t)rr * ld + c] * (float)dsq[rr]; }
+    if (MODE == FWD_P_FROM_T) return tp[(size_t)i * ld + c];
+    if (MODE == FWD_P_FROM_V) { const int rr = 3 * i + 2; return -vin[(size_t)rr * ld + c] * (float)dsq[rr]; }
+    if (MODE == BWD_U_TO_Z) return ty[(size_t)i * ld + c];
+    return tp[(size_t)i * ld + c];
+  };
+  auto write_out = [&](int i, int c, float y) {
+    if (MODE == FWD_U_FROM_V) ty[(size_t)i * ld + c] = y;
+    else if (MODE == FWD_P_FROM_T || MODE == FWD_P_FROM_V) tp[(size_t)i * ld + c] = y;
+    else if (MODE == BWD_U_TO_Z) z[(size_t)udof(i) * ld + c] = y;
+    else z[(size_t)(3 * i + 2) * ld + c] = y;
+  };
+  auto block_of = [&](int bi) { return kFwd ? bi : (nblk - 1 - bi); };
+  auto issue = [&](int bi) {
+    const int I = block_of(bi);
+    mbar_expect(&bar[bi & 1], tbytes + dbytes);
+    bulk_copy(tdst(bi & 1), tiles + (size_t)I * NB * W, tbytes, &bar[bi & 1]);
+    bulk_copy(ddst(bi & 1), Dnb + (size_t)I * NB * NB, dbytes, &bar[bi & 1]);
+  };
+
+  // window rows that no block has written (j < 0, j >= N) meet zero tile entries: keep them finite
+  for (int k = t; k < 2 * R * kCols; k += kTileThreads) ring[k] = 0.f;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (t == 0) {
+    issue(0);
+    if (nblk > 1) issue(1);
+  }
+  float rhs_next;
+  {
+    const int i = block_of(0) * NB + orow;
+    rhs_next = (owner && ocol < ncl && i < N) ? read_rhs(i, cbase + ocol) : 0.f;
+  }
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int I = block_of(bi);
+    const int i0 = I * NB;
+    const int io = i0 + orow;
+    const float rhs = rhs_next;
+    if (bi + 1 < nblk) {
+      const int in = block_of(bi + 1) * NB + orow;
+      rhs_next = (owner && ocol < ncl && in < N) ? read_rhs(in, cbase + ocol) : 0.f;
+    }
+    const bool ok = mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), kWaitBudget);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicExch(err, 1);
+        // let copies still in flight land before the CTA's shared memory is released
+        mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), kWaitBudget);
+        if (bi + 1 < nblk) mbar_wait_bounded(&bar[(bi + 1) & 1], (uint32_t)(((bi + 1) >> 1) & 1), kWaitBudget);
+      }
+      __syncthreads();
+      return;
+    }
+    // off-block products: tile rows warp*RB .. warp*RB + RB - 1 times the solution window
+    int s0 = (int)(tile_origin(kFwd, i0, b) % R);
+    if (s0 < 0) s0 += R;  // even: the origin and R are even, so window chunks are 16-byte aligned
+    const float* Trow = tbuf(bi & 1) + (size_t)(warp * RB) * W;
+    float acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+#pragma unroll 2
+    for (int ch = lane; ch < W / 4; ch += 32) {
+      const float4 ya = *reinterpret_cast<const float4*>(ring + (size_t)(s0 + 4 * ch) * kCols);
+      const float4 yb = *reinterpret_cast<const float4*>(ring + (size_t)(s0 + 4 * ch + 2) * kCols);
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr) {
+        const float4 tv = *reinterpret_cast<const float4*>(Trow + (size_t)rr * W + 4 * ch);
+        float a0 = acc[2 * rr], a1 = acc[2 * rr + 1];
+        a0 = fmaf(tv.x, ya.x, a0);
+        a1 = fmaf(tv.x, ya.y, a1);
+        a0 = fmaf(tv.y, ya.z, a0);
+        a1 = fmaf(tv.y, ya.w, a1);
+        a0 = fmaf(tv.z, yb.x, a0);
+        a1 = fmaf(tv.z, yb.y, a1);
+        a0 = fmaf(tv.w, yb.z, a0);
+        a1 = fmaf(tv.w, yb.w, a1);
+        acc[2 * rr] = a0;
+        acc[2 * rr + 1] = a1;
+      }
+    }
+    const float sum = reduce8(acc, lane);
+    if (owner) tb[orow * kCols + ocol] = rhs - sum;
+    __syncthreads();
+    // diagonal block: y = D_I tb with D_I's NB x NB inverse (zero outside the triangle)
+    {
+      const float* D = dbuf(bi & 1);
+      const int h = lane & 3;
+      float y = 0.f;
+#pragma unroll
+      for (int k = h; k < NB; k += 4) y = fmaf(kFwd ? D[orow * NB + k] : D[k * NB + orow], tb[k * kCols + ocol], y);
+      y += __shfl_xor_sync(0xffffffffu, y, 1);
+      y += __shfl_xor_sync(0xffffffffu, y, 2);
+      if (owner && io < N) {
+        const int sl = io % R;
+        ring[(size_t)sl * kCols + ocol] = y;
+        ring[(size_t)(sl + R) * kCols + ocol] = y;
+        if (ocol < ncl) write_out(io, cbase + ocol, y);
+      }
+    }
+    __syncthreads();
+    // both buffers of slot bi & 1 are free again: prefetch block bi + 2 into them
+    if (t == 0 && bi + 2 < nblk) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(bi + 2);
+    }
+  }
+}
+
+size_t tile_smem_bytes(int b) {
+  return 64 + 2 * align16((size_t)kTileNB * band_ld(b) * sizeof(float)) +
+         2 * align16((size_t)kTileNB * kTileNB * sizeof(float)) + 2 * (size_t)ring_rows(b) * kCols * sizeof(float) +
+         (size_t)kTileNB * kCols * sizeof(float);
+}
+
+template <int MODE>
+static void launch_tile(biot_ctx* ctx, int N, int b, const float* tiles, const float* Dnb, const float* vin, float* z,
+                        int c0, int ncols) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_band_solve_tile<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr_set = true;
+  }
+  const int rr = ring_rows(b);
+  const size_t smem = tile_smem_bytes(b);
+  BIOT_LAUNCH(k_band_solve_tile<MODE>, div_up(ncols, kCols), kTileThreads, smem, ctx->stream, N, b, tiles, Dnb, vin,
+              ctx->dsq, ctx->lp.tu, ctx->lp.tp, z, ctx->wcap, c0, ncols, rr - 1, ctx->status);
+}
+
 template <int MODE, typename T>
 static void launch_legacy(biot_ctx* ctx, int N, int b, const T* band, const T* Dinv, const T* vin, T* z, int c0,
                           int ncols) {
@@ -728,7 +953,7 @@ static void launch_legacy(biot_ctx* ctx, int N, int b, const T* band, const T* D
 // Band-solve variants the tuner chooses from: the register-streaming kernel, and
 // TMA-staged kernels with NB-row blocks and THREADS threads.
 const BandVariant kBandVariants[kBandVariantCount] = {
-    {0, 64, 256}, {1, 16, 128}, {1, 16, 256}, {1, 32, 256}, {1, 8, 128}, {1, 32, 128}};
+    {0, 64, 256}, {1, 16, 128}, {1, 16, 256}, {1, 32, 256}, {1, 8, 128}, {1, 32, 128}, {2, kTileNB, kTileThreads}};
 
 size_t band_variant_smem(int v, bool fp64, int b) {
   const BandVariant& V = kBandVariants[v];
@@ -738,10 +963,13 @@ size_t band_variant_smem(int v, bool fp64, int b) {
          2 * (size_t)ring_rows(b) * kCols * es + (size_t)V.nb * kCols * es;
 }
 
-bool band_variant_ok(int v, bool fp64, int b) { return band_variant_smem(v, fp64, b) <= 227 * 1024; }
+bool band_variant_ok(int v, bool fp64, int b) {
+  if (fp64 && kBandVariants[v].tma == 2) return false;  // the tile solve is FP32 only
+  return band_variant_smem(v, fp64, b) <= 227 * 1024;
+}
 
 int band_variant_default(bool fp64, int b) {
-  const int pref = fp64 ? 1 : 3;  // TMA NB=16 x 128 threads (FP64), NB=32 x 256 threads (FP32)
+  const int pref = fp64 ? 2 : 6;  // TMA NB=16 x 256 threads (FP64), skewed tiles NB=32 x 256 threads (FP32)
   if (band_variant_ok(pref, fp64, b)) return pref;
   for (int v = kBandVariantCount - 1; v > 0; --v)
     if (band_variant_ok(v, fp64, b)) return v;
@@ -759,6 +987,13 @@ static void solve(biot_ctx* ctx, int variant, int N, int b, const T* band, const
     case 3: launch_tma<MODE, T, 32, 256>(ctx, N, b, band, Dnb, vin, z, c0, ncols); break;
     case 4: launch_tma<MODE, T, 8, 128>(ctx, N, b, band, Dnb, vin, z, c0, ncols); break;
     case 5: launch_tma<MODE, T, 32, 128>(ctx, N, b, band, Dnb, vin, z, c0, ncols); break;
+    case 6:
+      if constexpr (sizeof(T) == 4) {
+        constexpr bool u = MODE == FWD_U_FROM_V || MODE == BWD_U_TO_Z;
+        constexpr bool fwd = MODE <= FWD_P_FROM_V;
+        launch_tile<MODE>(ctx, N, b, ctx->lp.tile[u ? 0 : 1][fwd ? 0 : 1], Dnb, vin, z, c0, ncols);
+      }
+      break;
     default: launch_legacy<MODE, T>(ctx, N, b, band, Dinv, vin, z, c0, ncols); break;
   }
 }
@@ -778,8 +1013,25 @@ static biot_status build_dnb(biot_ctx* ctx, bool u, int nb) {
   return BIOT_OK;
 }
 
+// Skewed block tiles of block u (A) or p (S), forward and backward, from the FP32 factors.
+static biot_status ensure_tiles(biot_ctx* ctx, bool u) {
+  const int k = u ? 0 : 1;
+  if (ctx->lp.tile_ok[k]) return BIOT_OK;
+  const int N = u ? 2 * ctx->n_nodes : ctx->n_nodes;
+  const int b = u ? ctx->band_u : ctx->band_p;
+  const size_t sz = (size_t)div_up(N, kTileNB) * kTileNB * band_ld(b);
+  for (int d = 0; d < 2; ++d)
+    if (!ctx->lp.tile[k][d]) BIOT_TRY(dalloc(ctx, (void**)&ctx->lp.tile[k][d], sizeof(float) * sz));
+  BIOT_LAUNCH(k_band_to_tiles, 1024, 256, 0, ctx->stream, u ? ctx->lp.Lu : ctx->lp.Lp, N, b, true, ctx->lp.tile[k][0]);
+  BIOT_LAUNCH(k_band_to_tiles, 1024, 256, 0, ctx->stream, u ? ctx->lp.Uu : ctx->lp.Up, N, b, false, ctx->lp.tile[k][1]);
+  BIOT_CU(ctx, cudaGetLastError());
+  ctx->lp.tile_ok[k] = 1;
+  return BIOT_OK;
+}
+
 biot_status ensure_dnb(biot_ctx* ctx, bool fp64, bool u, int variant) {
   if (!kBandVariants[variant].tma) return BIOT_OK;
+  if (kBandVariants[variant].tma == 2 && !fp64) BIOT_TRY(ensure_tiles(ctx, u));
   return fp64 ? build_dnb<double>(ctx, u, kBandVariants[variant].nb)
               : build_dnb<float>(ctx, u, kBandVariants[variant].nb);
 }

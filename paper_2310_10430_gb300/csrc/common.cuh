@@ -55,6 +55,8 @@ struct LowPrec {
   float* Lp = nullptr;
   float* Up = nullptr;
   float* Dp = nullptr;
+  float* tile[2][2] = {};        // [u, p][forward, backward]: skewed block tiles of the band solve
+  int tile_ok[2] = {0, 0};       // tiles of [u, p] built from the current factors
 };
 
 // One instance of a batch, as the batched kernels see it (device-resident table).
@@ -217,11 +219,11 @@ template <typename T> void launch_coupling(biot_ctx* ctx, const T* z, const T* v
 
 // ---- band.cu ----
 struct BandVariant {
-  int tma;      // 1: band rows staged in shared memory by bulk copies
+  int tma;      // 1: band rows staged in shared memory by bulk copies; 2: skewed block tiles (FP32)
   int nb;       // rows per block
   int threads;  // CTA size
 };
-constexpr int kBandVariantCount = 6;
+constexpr int kBandVariantCount = 7;
 extern const BandVariant kBandVariants[kBandVariantCount];
 size_t band_variant_smem(int v, bool fp64, int b);
 bool band_variant_ok(int v, bool fp64, int b);

@@ -156,6 +156,123 @@ __device__ __forceinline__ void spmm_body(int nn, const int32_t* __restrict__ no
   }
 }
 
+// 16-byte vector of XT (four floats or two doubles).
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using V = float4;
+  static constexpr int n = 4;
+  __device__ __forceinline__ static void get(const V& v, float* o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  __device__ __forceinline__ static V make(const float* o) { return make_float4(o[0], o[1], o[2], o[3]); }
+};
+template <> struct Vec16<double> {
+  using V = double2;
+  static constexpr int n = 2;
+  __device__ __forceinline__ static void get(const V& v, double* o) { o[0] = v.x; o[1] = v.y; }
+  __device__ __forceinline__ static V make(const double* o) { return make_double2(o[0], o[1]); }
+};
+
+// spmm_body with 16-byte accesses: a lane owns VEC consecutive columns, so every DOF row
+// of z is read with one 128-bit load per lane and a warp covers 32 * VEC columns per
+// pass. The column range is widened down to a multiple of VEC; lanes mask what lies
+// outside [c0, c0 + ncols). Needs ld % VEC == 0 and 16-byte aligned z and w. The sums
+// run in the same order as spmm_body, and the per-column norm partials land in the same
+// slots part[block * ld + column].
+template <typename XT, typename VT>
+__device__ __forceinline__ void spmm_vec_body(int nn, const int32_t* __restrict__ nodeptr,
+              const int32_t* __restrict__ nbr, const int32_t* __restrict__ rowptr, const VT* __restrict__ val,
+              const double* __restrict__ dsc, const XT* __restrict__ z, XT* __restrict__ w, int ld, int c0,
+              int ncols, double* __restrict__ part) {
+  using A = typename Acc<XT>::T;
+  using V = typename Vec16<XT>::V;
+  constexpr int VEC = Vec16<XT>::n;
+  __shared__ double sm[kWarps][32 * VEC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = (nn + gridDim.x - 1) / gridDim.x;
+  const int vb = blockIdx.x * per, ve = min(nn, vb + per);
+  const int ca = c0 & ~(VEC - 1), ce = c0 + ncols;
+  for (int cb = ca; cb < ce; cb += 32 * VEC) {
+    const int c = cb + lane * VEC;
+    const bool any = c < ce;
+    const bool full = c >= c0 && c + VEC <= ce;
+    const int cc = any ? c : ca;
+    A ww[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) ww[q] = 0;
+    for (int v = vb + warp; v < ve; v += kWarps) {
+      const int32_t np = nodeptr[v];
+      const int deg = nodeptr[v + 1] - np;
+      const int32_t r0 = rowptr[3 * v], r1 = r0 + 3 * deg, r2 = r1 + 3 * deg;
+      A a0[VEC], a1[VEC], a2[VEC];
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) a0[q] = a1[q] = a2[q] = 0;
+#pragma unroll 4
+      for (int k = 0; k < deg; ++k) {
+        const int m = nbr[np + k];
+        const XT* zm = z + (size_t)(3 * m) * ld + cc;
+        XT x0[VEC], x1[VEC], x2[VEC];
+        Vec16<XT>::get(*reinterpret_cast<const V*>(zm), x0);
+        Vec16<XT>::get(*reinterpret_cast<const V*>(zm + ld), x1);
+        Vec16<XT>::get(*reinterpret_cast<const V*>(zm + 2 * ld), x2);
+        const VT* e0 = val + r0 + 3 * k;
+        const VT* e1 = val + r1 + 3 * k;
+        const VT* e2 = val + r2 + 3 * k;
+        const A m00 = to_acc(e0[0]), m01 = to_acc(e0[1]), m02 = to_acc(e0[2]);
+        const A m10 = to_acc(e1[0]), m11 = to_acc(e1[1]), m12 = to_acc(e1[2]);
+        const A m20 = to_acc(e2[0]), m21 = to_acc(e2[1]), m22 = to_acc(e2[2]);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+          a0[q] += m00 * (A)x0[q] + m01 * (A)x1[q] + m02 * (A)x2[q];
+          a1[q] += m10 * (A)x0[q] + m11 * (A)x1[q] + m12 * (A)x2[q];
+          a2[q] += m20 * (A)x0[q] + m21 * (A)x1[q] + m22 * (A)x2[q];
+        }
+      }
+      const A d0 = (A)dsc[3 * v], d1 = (A)dsc[3 * v + 1], d2 = (A)dsc[3 * v + 2];
+      XT o0[VEC], o1[VEC], o2[VEC];
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) {
+        const A q0 = d0 * a0[q], q1 = d1 * a1[q], q2 = d2 * a2[q];
+        o0[q] = (XT)q0;
+        o1[q] = (XT)q1;
+        o2[q] = (XT)q2;
+        const bool in = c + q >= c0 && c + q < ce;
+        if (in) ww[q] += q0 * q0 + q1 * q1 + q2 * q2;
+      }
+      XT* w0 = w + (size_t)(3 * v) * ld + c;
+      if (full) {
+        *reinterpret_cast<V*>(w0) = Vec16<XT>::make(o0);
+        *reinterpret_cast<V*>(w0 + ld) = Vec16<XT>::make(o1);
+        *reinterpret_cast<V*>(w0 + 2 * ld) = Vec16<XT>::make(o2);
+      } else if (any) {
+#pragma unroll
+        for (int q = 0; q < VEC; ++q)
+          if (c + q >= c0 && c + q < ce) {
+            w0[q] = o0[q];
+            w0[ld + q] = o1[q];
+            w0[2 * ld + q] = o2[q];
+          }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) sm[warp][lane * VEC + q] = (double)ww[q];
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * VEC; t += blockDim.x) {
+      double sum = 0.0;
+      for (int u = 0; u < kWarps; ++u) sum += sm[u][t];
+      const int col = cb + t;
+      if (col >= c0 && col < ce) part[(size_t)blockIdx.x * ld + col] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename XT, typename VT>
+__global__ void __launch_bounds__(kWarps * 32, 2)
+k_spmm_vec(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
+           const int32_t* __restrict__ rowptr, const VT* __restrict__ val, const double* __restrict__ dsc,
+           const XT* __restrict__ z, XT* __restrict__ w, int ld, int c0, int ncols, double* __restrict__ part) {
+  spmm_vec_body<XT, VT>(nn, nodeptr, nbr, rowptr, val, dsc, z, w, ld, c0, ncols, part);
+}
+
 template <typename XT, typename VT>
 __global__ void __launch_bounds__(kWarps * 32)
 k_spmm_scaled(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
@@ -237,6 +354,13 @@ __global__ void kb_coupling(const InstDev* __restrict__ tab, int j) {
 
 }  // namespace
 
+// The 16-byte SpMM needs rows of z and w that start on 16-byte boundaries.
+template <typename XT>
+static bool vec_ok(const biot_ctx* ctx, const XT* z, const XT* w) {
+  constexpr int VEC = Vec16<XT>::n;
+  return ctx->wcap % VEC == 0 && reinterpret_cast<uintptr_t>(z) % 16 == 0 && reinterpret_cast<uintptr_t>(w) % 16 == 0;
+}
+
 void launch_residual_raw(int n_nodes, const int32_t* nodeptr, const int32_t* nbr, const int32_t* rowptr,
                          const double* val, const double* apval, const double* dsc, const double* X,
                          const double* F, int ldx, int lo, int ncols, double* out, int ldo, double* part, int ldp,
@@ -264,20 +388,35 @@ void launch_residual_lp(biot_ctx* ctx, int lo, int ncols) {
 template <>
 void launch_spmm_scaled<double>(biot_ctx* ctx, const double* z, double* w, int c0, int ncols) {
   KTimer tm(ctx, BIOT_KC_SPMM);
-  BIOT_LAUNCH((k_spmm_scaled<double, double>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr,
-              ctx->nbr, ctx->rowptr, ctx->val, ctx->dsc, z, w, ctx->wcap, c0, ncols, ctx->part);
+  if (vec_ok<double>(ctx, z, w))
+    BIOT_LAUNCH((k_spmm_vec<double, double>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr,
+                ctx->nbr, ctx->rowptr, ctx->val, ctx->dsc, z, w, ctx->wcap, c0, ncols, ctx->part);
+  else
+    BIOT_LAUNCH((k_spmm_scaled<double, double>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes,
+                ctx->nodeptr, ctx->nbr, ctx->rowptr, ctx->val, ctx->dsc, z, w, ctx->wcap, c0, ncols, ctx->part);
 }
 
 template <>
 void launch_spmm_scaled<float>(biot_ctx* ctx, const float* z, float* w, int c0, int ncols) {
   KTimer tm(ctx, BIOT_KC_SPMM);
-  if (ctx->prm.precision == BIOT_BF16VAL_FP32ACC)
-    BIOT_LAUNCH((k_spmm_scaled<float, __nv_bfloat16>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes,
-                ctx->nodeptr, ctx->nbr, ctx->rowptr, ctx->lp.val_bf16, ctx->dsc, z, w, ctx->wcap, c0, ncols,
-                ctx->part);
-  else
-    BIOT_LAUNCH((k_spmm_scaled<float, float>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr,
-                ctx->nbr, ctx->rowptr, ctx->lp.val, ctx->dsc, z, w, ctx->wcap, c0, ncols, ctx->part);
+  const bool vec = vec_ok<float>(ctx, z, w);
+  if (ctx->prm.precision == BIOT_BF16VAL_FP32ACC) {
+    if (vec)
+      BIOT_LAUNCH((k_spmm_vec<float, __nv_bfloat16>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes,
+                  ctx->nodeptr, ctx->nbr, ctx->rowptr, ctx->lp.val_bf16, ctx->dsc, z, w, ctx->wcap, c0, ncols,
+                  ctx->part);
+    else
+      BIOT_LAUNCH((k_spmm_scaled<float, __nv_bfloat16>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes,
+                  ctx->nodeptr, ctx->nbr, ctx->rowptr, ctx->lp.val_bf16, ctx->dsc, z, w, ctx->wcap, c0, ncols,
+                  ctx->part);
+  } else {
+    if (vec)
+      BIOT_LAUNCH((k_spmm_vec<float, float>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes,
+                  ctx->nodeptr, ctx->nbr, ctx->rowptr, ctx->lp.val, ctx->dsc, z, w, ctx->wcap, c0, ncols, ctx->part);
+    else
+      BIOT_LAUNCH((k_spmm_scaled<float, float>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes,
+                  ctx->nodeptr, ctx->nbr, ctx->rowptr, ctx->lp.val, ctx->dsc, z, w, ctx->wcap, c0, ncols, ctx->part);
+  }
 }
 
 template <>

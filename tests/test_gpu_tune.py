@@ -25,7 +25,7 @@ from paper_2310_10430_gb300 import biot  # noqa: E402
 from paper_2310_10430_gb300 import build as B  # noqa: E402
 
 B.build()
-N_VARIANTS = 6
+N_VARIANTS = 7
 
 
 @pytest.mark.parametrize("precision,bound", [("fp64", 1e-9), ("fp32", 1e-3)])
