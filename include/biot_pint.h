@@ -24,7 +24,11 @@
  *  - Host buffers are owned by the caller; device memory is owned by the
  *    context and released by biot_destroy. Work is stream-ordered on the CUDA
  *    stream given to biot_mesh_create; calls that return host data synchronise
- *    that stream before returning.
+ *    that stream before returning. The context also owns one non-blocking
+ *    stream of the highest priority: the block-diagonal preconditioner runs its
+ *    solves on A there, concurrently with its solves on S on the caller's
+ *    stream, forked from and joined back to the caller's stream by events, so
+ *    the ordering seen on the caller's stream is unchanged.
  *  - No C++ exception or exit() crosses the ABI. Every call returns a
  *    biot_status; biot_last_error() gives a one-line message for the last
  *    failure on that context. A call made in the wrong order returns
@@ -276,8 +280,10 @@ typedef struct {
   int32_t from_cache;                   /* 1 if both choices came from the cache file */
 } biot_tuning;
 
-/* Pick the band triangular-solve kernel variant (register-streamed, or TMA-staged
- * with 8/16/32-row blocks and 128/256 threads; those whose shared memory fits)
+/* Pick the band triangular-solve kernel variant (register-streamed; TMA-staged
+ * band rows with 8/16/32-row blocks and 128/256 threads; in FP32 also skewed
+ * 32-row block tiles with as many bulk-copy stages as fit; those whose shared
+ * memory fits)
  * for A and for S by timing a forward + backward solve pair of each candidate on
  * this context's factors at full window width, in the context's precision.
  * cache_path (nullable): JSON file of earlier choices keyed by precision, block

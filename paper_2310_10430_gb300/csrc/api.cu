@@ -475,6 +475,18 @@ biot_status biot_mesh_create(int32_t n, double Lx, double Ly, void* cuda_stream,
   ctx->Lx = Lx;
   ctx->Ly = Ly;
   ctx->stream = (cudaStream_t)cuda_stream;
+  {
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      biot_status st = fail(nullptr, BIOT_E_CUDA, "biot_mesh_create: side stream: %s", cudaGetErrorString(e));
+      biot_destroy(ctx);
+      return st;
+    }
+  }
   ctx->n_nodes = (n + 1) * (n + 1);
   ctx->n_dof = 3 * ctx->n_nodes;
   ctx->n_pairs = 7 * n * n + 6 * n + 1;
@@ -819,6 +831,12 @@ const char* biot_last_error(const biot_ctx* ctx) {
 void biot_destroy(biot_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   dfree_all(ctx);
   delete ctx;

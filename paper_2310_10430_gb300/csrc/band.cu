@@ -726,6 +726,9 @@ static void launch_tma(biot_ctx* ctx, int N, int b, const T* band, const T* Dinv
 // row-by-row kernel's.
 constexpr int kTileNB = 32;
 constexpr int kTileThreads = 256;
+// Two stages: deeper pipelines measured no faster alone and slower beside the concurrent
+// S solves of P2 (a smaller footprint lets two S-solve CTAs share an SM).
+constexpr int kTileMaxStages = 2;
 
 __host__ __device__ inline long long tile_origin(bool fwd, int i0, int b) {
   return fwd ? (long long)((i0 - b) & ~1) : (long long)i0 + kTileNB;
@@ -774,22 +777,23 @@ __global__ void __launch_bounds__(kTileThreads)
 k_band_solve_tile(int N, int b, const float* __restrict__ tiles, const float* __restrict__ Dnb,
                   const float* __restrict__ vin, const double* __restrict__ dsq, float* __restrict__ ty,
                   float* __restrict__ tp, float* __restrict__ z, int ld, int c0, int ncols, int ring_mask,
-                  int32_t* __restrict__ err) {
+                  int nst, int32_t* __restrict__ err) {
   constexpr bool kFwd = MODE <= FWD_P_FROM_V;
   constexpr int NB = kTileNB;
   constexpr int RB = NB / (kTileThreads / 32);  // tile rows per warp
   static_assert(RB == 4 && kCols == 2, "reduce8 sums 4 rows x 2 columns per warp");
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  // nst pipeline stages of (tile, block inverse); the ring holds every solution row twice,
+  // slots j mod R and j mod R + R, R a power of two above the rows alive at once (W + NB)
   const int W = band_ld(b);
-  const int R = ring_mask + 1;  // the ring holds every row twice: slots j mod R and j mod R + R
+  const int R = ring_mask + 1;
   const size_t tbytes_al = align16((size_t)NB * W * sizeof(float));
   constexpr size_t dbytes_al = align16((size_t)NB * NB * sizeof(float));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  auto tbuf = [&](int slot) { return reinterpret_cast<const float*>(smem_raw + 64 + slot * tbytes_al); };
-  auto dbuf = [&](int slot) { return reinterpret_cast<const float*>(smem_raw + 64 + 2 * tbytes_al + slot * dbytes_al); };
-  auto tdst = [&](int slot) { return reinterpret_cast<float*>(smem_raw + 64 + slot * tbytes_al); };
-  auto ddst = [&](int slot) { return reinterpret_cast<float*>(smem_raw + 64 + 2 * tbytes_al + slot * dbytes_al); };
-  float* ring = reinterpret_cast<float*>(smem_raw + 64 + 2 * tbytes_al + 2 * dbytes_al);  // [2R][kCols]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);  // [nst], nst <= kTileMaxStages
+  unsigned char* stage0 = smem_raw + 8 * kTileMaxStages;
+  auto tdst = [&](int slot) { return reinterpret_cast<float*>(stage0 + slot * tbytes_al); };
+  auto ddst = [&](int slot) { return reinterpret_cast<float*>(stage0 + nst * tbytes_al + slot * dbytes_al); };
+  float* ring = reinterpret_cast<float*>(stage0 + nst * (tbytes_al + dbytes_al));  // [2R][kCols]
   float* tb = ring + (size_t)2 * R * kCols;                                               // [NB][kCols]
   const int cbase = c0 + blockIdx.x * kCols;
   const int ncl = min(kCols, c0 + ncols - cbase);
@@ -816,30 +820,31 @@ k_band_solve_tile(int N, int b, const float* __restrict__ tiles, const float* __
     else z[(size_t)(3 * i + 2) * ld + c] = y;
   };
   auto block_of = [&](int bi) { return kFwd ? bi : (nblk - 1 - bi); };
-  auto issue = [&](int bi) {
+  auto issue = [&](int bi, int sl) {
     const int I = block_of(bi);
-    mbar_expect(&bar[bi & 1], tbytes + dbytes);
-    bulk_copy(tdst(bi & 1), tiles + (size_t)I * NB * W, tbytes, &bar[bi & 1]);
-    bulk_copy(ddst(bi & 1), Dnb + (size_t)I * NB * NB, dbytes, &bar[bi & 1]);
+    mbar_expect(&bar[sl], tbytes + dbytes);
+    bulk_copy(tdst(sl), tiles + (size_t)I * NB * W, tbytes, &bar[sl]);
+    bulk_copy(ddst(sl), Dnb + (size_t)I * NB * NB, dbytes, &bar[sl]);
   };
 
   // window rows that no block has written (j < 0, j >= N) meet zero tile entries: keep them finite
   for (int k = t; k < 2 * R * kCols; k += kTileThreads) ring[k] = 0.f;
   if (t == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int k = 0; k < nst; ++k) mbar_init(&bar[k], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (t == 0) {
-    issue(0);
-    if (nblk > 1) issue(1);
-  }
+  if (t == 0)
+    for (int k = 0; k < nst && k < nblk; ++k) issue(k, k);
   float rhs_next;
   {
     const int i = block_of(0) * NB + orow;
     rhs_next = (owner && ocol < ncl && i < N) ? read_rhs(i, cbase + ocol) : 0.f;
   }
+  // stage and its barrier phase, and the window's first ring slot, advance with bi
+  int slot = 0;
+  uint32_t phase = 0;
+  int s0 = (kFwd ? ((block_of(0) * NB - b) & ~1) : block_of(0) * NB + NB) & ring_mask;  // even
   for (int bi = 0; bi < nblk; ++bi) {
     const int I = block_of(bi);
     const int i0 = I * NB;
@@ -849,21 +854,20 @@ k_band_solve_tile(int N, int b, const float* __restrict__ tiles, const float* __
       const int in = block_of(bi + 1) * NB + orow;
       rhs_next = (owner && ocol < ncl && in < N) ? read_rhs(in, cbase + ocol) : 0.f;
     }
-    const bool ok = mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), kWaitBudget);
+    const bool ok = mbar_wait_bounded(&bar[slot], phase, kWaitBudget);
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
         atomicExch(err, 1);
         // let copies still in flight land before the CTA's shared memory is released
-        mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), kWaitBudget);
-        if (bi + 1 < nblk) mbar_wait_bounded(&bar[(bi + 1) & 1], (uint32_t)(((bi + 1) >> 1) & 1), kWaitBudget);
+        for (int k = bi; k < bi + nst && k < nblk; ++k)
+          mbar_wait_bounded(&bar[k % nst], (uint32_t)((k / nst) & 1), kWaitBudget);
       }
       __syncthreads();
       return;
     }
-    // off-block products: tile rows warp*RB .. warp*RB + RB - 1 times the solution window
-    int s0 = (int)(tile_origin(kFwd, i0, b) % R);
-    if (s0 < 0) s0 += R;  // even: the origin and R are even, so window chunks are 16-byte aligned
-    const float* Trow = tbuf(bi & 1) + (size_t)(warp * RB) * W;
+    // off-block products: tile rows warp*RB .. warp*RB + RB - 1 times the solution window,
+    // ring slots s0 .. s0 + W - 1 (s0 even, so the window's 16-byte chunks are aligned)
+    const float* Trow = tdst(slot) + (size_t)(warp * RB) * W;
     float acc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = 0.f;
@@ -892,7 +896,7 @@ k_band_solve_tile(int N, int b, const float* __restrict__ tiles, const float* __
     __syncthreads();
     // diagonal block: y = D_I tb with D_I's NB x NB inverse (zero outside the triangle)
     {
-      const float* D = dbuf(bi & 1);
+      const float* D = ddst(slot);
       const int h = lane & 3;
       float y = 0.f;
 #pragma unroll
@@ -900,25 +904,46 @@ k_band_solve_tile(int N, int b, const float* __restrict__ tiles, const float* __
       y += __shfl_xor_sync(0xffffffffu, y, 1);
       y += __shfl_xor_sync(0xffffffffu, y, 2);
       if (owner && io < N) {
-        const int sl = io % R;
+        const int sl = io & ring_mask;
         ring[(size_t)sl * kCols + ocol] = y;
         ring[(size_t)(sl + R) * kCols + ocol] = y;
         if (ocol < ncl) write_out(io, cbase + ocol, y);
       }
     }
     __syncthreads();
-    // both buffers of slot bi & 1 are free again: prefetch block bi + 2 into them
-    if (t == 0 && bi + 2 < nblk) {
+    // this stage is free again: prefetch block bi + nst into it
+    if (t == 0 && bi + nst < nblk) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(bi + 2);
+      issue(bi + nst, slot);
     }
+    if (++slot == nst) {
+      slot = 0;
+      phase ^= 1u;
+    }
+    s0 = (s0 + (kFwd ? NB : -NB)) & ring_mask;
   }
 }
 
-size_t tile_smem_bytes(int b) {
-  return 64 + 2 * align16((size_t)kTileNB * band_ld(b) * sizeof(float)) +
-         2 * align16((size_t)kTileNB * kTileNB * sizeof(float)) + 2 * (size_t)ring_rows(b) * kCols * sizeof(float) +
-         (size_t)kTileNB * kCols * sizeof(float);
+// Ring rows of the tile solve: a power of two above the W + NB rows alive at once.
+int tile_ring_rows(int b) {
+  int r = 2;
+  while (r < band_ld(b) + kTileNB + 1) r <<= 1;
+  return r;
+}
+
+// Shared memory of the tile solve with nst stages.
+size_t tile_smem_bytes(int b, int nst) {
+  return 8 * kTileMaxStages +
+         nst * (align16((size_t)kTileNB * band_ld(b) * sizeof(float)) + align16((size_t)kTileNB * kTileNB * sizeof(float))) +
+         2 * (size_t)tile_ring_rows(b) * kCols * sizeof(float) + (size_t)kTileNB * kCols * sizeof(float);
+}
+
+// As many bulk-copy stages as fit in 227 KB, at most kTileMaxStages (0 if fewer than 2 fit);
+// a stage is refilled nst - 1 blocks before its use.
+int tile_stages(int b) {
+  for (int nst = kTileMaxStages; nst >= 2; --nst)
+    if (tile_smem_bytes(b, nst) <= 227 * 1024) return nst;
+  return 0;
 }
 
 template <int MODE>
@@ -929,10 +954,11 @@ static void launch_tile(biot_ctx* ctx, int N, int b, const float* tiles, const f
     cudaFuncSetAttribute(k_band_solve_tile<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr_set = true;
   }
-  const int rr = ring_rows(b);
-  const size_t smem = tile_smem_bytes(b);
+  const int nst = tile_stages(b);
+  const size_t smem = tile_smem_bytes(b, nst);
   BIOT_LAUNCH(k_band_solve_tile<MODE>, div_up(ncols, kCols), kTileThreads, smem, ctx->stream, N, b, tiles, Dnb, vin,
-              ctx->dsq, ctx->lp.tu, ctx->lp.tp, z, ctx->wcap, c0, ncols, rr - 1, ctx->status);
+              ctx->dsq, ctx->lp.tu, ctx->lp.tp, z, ctx->wcap, c0, ncols, tile_ring_rows(b) - 1, nst,
+              ctx->status);
 }
 
 template <int MODE, typename T>
@@ -959,6 +985,7 @@ size_t band_variant_smem(int v, bool fp64, int b) {
   const BandVariant& V = kBandVariants[v];
   const size_t es = fp64 ? 8 : 4;
   if (!V.tma) return es * ((size_t)ring_rows(b) * kCols + kNB * kCols);
+  if (V.tma == 2) return tile_stages(b) ? tile_smem_bytes(b, tile_stages(b)) : (size_t)1 << 30;
   return 64 + 2 * align16((size_t)V.nb * band_ld(b) * es) + 2 * align16((size_t)V.nb * V.nb * es) +
          2 * (size_t)ring_rows(b) * kCols * es + (size_t)V.nb * kCols * es;
 }
@@ -980,7 +1007,6 @@ int band_variant_default(bool fp64, int b) {
 template <int MODE, typename T>
 static void solve(biot_ctx* ctx, int variant, int N, int b, const T* band, const T* Dinv, const T* Dnb, const T* vin,
                   T* z, int c0, int ncols) {
-  KTimer tm(ctx, BIOT_KC_BAND_SOLVE);
   switch (variant) {
     case 1: launch_tma<MODE, T, 16, 128>(ctx, N, b, band, Dnb, vin, z, c0, ncols); break;
     case 2: launch_tma<MODE, T, 16, 256>(ctx, N, b, band, Dnb, vin, z, c0, ncols); break;
@@ -1037,12 +1063,39 @@ biot_status ensure_dnb(biot_ctx* ctx, bool fp64, bool u, int variant) {
 }
 
 
+// Runs the launches of its scope on ctx->side instead of ctx->stream.
+struct OnSide {
+  biot_ctx* ctx;
+  cudaStream_t keep;
+  explicit OnSide(biot_ctx* c) : ctx(c), keep(c->stream) { ctx->stream = ctx->side; }
+  ~OnSide() { ctx->stream = keep; }
+};
+
+// z = P^{-1} vin on columns [c0, c0 + ncols). The band-solve timing class brackets the
+// whole apply (four solves, plus the coupling for P1) on the caller's stream.
 template <typename T>
 void precond_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols) {
   using B = BandBufs<T>;
+  KTimer tm(ctx, BIOT_KC_BAND_SOLVE);
   const int nn = ctx->n_nodes;
   const int pi = sizeof(T) == 8 ? 0 : 1;
   const int vu = ctx->band_var_u[pi], vp = ctx->band_var_p[pi];
+  if (ctx->precond == BIOT_PRECOND_DIAG && ctx->side) {
+    // P2 is block diagonal: A's two solves (the long ones) on the high-priority side stream,
+    // S's on the caller's stream, filling the SMs that A's CTAs leave free
+    cudaEventRecord(ctx->ev_fork, ctx->stream);
+    cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+    {
+      OnSide on(ctx);
+      solve<FWD_U_FROM_V, T>(ctx, vu, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, c0, ncols);
+      solve<BWD_U_TO_Z, T>(ctx, vu, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, c0, ncols);
+    }
+    solve<FWD_P_FROM_V, T>(ctx, vp, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
+    solve<BWD_P_TO_Z, T>(ctx, vp, nn, ctx->band_p, B::Up(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
+    cudaEventRecord(ctx->ev_join, ctx->side);
+    cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
+    return;
+  }
   solve<FWD_U_FROM_V, T>(ctx, vu, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, c0, ncols);
   solve<BWD_U_TO_Z, T>(ctx, vu, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, c0, ncols);
   if (ctx->precond == BIOT_PRECOND_TRI) {

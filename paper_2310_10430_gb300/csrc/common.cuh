@@ -103,6 +103,9 @@ struct biot_ctx {
   int n = 0;
   double Lx = 1.0, Ly = 1.0;
   cudaStream_t stream = nullptr;
+  // P2's two block solves run concurrently: A's on `side` (highest priority), S's on `stream`
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int n_nodes = 0, n_dof = 0, n_pairs = 0;
   int64_t nnz = 0;
   // pattern (device)
