@@ -190,14 +190,35 @@ class ClockSampler:
 # roofline helpers
 # ---------------------------------------------------------------------------
 
-def band_solve_flops(info, ncols, precond):
-    """Algorithmic FP64 flops of the band triangular solves of one P apply
-    (forward + backward on A and on S): 2 flops per band entry per column."""
+def band_solve_flops(info, ncols, precond, strips=0):
+    """Algorithmic FP64 flops of the exact block solves of one P apply: 2 flops per band
+    entry per column of every triangular solve, tri(N, b) = 2 W (N b - b (b + 1) / 2).
+
+    Plain band factors (strips < 2): forward + backward on A (half-band 2n+5) and on S
+    (n+2). Substructured (strips >= 2, the library's layout): per block (d = 2 for A, 1 for
+    S) two forward + backward pairs on every strip interior (N_t = d w_t (n + 1) rows,
+    half-band d (w_max + 2) - 1) and one pair on the separators' Schur complement
+    ((k - 1) d (n + 1) rows, half-band 2 d (n + 1) - 1), plus the two sparse couplings
+    (2 flops per separator-interior entry per column, twice)."""
     def tri(N, b):
         return 2.0 * ncols * (N * b - b * (b + 1) / 2.0)
-    fa = tri(2 * info.n_nodes, info.band_u)
-    fs = tri(info.n_nodes, info.band_p)
-    return 2 * fa + 2 * fs, 4
+    n = round((info.n_nodes) ** 0.5) - 1
+    if strips < 2:
+        fa = tri(2 * info.n_nodes, info.band_u)
+        fs = tri(info.n_nodes, info.band_p)
+        return 2 * fa + 2 * fs, 4
+    C = n + 1
+    ni = C - (strips - 1)
+    widths = [ni // strips + (1 if t < ni % strips else 0) for t in range(strips)]
+    total = 0.0
+    for d in (2, 1):
+        bI = d * (max(widths) + 2) - 1
+        interior = sum(tri(d * w * C, bI) for w in widths)
+        NS, bS = (strips - 1) * d * C, 2 * d * C - 1
+        # each separator node couples to its 4 interior neighbours (i +- 1 columns): d*d entries each
+        coupling = 2 * 2.0 * ncols * (strips - 1) * C * 4 * d * d
+        total += 4 * interior + 2 * tri(NS, bS) + coupling
+    return total, 10
 
 
 def nvtx_push(name):
@@ -366,7 +387,8 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (band triangular solves, FP64 ALU) --
     # the band-solve timing class brackets one whole P apply (its four solve launches; for
     # P2 the solves on A and on S run concurrently on two streams)
-    flops_per_apply, launches_per_apply = band_solve_flops(info, hi - lo + 1, case.precond)
+    flops_per_apply, launches_per_apply = band_solve_flops(info, hi - lo + 1, case.precond,
+                                                           int(tuning.get("strips", 0)))
     achieved = flops_per_apply / (band_ms / band_n / 1e3) / 1e12
     traffic = profile_traffic(os.path.join(ROOT, "paper_2310_10430_gb300", "csrc", "band.cu"),
                               "k_band_solve_tma" if args.precision == "fp64" else "k_band_solve_tile")
@@ -445,7 +467,7 @@ def sweep_variant(case, precision, steps, warmup, stream):
         band_ms, band_n = biot.biot_timing_read(c.ctx, biot.BIOT_KC_BAND_SOLVE)
         biot.biot_timing_enable(c.ctx, False)
         ms = e0.elapsed_time(e1) / steps
-        fl, per = band_solve_flops(info, case.n_t, case.precond)
+        fl, per = band_solve_flops(info, case.n_t, case.precond, int(tuning.get("strips", 0)))
         ach = fl / (band_ms / band_n / 1e3) / 1e12
         return {"ms_per_step": ms, "value": case.n_dof * case.n_t / (ms / 1e3), "unit": UNIT,
                 "band_solve": {"achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "bound": "alu",

@@ -138,6 +138,19 @@ biot_status biot_assemble(biot_ctx* ctx, const biot_params* params);
  * BIOT_E_INVALID (kind), BIOT_E_CUDA (including a non-positive pivot). */
 biot_status biot_precond_setup(biot_ctx* ctx, int32_t kind);
 
+/* Exact block solves by one-level substructuring (an implementation choice; the
+ * paper leaves the inner solvers of Sec. 3.1 open). strips = 0: automatic (about 32
+ * node columns per strip, none below n = 63); 1: plain band factorisations of A and
+ * S in natural order; k >= 2: the n + 1 node columns are cut by k - 1 separator
+ * columns into k strips, each strip's interior is factored along its short side
+ * (half-band d (w + 2) - 1 for a strip w nodes wide, d = 2 for A, 1 for S), and the
+ * separators' Schur complement A_SS - A_SI A_II^{-1} A_IS (block tridiagonal, half-band
+ * 2 d (n + 1) - 1) is formed and factored on the device. The solves stay exact (block
+ * Gaussian elimination); only their cost and rounding order change. Takes effect at
+ * the next biot_precond_setup. Errors: BIOT_E_INVALID (strips < 0, or fewer than two
+ * node columns per strip: 3 strips > n + 2). */
+biot_status biot_set_substructure(biot_ctx* ctx, int32_t strips);
+
 /* Run the inverted time stepping (Alg. 3) as windowed snapshot sweeps: at sweep
  * w every active step n uses x_{n-1} and x_n from the state after sweep w-1;
  * step n becomes active at sweep n, which reproduces Alg. 3's iterates
@@ -278,6 +291,7 @@ typedef struct {
   double ms_u, ms_p;                    /* forward + backward solve pair, chosen variant */
   double ms_u_default, ms_p_default;    /* same with the default variant */
   int32_t from_cache;                   /* 1 if both choices came from the cache file */
+  int32_t strips;                       /* substructured block solves: strips (0: plain band) */
 } biot_tuning;
 
 /* Pick the band triangular-solve kernel variant (register-streamed; TMA-staged
@@ -288,7 +302,10 @@ typedef struct {
  * this context's factors at full window width, in the context's precision.
  * cache_path (nullable): JSON file of earlier choices keyed by precision, block
  * size, half-band and window; read first, rewritten with the new choices.
- * Requires biot_precond_setup. out (nullable) receives the choices and times. */
+ * Requires biot_precond_setup. out (nullable) receives the choices and times.
+ * With substructured block solves (biot_set_substructure) the variants follow
+ * from the strips' half-bands: nothing is timed, the cache is not touched, and
+ * out reports the interior variants of A and S and the strip count. */
 biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out);
 
 /* Kernel launches issued by this library since it was loaded (all contexts). */

@@ -54,7 +54,7 @@ class BiotTuning(ctypes.Structure):
         ("tma_p", ctypes.c_int32), ("nb_p", ctypes.c_int32), ("threads_p", ctypes.c_int32),
         ("ms_u", ctypes.c_double), ("ms_p", ctypes.c_double),
         ("ms_u_default", ctypes.c_double), ("ms_p_default", ctypes.c_double),
-        ("from_cache", ctypes.c_int32),
+        ("from_cache", ctypes.c_int32), ("strips", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -82,6 +82,7 @@ _SIGNATURES = {
     "biot_mesh_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P, ctypes.POINTER(_P)]),
     "biot_assemble": (ctypes.c_int, [_P, ctypes.POINTER(BiotParams)]),
     "biot_precond_setup": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "biot_set_substructure": (ctypes.c_int, [_P, ctypes.c_int32]),
     "biot_pint_solve": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int32, _I32, _D]),
     "biot_sweep": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _D]),
     "biot_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
@@ -177,6 +178,10 @@ def biot_assemble(ctx, params: BiotParams):
 
 def biot_precond_setup(ctx, kind: int):
     _check(lib().biot_precond_setup(ctx, int(kind)), ctx, "biot_precond_setup")
+
+
+def biot_set_substructure(ctx, strips: int):
+    _check(lib().biot_set_substructure(ctx, int(strips)), ctx, "biot_set_substructure")
 
 
 def biot_pint_solve(ctx, tol: float, max_outer: int, allow_not_converged: bool = False):
@@ -323,7 +328,7 @@ class Context:
     """Owns one biot_ctx built from an object with the attributes of workloads.BiotCase."""
 
     def __init__(self, case, stream=None, window: int = 0, schedule: int = BIOT_SCHED_TOL,
-                 precision: str = "fp64", precond: Optional[str] = None):
+                 precision: str = "fp64", precond: Optional[str] = None, strips: Optional[int] = None):
         self.case = case
         self.ctx = biot_mesh_create(case.n, case.Lx, case.Ly, stream)
         try:
@@ -333,6 +338,8 @@ class Context:
                                   window, schedule, _PRECISION[precision])
             biot_assemble(self.ctx, p)
             del keep
+            if strips is not None:
+                biot_set_substructure(self.ctx, strips)
             biot_precond_setup(self.ctx, _PRECOND[precond or case.precond])
         except Exception:
             biot_destroy(self.ctx)

@@ -51,13 +51,27 @@ biot_status dalloc(biot_ctx* ctx, void** p, size_t bytes) {
                 cudaGetErrorString(e));
   }
   ctx->allocs.push_back(*p);
+  ctx->alloc_bytes.push_back(bytes);
   ctx->device_bytes += (int64_t)bytes;
   return BIOT_OK;
+}
+
+void dfree(biot_ctx* ctx, void* p) {
+  if (!p) return;
+  for (size_t k = 0; k < ctx->allocs.size(); ++k)
+    if (ctx->allocs[k] == p) {
+      cudaFree(p);
+      ctx->device_bytes -= (int64_t)ctx->alloc_bytes[k];
+      ctx->allocs.erase(ctx->allocs.begin() + k);
+      ctx->alloc_bytes.erase(ctx->alloc_bytes.begin() + k);
+      return;
+    }
 }
 
 void dfree_all(biot_ctx* ctx) {
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
+  ctx->alloc_bytes.clear();
   ctx->device_bytes = 0;
 }
 
@@ -575,6 +589,14 @@ biot_status biot_precond_setup(biot_ctx* ctx, int32_t kind) {
   return BIOT_OK;
 }
 
+biot_status biot_set_substructure(biot_ctx* ctx, int32_t strips) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  if (strips < 0 || (strips >= 2 && 3 * strips > ctx->n + 2))
+    return fail(ctx, BIOT_E_INVALID, "strips = %d: need 0, 1 or 2 .. (n + 2) / 3 at n = %d", strips, ctx->n);
+  ctx->sub_req = strips;
+  return BIOT_OK;
+}
+
 biot_status biot_sweep(biot_ctx* ctx, int32_t lo, int32_t hi, double* rel_out) {
   if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
   BIOT_TRY(need_precond(ctx));
@@ -761,9 +783,25 @@ biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out) {
   const int nc = ctx->wcap;
   const int bu = ctx->band_u, bp = ctx->band_p;
   const std::string ku = tune_key(fp64, 2 * ctx->n_nodes, bu, nc), kp = tune_key(fp64, ctx->n_nodes, bp, nc);
-  std::map<std::string, int> cache = read_tune_cache(cache_path);
   biot_tuning res{};
   res.from_cache = 0;
+  if (ctx->sub[0]) {
+    // substructured block solves: the variants follow from the strips' half-bands; report them
+    const SubBlock* su = ctx->sub[0];
+    const SubBlock* sp = ctx->sub[1];
+    res.variant_u = su->varI[pi];
+    res.variant_p = sp->varI[pi];
+    res.tma_u = kBandVariants[res.variant_u].tma;
+    res.nb_u = kBandVariants[res.variant_u].nb;
+    res.threads_u = kBandVariants[res.variant_u].threads;
+    res.tma_p = kBandVariants[res.variant_p].tma;
+    res.nb_p = kBandVariants[res.variant_p].nb;
+    res.threads_p = kBandVariants[res.variant_p].threads;
+    res.strips = su->k;
+    if (out) *out = res;
+    return BIOT_OK;
+  }
+  std::map<std::string, int> cache = read_tune_cache(cache_path);
   const int def_u = band_variant_default(fp64, bu), def_p = band_variant_default(fp64, bp);
   // clean inputs for the timing runs
   const size_t es = fp64 ? 8 : 4;
@@ -831,12 +869,15 @@ const char* biot_last_error(const biot_ctx* ctx) {
 void biot_destroy(biot_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  sub_free(ctx);  // synchronises both streams: before the side stream is destroyed
   if (ctx->side) {
     cudaStreamSynchronize(ctx->side);
     cudaStreamDestroy(ctx->side);
+    ctx->side = nullptr;
   }
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  ctx->ev_fork = ctx->ev_join = nullptr;
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   dfree_all(ctx);
   delete ctx;

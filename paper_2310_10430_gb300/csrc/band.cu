@@ -30,13 +30,9 @@ namespace biot {
 namespace {
 
 constexpr int kSolveThreads = 256;
-constexpr int kNB = 64;                         // rows per block of the triangular solves
 constexpr int kKSplit = kSolveThreads / kNB;    // lanes sharing one row's band product
 constexpr int kCols = 2;                        // time steps (columns) per CTA
 
-// Leading dimension of the band rows: b + 1 entries padded to a multiple of 4, so every
-// row starts on a 16-byte boundary (vector loads, whole-block bulk copies).
-__host__ __device__ constexpr int band_ld(int b) { return (b + 1 + 3) & ~3; }
 
 __global__ void k_band_extract_u(int nn, int bu, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                  const double* __restrict__ val, double* __restrict__ Lb) {
@@ -146,7 +142,8 @@ enum SolveMode {
   FWD_P_FROM_T = 1,   // rhs_i = tp[i],                 out tp[i]
   FWD_P_FROM_V = 2,   // rhs_i = -vin[3i+2] / d,        out tp[i]
   BWD_U_TO_Z = 3,     // rhs_i = ty[i],                 out z[u-dof(i)]
-  BWD_P_TO_Z = 4      // rhs_i = tp[i],                 out z[3i+2]
+  BWD_P_TO_Z = 4,     // rhs_i = tp[i],                 out z[3i+2]
+  BWD_INPLACE = 5     // rhs_i = tp[i],                 out tp[i]
 };
 
 __device__ __forceinline__ int udof(int i) { return 3 * (i >> 1) + (i & 1); }
@@ -432,7 +429,7 @@ template <int MODE, typename T, int NB, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__ Dnb, const T* __restrict__ vin,
                  const double* __restrict__ dsq, T* __restrict__ ty, T* __restrict__ tp, T* __restrict__ z, int ld,
-                 int c0, int ncols, int ring_mask, int32_t* __restrict__ err) {
+                 int c0, int ncols, int ring_mask, int strip_rows, int32_t* __restrict__ err) {
   constexpr bool kFwd = MODE <= FWD_P_FROM_V;
   constexpr int KS = THREADS / NB;  // lanes sharing one row
   constexpr int VQ = Vec16<T>::n;   // band entries per 16-byte load
@@ -442,6 +439,14 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lb = band_ld(b);
   const int R = ring_mask + 1;   // the ring holds every row twice: slots j mod R and j mod R + R
+  if (strip_rows > 0) {
+    // strip blockIdx.y of a block-diagonal band matrix (N = strip_rows rows each, a multiple
+    // of NB): its own band rows, block inverses and rows of the in-place buffer
+    const size_t r0 = (size_t)blockIdx.y * strip_rows;
+    band += r0 * lb;
+    Dnb += r0 * NB;
+    tp += r0 * ld;
+  }
   const size_t bufb = align16((size_t)NB * lb * sizeof(T));
   constexpr size_t dbufb = align16((size_t)NB * NB * sizeof(T));
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -468,6 +473,7 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
     if (MODE == FWD_U_FROM_V) ty[(size_t)i * ld + c] = y;
     else if (MODE == FWD_P_FROM_T || MODE == FWD_P_FROM_V) tp[(size_t)i * ld + c] = y;
     else if (MODE == BWD_U_TO_Z) z[(size_t)udof(i) * ld + c] = y;
+    else if (MODE == BWD_INPLACE) tp[(size_t)i * ld + c] = y;
     else z[(size_t)(3 * i + 2) * ld + c] = y;
   };
   auto block_of = [&](int bi) { return kFwd ? bi : (nblk - 1 - bi); };
@@ -666,6 +672,7 @@ biot_status band_setup(biot_ctx* ctx, int kind) {
     BIOT_TRY(ensure_dnb(ctx, pi == 0, true, ctx->band_var_u[pi]));
     BIOT_TRY(ensure_dnb(ctx, pi == 0, false, ctx->band_var_p[pi]));
   }
+  BIOT_TRY(sub_setup(ctx));
   ctx->precond = kind;
   return BIOT_OK;
 }
@@ -697,8 +704,8 @@ template <> struct BandBufs<float> {
 };
 
 template <int MODE, typename T, int NB, int THREADS>
-static void launch_tma(biot_ctx* ctx, int N, int b, const T* band, const T* Dinv, const T* vin, T* z, int c0,
-                       int ncols) {
+static void launch_tma_raw(biot_ctx* ctx, int N, int b, const T* band, const T* Dnb, const T* vin, T* ty, T* tp, T* z,
+                           int ld, int c0, int ncols, int nstrips, int strip_rows) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_band_solve_tma<MODE, T, NB, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -707,8 +714,16 @@ static void launch_tma(biot_ctx* ctx, int N, int b, const T* band, const T* Dinv
   }
   const int rr = ring_rows(b);
   const size_t smem = tma_smem_bytes<T, NB>(b);
-  BIOT_LAUNCH((k_band_solve_tma<MODE, T, NB, THREADS>), div_up(ncols, kCols), THREADS, smem, ctx->stream, N, b, band, Dinv, vin, ctx->dsq, BandBufs<T>::tu(ctx), BandBufs<T>::tp(ctx), z, ctx->wcap,
-              c0, ncols, rr - 1, ctx->status);
+  const dim3 grid(div_up(ncols, kCols), nstrips);
+  BIOT_LAUNCH((k_band_solve_tma<MODE, T, NB, THREADS>), grid, THREADS, smem, ctx->stream, N, b, band, Dnb, vin,
+              ctx->dsq, ty, tp, z, ld, c0, ncols, rr - 1, strip_rows, ctx->status);
+}
+
+template <int MODE, typename T, int NB, int THREADS>
+static void launch_tma(biot_ctx* ctx, int N, int b, const T* band, const T* Dinv, const T* vin, T* z, int c0,
+                       int ncols) {
+  launch_tma_raw<MODE, T, NB, THREADS>(ctx, N, b, band, Dinv, vin, BandBufs<T>::tu(ctx), BandBufs<T>::tp(ctx), z,
+                                       ctx->wcap, c0, ncols, 1, 0);
 }
 
 // ---- FP32 band solves on skewed block tiles ----
@@ -1080,31 +1095,46 @@ void precond_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols) {
   const int nn = ctx->n_nodes;
   const int pi = sizeof(T) == 8 ? 0 : 1;
   const int vu = ctx->band_var_u[pi], vp = ctx->band_var_p[pi];
+  auto solve_u = [&]() {
+    if (ctx->sub[0]) {
+      sub_apply<T>(ctx, 0, vin, z, c0, ncols);
+      return;
+    }
+    solve<FWD_U_FROM_V, T>(ctx, vu, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, c0, ncols);
+    solve<BWD_U_TO_Z, T>(ctx, vu, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, c0, ncols);
+  };
+  auto solve_p = [&](bool from_t) {
+    if (ctx->sub[1]) {
+      sub_apply<T>(ctx, 1, from_t ? nullptr : vin, z, c0, ncols);
+      return;
+    }
+    if (from_t)
+      solve<FWD_P_FROM_T, T>(ctx, vp, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
+    else
+      solve<FWD_P_FROM_V, T>(ctx, vp, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
+    solve<BWD_P_TO_Z, T>(ctx, vp, nn, ctx->band_p, B::Up(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
+  };
   if (ctx->precond == BIOT_PRECOND_DIAG && ctx->side) {
-    // P2 is block diagonal: A's two solves (the long ones) on the high-priority side stream,
+    // P2 is block diagonal: A's solves (the long ones) on the high-priority side stream,
     // S's on the caller's stream, filling the SMs that A's CTAs leave free
     cudaEventRecord(ctx->ev_fork, ctx->stream);
     cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
     {
       OnSide on(ctx);
-      solve<FWD_U_FROM_V, T>(ctx, vu, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, c0, ncols);
-      solve<BWD_U_TO_Z, T>(ctx, vu, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, c0, ncols);
+      solve_u();
     }
-    solve<FWD_P_FROM_V, T>(ctx, vp, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
-    solve<BWD_P_TO_Z, T>(ctx, vp, nn, ctx->band_p, B::Up(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
+    solve_p(false);
     cudaEventRecord(ctx->ev_join, ctx->side);
     cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
     return;
   }
-  solve<FWD_U_FROM_V, T>(ctx, vu, 2 * nn, ctx->band_u, B::Lu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, c0, ncols);
-  solve<BWD_U_TO_Z, T>(ctx, vu, 2 * nn, ctx->band_u, B::Uu(ctx), B::Du(ctx), B::Dnbu(ctx), vin, z, c0, ncols);
+  solve_u();
   if (ctx->precond == BIOT_PRECOND_TRI) {
     launch_coupling<T>(ctx, z, vin, B::tp(ctx), c0, ncols);
-    solve<FWD_P_FROM_T, T>(ctx, vp, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
+    solve_p(true);
   } else {
-    solve<FWD_P_FROM_V, T>(ctx, vp, nn, ctx->band_p, B::Lp(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
+    solve_p(false);
   }
-  solve<BWD_P_TO_Z, T>(ctx, vp, nn, ctx->band_p, B::Up(ctx), B::Dp(ctx), B::Dnbp(ctx), vin, z, c0, ncols);
 }
 
 // Time one forward + backward solve pair of block u (A) or p (S) with a variant.
@@ -1172,5 +1202,58 @@ void batched_precond_apply(const InstDev* tab, int count, int j, int max_wcap, i
   BIOT_LAUNCH(kb_band_solve<BWD_P_TO_Z>, grid, kSolveThreads, smem, s, tab, j);
 }
 template void precond_apply<float>(biot_ctx*, const float*, float*, int, int);
+
+// ---- building blocks of the substructured block solves ----
+
+// Cholesky factor L of a band matrix (rows of Lb, zero beyond N), its transposed rows U and
+// the inverses of its 64 x 64 diagonal blocks.
+biot_status band_factor(biot_ctx* ctx, int N, int b, double* L, double* U, double* D) {
+  BIOT_TRY(band_cholesky(ctx, N, b, L));
+  BIOT_LAUNCH(k_band_transpose, div_up((long long)N * (b + 1), 256), 256, 0, ctx->stream, N, b, L, U);
+  BIOT_LAUNCH(k_diag_inverse, div_up(N, kNB), 256, 0, ctx->stream, N, b, L, D);
+  BIOT_CU(ctx, cudaGetLastError());
+  return BIOT_OK;
+}
+
+// In-place forward (L y = buf) or backward (L^T x = buf) solve of columns [c0, c0 + ncols)
+// of buf [rows][ld] with TMA variant `variant` (1..5). nstrips > 1: a block-diagonal band
+// matrix of nstrips strips of N rows each (N a multiple of 64), solved strip-parallel.
+template <typename T>
+void band_solve_inplace(biot_ctx* ctx, bool fwd, int variant, int N, int nstrips, int b, const T* band,
+                        const T* Dnb, T* buf, int ld, int c0, int ncols) {
+#define BIOT_INPLACE_CASE(v, NB, TH)                                                                         \
+  case v:                                                                                                    \
+    if (fwd)                                                                                                 \
+      launch_tma_raw<FWD_P_FROM_T, T, NB, TH>(ctx, N, b, band, Dnb, nullptr, nullptr, buf, nullptr, ld, c0,  \
+                                              ncols, nstrips, N);                                            \
+    else                                                                                                     \
+      launch_tma_raw<BWD_INPLACE, T, NB, TH>(ctx, N, b, band, Dnb, nullptr, nullptr, buf, nullptr, ld, c0,   \
+                                             ncols, nstrips, N);                                             \
+    break;
+  switch (variant) {
+    BIOT_INPLACE_CASE(1, 16, 128)
+    BIOT_INPLACE_CASE(2, 16, 256)
+    BIOT_INPLACE_CASE(3, 32, 256)
+    BIOT_INPLACE_CASE(4, 8, 128)
+    BIOT_INPLACE_CASE(5, 32, 128)
+    default: break;
+  }
+#undef BIOT_INPLACE_CASE
+}
+template void band_solve_inplace<double>(biot_ctx*, bool, int, int, int, int, const double*, const double*, double*,
+                                         int, int, int);
+template void band_solve_inplace<float>(biot_ctx*, bool, int, int, int, int, const float*, const float*, float*, int,
+                                        int, int);
+
+template <typename T>
+void extract_dnb_raw(biot_ctx* ctx, const T* D64, int N, int nb, T* out) {
+  BIOT_LAUNCH(k_extract_dnb<T>, 512, 256, 0, ctx->stream, D64, N, nb, out);
+}
+template void extract_dnb_raw<double>(biot_ctx*, const double*, int, int, double*);
+template void extract_dnb_raw<float>(biot_ctx*, const float*, int, int, float*);
+
+void to_f32(biot_ctx* ctx, const double* in, float* out, size_t n) {
+  BIOT_LAUNCH(k_to_f32, 1024, 256, 0, ctx->stream, in, out, n);
+}
 
 }  // namespace biot

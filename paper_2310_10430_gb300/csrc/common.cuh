@@ -98,6 +98,36 @@ struct InstDev {
 
 }  // namespace biot
 
+// Rows per block of the band solves' diagonal-block inverses (and of the legacy solve).
+constexpr int kNB = 64;
+// Leading dimension of the band rows: b + 1 entries padded to a multiple of 4, so every
+// row starts on a 16-byte boundary (vector loads, whole-block bulk copies).
+__host__ __device__ constexpr int band_ld(int b) { return (b + 1 + 3) & ~3; }
+
+// Exact solve of one preconditioner block (A: d = 2 DOFs per node, S: d = 1) by one-level
+// substructuring: k strips of node columns separated by k - 1 separator node columns
+// (substructure.cu). New order: strip interiors (strip t at rows t Ps .., x fastest within
+// the strip, padded to Ps rows with identity rows), then separators (line by line, along y).
+struct SubBlock {
+  int d = 0, k = 0;                 // DOFs per node, strips
+  int B = 0;                        // DOFs per separator line: d (n + 1)
+  int Ps = 0, NI = 0, NS = 0;       // rows per strip (multiple of 64), k Ps, (k - 1) B
+  int bI = 0, bS = 0;               // half-bands of the interior factor and of the separator Schur complement
+  int nadj = 0;                     // interior rows coupled to a separator
+  int32_t* pos = nullptr;           // [d (n+1)^2] natural block index -> new index (NI + s for separators)
+  int32_t* oldI = nullptr;          // [NI] new interior row -> natural block index (-1: padding)
+  int32_t* oldS = nullptr;          // [NS]
+  int32_t* adjI = nullptr;          // [nadj] interior rows coupled to a separator
+  double *LI = nullptr, *UI = nullptr, *DI = nullptr, *LS = nullptr, *US = nullptr, *DS = nullptr;
+  float *LIf = nullptr, *UIf = nullptr, *DIf = nullptr, *LSf = nullptr, *USf = nullptr, *DSf = nullptr;
+  void* dnbI[2] = {nullptr, nullptr};  // compact block inverses for the chosen variants [FP64, FP32]
+  void* dnbS[2] = {nullptr, nullptr};
+  int varI[2] = {0, 0}, varS[2] = {0, 0};  // TMA band-solve variants [FP64, FP32]
+  void* tI[2] = {nullptr, nullptr};       // workspaces [NI][wcap], [NI][wcap], [NS][wcap] per precision
+  void* tI2[2] = {nullptr, nullptr};
+  void* tS[2] = {nullptr, nullptr};
+};
+
 struct biot_ctx {
   // mesh
   int n = 0;
@@ -106,6 +136,10 @@ struct biot_ctx {
   // P2's two block solves run concurrently: A's on `side` (highest priority), S's on `stream`
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // substructured block solves: requested strip count (0 automatic, 1 off, >= 2 forced)
+  // and the set-up blocks [A, S] (null: plain band solves)
+  int sub_req = 0;
+  SubBlock* sub[2] = {nullptr, nullptr};
   int n_nodes = 0, n_dof = 0, n_pairs = 0;
   int64_t nnz = 0;
   // pattern (device)
@@ -167,6 +201,7 @@ struct biot_ctx {
   // bookkeeping
   int64_t device_bytes = 0;
   std::vector<void*> allocs;
+  std::vector<size_t> alloc_bytes;
   std::string err;
 };
 
@@ -185,6 +220,7 @@ struct KTimer {
 biot_status fail(biot_ctx* ctx, biot_status st, const char* fmt, ...);
 biot_status cuda_check(biot_ctx* ctx, cudaError_t e, const char* what);
 biot_status dalloc(biot_ctx* ctx, void** p, size_t bytes);
+void dfree(biot_ctx* ctx, void* p);  // one dalloc'ed block (the stream must not still use it)
 void dfree_all(biot_ctx* ctx);
 
 #define BIOT_CU(ctx, call)                                                   \
@@ -199,6 +235,20 @@ void dfree_all(biot_ctx* ctx);
   } while (0)
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ---- band.cu: building blocks shared with the substructured solves ----
+biot_status band_factor(biot_ctx* ctx, int N, int b, double* L, double* U, double* D);
+template <typename T>
+void band_solve_inplace(biot_ctx* ctx, bool fwd, int variant, int N, int nstrips, int b, const T* band,
+                        const T* Dnb, T* buf, int ld, int c0, int ncols);
+template <typename T> void extract_dnb_raw(biot_ctx* ctx, const T* D64, int N, int nb, T* out);
+void to_f32(biot_ctx* ctx, const double* in, float* out, size_t n);
+
+// ---- substructure.cu ----
+int sub_auto_strips(int n);
+biot_status sub_setup(biot_ctx* ctx);
+void sub_free(biot_ctx* ctx);
+template <typename T> void sub_apply(biot_ctx* ctx, int which, const T* vin, T* z, int c0, int ncols);
 
 // ---- assembly.cu ----
 biot_status build_pattern(biot_ctx* ctx);

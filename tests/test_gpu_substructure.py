@@ -1,0 +1,123 @@
+"""Substructured exact block solves (strips + separator Schur complement) against the oracle.
+
+The preconditioner's blocks A and S are solved exactly either by plain band Cholesky in
+natural order or, with biot_set_substructure(k), by k strips whose interiors are factored
+along their short side plus the factored Schur complement of the k - 1 separator lines.
+Both are exact, so a P^{-1} apply must match the oracle's sparse-LU block solves to within
+cond(block) * eps (1e-9 relative per field in FP64, 1e-3 with the FP32-rounded factors),
+and a converged PinT solve must match backward Euler to the FP64 parity bound 1e-10.
+The strip counts cover uneven strip widths, the narrowest legal strips (two node columns)
+and ragged windows; the automatic choice is checked at n = 64 where it substructures.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.solvers import BlockPreconditioner, field_rel_errors, seq_solve
+from oracle.system import build_system
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2310_10430_gb300 import biot  # noqa: E402
+from paper_2310_10430_gb300 import build as B  # noqa: E402
+
+B.build()
+
+
+def apply_errors(case, kind, strips, precision, ncols=4, seed=5):
+    s = build_system(case)
+    P = BlockPreconditioner(s, kind)
+    vin = np.random.default_rng(seed).standard_normal((ncols, s.n_dof))
+    with biot.Context(case, precision=precision, precond=kind, strips=strips) as c:
+        t = biot.biot_tune(c.ctx, None)
+        z = biot.biot_precond_apply(c.ctx, vin)
+    worst = 0.0
+    for k in range(ncols):
+        ref = P.apply(vin[k])
+        eu, ep = field_rel_errors(z[k][None].repeat(2, 0), ref[None].repeat(2, 0))
+        worst = max(worst, eu, ep)
+    return worst, t
+
+
+@pytest.mark.parametrize("kind", ["diag", "tri"])
+@pytest.mark.parametrize("n,strips", [(16, 2), (20, 3), (24, 4), (22, 8)])
+def test_apply_matches_oracle_fp64(kind, n, strips):
+    case = W.terzaghi_small().with_(n=n, n_t=6)
+    err, t = apply_errors(case, kind, strips, "fp64")
+    assert t.strips == strips
+    assert err < 1e-9, err
+
+
+@pytest.mark.parametrize("kind", ["diag", "tri"])
+def test_apply_matches_oracle_fp32(kind):
+    case = W.terzaghi_small().with_(n=20, n_t=5)
+    err, t = apply_errors(case, kind, 3, "fp32")
+    assert t.strips == 3
+    assert err < 1e-3, err
+
+
+def test_apply_lognormal_and_mms():
+    base = W.terzaghi_small()
+    for case in (base.with_(n=18, kappa=W.lognormal_kappa(18, sigma=1.5, seed=3), nu=0.45, n_t=3),
+                 base.with_(n=17, problem="mms", E=3.0, nu=0.25, kappa=0.7, tau=0.05, n_t=3)):
+        err, _ = apply_errors(case, "tri", 3, "fp64", ncols=3)
+        assert err < 1e-9, err
+
+
+def test_substructured_equals_plain_band():
+    case = W.terzaghi_small().with_(n=24, n_t=8)
+    vin = np.random.default_rng(9).standard_normal((8, case.n_dof))
+    out = []
+    for strips in (1, 5):
+        with biot.Context(case, strips=strips) as c:
+            out.append(biot.biot_precond_apply(c.ctx, vin))
+    eu, ep = field_rel_errors(out[1], out[0])
+    assert eu < 1e-10 and ep < 1e-10, (eu, ep)
+
+
+def test_automatic_strips_at_n64():
+    case = W.terzaghi_small().with_(n=64, n_t=3)
+    err, t = apply_errors(case, "diag", None, "fp64", ncols=3)
+    assert t.strips == 2
+    assert err < 1e-9, err
+
+
+@pytest.mark.parametrize("kind", ["diag", "tri"])
+def test_converged_solve_matches_sequential(kind):
+    case = W.terzaghi_small().with_(precond=kind, n_t=12)
+    s = build_system(case)
+    Xs = seq_solve(s)
+    with biot.Context(case, strips=3, window=5) as c:
+        st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-13, 100000)
+        X = biot.biot_get_state(c.ctx, 0, case.n_t)
+    eu, ep = field_rel_errors(X, Xs)
+    assert st == biot.BIOT_OK and eu < 1e-10 and ep < 1e-10, (eu, ep)
+    assert rel < 1e-12
+
+
+def test_mixed_precision_solve_with_strips():
+    case = W.terzaghi_small().with_(n=20, n_t=8)
+    s = build_system(case)
+    Xs = seq_solve(s)
+    with biot.Context(case, strips=3, precision="fp32") as c:
+        st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-10, 100000)
+        X = biot.biot_get_state(c.ctx, 0, case.n_t)
+    eu, ep = field_rel_errors(X, Xs)
+    assert st == biot.BIOT_OK and eu < 1e-8 and ep < 1e-8, (eu, ep)
+
+
+def test_invalid_strip_counts():
+    ctx = biot.biot_mesh_create(10)
+    try:
+        for bad in (-1, 5, 100):  # 3 k > n + 2 leaves fewer than two columns per strip
+            with pytest.raises(biot.BiotError) as e:
+                biot.biot_set_substructure(ctx, bad)
+            assert e.value.status == biot.BIOT_E_INVALID
+        for ok in (0, 1, 2, 4):
+            biot.biot_set_substructure(ctx, ok)
+    finally:
+        biot.biot_destroy(ctx)
