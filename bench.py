@@ -328,7 +328,7 @@ def run_ours(args):
     case = workload()
     stream = torch.cuda.current_stream()
     W_ = case.n_t
-    ctx = biot.Context(case, stream=stream, window=W_, precision=args.precision)
+    ctx = biot.Context(case, stream=stream, window=W_, precision=args.precision, strips=args.strips)
     info = ctx.info
     lo, hi = 1, case.n_t
     tuning = biot.biot_tune(ctx.ctx, args.tune_cache).as_dict()
@@ -585,6 +585,8 @@ def main():
                     help="skip the reduced-precision, time-to-solution and batched measurements")
     ap.add_argument("--n", type=int, default=None, help="override the mesh size (profiling runs only)")
     ap.add_argument("--nt", type=int, default=None, help="override N_t (profiling runs only)")
+    ap.add_argument("--strips", type=int, default=None,
+                    help="substructure strip count (profiling runs; default: the library's automatic choice)")
     ap.add_argument("--tune-cache", default=None,
                     help="band-solve tuning cache (JSON): read if present, written otherwise; profiling runs "
                          "use it to replay the plain run's variant choice")

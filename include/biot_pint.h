@@ -139,8 +139,8 @@ biot_status biot_assemble(biot_ctx* ctx, const biot_params* params);
 biot_status biot_precond_setup(biot_ctx* ctx, int32_t kind);
 
 /* Exact block solves by one-level substructuring (an implementation choice; the
- * paper leaves the inner solvers of Sec. 3.1 open). strips = 0: automatic (about 32
- * node columns per strip, none below n = 63); 1: plain band factorisations of A and
+ * paper leaves the inner solvers of Sec. 3.1 open). strips = 0: automatic (about 21
+ * node columns per strip, none below n = 32); 1: plain band factorisations of A and
  * S in natural order; k >= 2: the n + 1 node columns are cut by k - 1 separator
  * columns into k strips, each strip's interior is factored along its short side
  * (half-band d (w + 2) - 1 for a strip w nodes wide, d = 2 for A, 1 for S), and the
@@ -303,9 +303,11 @@ typedef struct {
  * cache_path (nullable): JSON file of earlier choices keyed by precision, block
  * size, half-band and window; read first, rewritten with the new choices.
  * Requires biot_precond_setup. out (nullable) receives the choices and times.
- * With substructured block solves (biot_set_substructure) the variants follow
- * from the strips' half-bands: nothing is timed, the cache is not touched, and
- * out reports the interior variants of A and S and the strip count. */
+ * With substructured block solves (biot_set_substructure) it times, for A and
+ * for S, every fitting TMA variant of the strip-parallel interior solves and of the
+ * separator solves instead, keeps the fastest, leaves the cache untouched, and
+ * reports the interior variants, the interior + separator pair times (ms_u, ms_p)
+ * and the strip count. */
 biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out);
 
 /* Kernel launches issued by this library since it was loaded (all contexts). */

@@ -786,9 +786,14 @@ biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out) {
   biot_tuning res{};
   res.from_cache = 0;
   if (ctx->sub[0]) {
-    // substructured block solves: the variants follow from the strips' half-bands; report them
+    // substructured block solves: time the interior and separator variants of A and S
+    double ms[2] = {0.0, 0.0};
+    BIOT_TRY(sub_tune(ctx, ms));
+    BIOT_TRY(device_status(ctx));
     const SubBlock* su = ctx->sub[0];
     const SubBlock* sp = ctx->sub[1];
+    res.ms_u = ms[0];
+    res.ms_p = ms[1];
     res.variant_u = su->varI[pi];
     res.variant_p = sp->varI[pi];
     res.tma_u = kBandVariants[res.variant_u].tma;

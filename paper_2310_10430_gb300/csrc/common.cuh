@@ -249,6 +249,7 @@ int sub_auto_strips(int n);
 biot_status sub_setup(biot_ctx* ctx);
 void sub_free(biot_ctx* ctx);
 template <typename T> void sub_apply(biot_ctx* ctx, int which, const T* vin, T* z, int c0, int ncols);
+biot_status sub_tune(biot_ctx* ctx, double* ms);
 
 // ---- assembly.cu ----
 biot_status build_pattern(biot_ctx* ctx);

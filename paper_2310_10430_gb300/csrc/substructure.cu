@@ -353,10 +353,11 @@ biot_status setup_block(biot_ctx* ctx, int k, SubBlock*& out) {
   BIOT_TRY(band_factor(ctx, sb->NI, sb->bI, sb->LI, sb->UI, sb->DI));
   BIOT_CU(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), st));
   // variants: interior strips solved strip-parallel, separators as one band
-  sb->varI[0] = pick_variant(true, sb->bI, {2, 1, 3, 5, 4});
-  sb->varS[0] = pick_variant(true, sb->bS, {2, 1, 4});
-  sb->varI[1] = pick_variant(false, sb->bI, {3, 2, 1, 5, 4});
-  sb->varS[1] = pick_variant(false, sb->bS, {3, 2, 1, 4});
+  // defaults (biot_tune re-times them): 128-thread CTAs for the many small strip solves
+  sb->varI[0] = pick_variant(true, sb->bI, {5, 1, 2, 3, 4});
+  sb->varS[0] = pick_variant(true, sb->bS, {5, 1, 2, 4});
+  sb->varI[1] = pick_variant(false, sb->bI, {5, 3, 1, 2, 4});
+  sb->varS[1] = pick_variant(false, sb->bS, {5, 3, 1, 2, 4});
   if (sb->varI[0] < 0 || sb->varS[0] < 0 || sb->varI[1] < 0 || sb->varS[1] < 0)
     return fail(ctx, BIOT_E_INVALID, "substructure: no band-solve variant fits half-bands %d / %d", sb->bI, sb->bS);
   const int nbI = kBandVariants[sb->varI[0]].nb;
@@ -491,10 +492,10 @@ biot_status ensure_workspace(biot_ctx* ctx, SubBlock* sb) {
 
 }  // namespace
 
-// Strips for an n x n mesh when the caller leaves the choice open: about 32 node columns per
-// strip (measured fastest at n = 256), none below n = 63.
+// Strips for an n x n mesh when the caller leaves the choice open: about 21 node columns per
+// strip (k = 12 at n = 256, the fastest of k = 4 .. 24 in FP64 and in FP32), none below n = 32.
 int sub_auto_strips(int n) {
-  const int k = (n + 1) / 32;
+  const int k = (n + 1 + 10) / 21;
   return k >= 2 ? k : 1;
 }
 
@@ -546,5 +547,85 @@ void sub_apply(biot_ctx* ctx, int which, const T* vin, T* z, int c0, int ncols) 
 }
 template void sub_apply<double>(biot_ctx*, int, const double*, double*, int, int);
 template void sub_apply<float>(biot_ctx*, int, const float*, float*, int, int);
+
+namespace {
+
+// Forward + backward in-place solve pair of a substructured block's interiors (all strips)
+// or separators, on its workspace at full window width; best of two timed repetitions.
+template <typename T>
+float time_sub_pair(biot_ctx* ctx, SubBlock* sb, bool interior, int v) {
+  using F = SubFactors<T>;
+  constexpr int pi = F::pi;
+  const int N = interior ? sb->Ps : sb->NS, nst = interior ? sb->k : 1, b = interior ? sb->bI : sb->bS;
+  const T* L = interior ? F::LI(sb) : F::LS(sb);
+  const T* U = interior ? F::UI(sb) : F::US(sb);
+  const T* dnb = (const T*)(interior ? sb->dnbI[pi] : sb->dnbS[pi]);
+  T* buf = (T*)(interior ? sb->tI[pi] : sb->tS[pi]);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, ctx->stream);
+    band_solve_inplace<T>(ctx, true, v, N, nst, b, L, dnb, buf, ctx->wcap, 0, ctx->wcap);
+    band_solve_inplace<T>(ctx, false, v, N, nst, b, U, dnb, buf, ctx->wcap, 0, ctx->wcap);
+    cudaEventRecord(e1, ctx->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+template <typename T>
+void set_dnb(biot_ctx* ctx, SubBlock* sb, bool interior, int v) {
+  constexpr int pi = SubFactors<T>::pi;
+  const T* D = (const T*)(interior ? (pi ? (const void*)sb->DIf : (const void*)sb->DI)
+                                   : (pi ? (const void*)sb->DSf : (const void*)sb->DS));
+  extract_dnb_raw<T>(ctx, D, interior ? sb->NI : sb->NS, kBandVariants[v].nb,
+                     (T*)(interior ? sb->dnbI[pi] : sb->dnbS[pi]));
+}
+
+template <typename T>
+float tune_part(biot_ctx* ctx, SubBlock* sb, bool interior) {
+  constexpr int pi = SubFactors<T>::pi;
+  const bool fp64 = pi == 0;
+  int& var = interior ? sb->varI[pi] : sb->varS[pi];
+  const int b = interior ? sb->bI : sb->bS;
+  float tbest = time_sub_pair<T>(ctx, sb, interior, var);
+  int best = var;
+  for (int v = 1; v < kBandVariantCount; ++v) {
+    if (v == var || kBandVariants[v].tma != 1 || !band_variant_ok(v, fp64, b)) continue;
+    set_dnb<T>(ctx, sb, interior, v);
+    const float t = time_sub_pair<T>(ctx, sb, interior, v);
+    if (t < tbest) {
+      tbest = t;
+      best = v;
+    }
+  }
+  var = best;
+  set_dnb<T>(ctx, sb, interior, best);
+  return tbest;
+}
+
+}  // namespace
+
+// Times every fitting TMA variant for the strip interiors and for the separators of A and
+// S and keeps the fastest; ms[0], ms[1]: the chosen interior + separator pair times of A, S.
+biot_status sub_tune(biot_ctx* ctx, double* ms) {
+  const bool fp64 = ctx->prm.precision == BIOT_FP64;
+  for (int w = 0; w < 2; ++w) {
+    SubBlock* sb = ctx->sub[w];
+    ms[w] = 0.0;
+    if (!sb) continue;
+    ms[w] += fp64 ? tune_part<double>(ctx, sb, true) : tune_part<float>(ctx, sb, true);
+    if (sb->NS > 0) ms[w] += fp64 ? tune_part<double>(ctx, sb, false) : tune_part<float>(ctx, sb, false);
+  }
+  BIOT_CU(ctx, cudaGetLastError());
+  return BIOT_OK;
+}
 
 }  // namespace biot
