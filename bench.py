@@ -218,7 +218,8 @@ def band_solve_flops(info, ncols, precond, strips=0):
         # each separator node couples to its 4 interior neighbours (i +- 1 columns): d*d entries each
         coupling = 2 * 2.0 * ncols * (strips - 1) * C * 4 * d * d
         total += 4 * interior + 2 * tri(NS, bS) + coupling
-    return total, 10
+    # launches per block: gather, 2 x interior pair, separator pair, 2 couplings, scatter
+    return total, 20
 
 
 def nvtx_push(name):
@@ -399,7 +400,7 @@ def run_ours(args):
                 "frac": achieved / peak,
                 "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (FP64 not in MEASURED_PEAKS.json)"
                                 if fp64 else "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz"),
-                "traffic": traffic, "traffic_per": "band-solve launch (mean of the four launches of one apply)",
+                "traffic": traffic, "traffic_per": "k_band_solve_tma launch (mean of the captured launches of one apply)",
                 "applies": band_n, "launches_per_apply": launches_per_apply,
                 "avg_apply_ms": band_ms / band_n, "avg_launch_ms": band_ms / band_n / launches_per_apply,
                 "share_of_step": band_ms / ms}
