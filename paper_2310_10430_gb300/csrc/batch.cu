@@ -68,6 +68,10 @@ InstDev describe(biot_ctx* c) {
   I.Lp = c->lp.Lp;
   I.Up = c->lp.Up;
   I.Dp = c->lp.Dp;
+  I.dsq = c->dsq;
+  I.dnbu = c->lp.bdnb[0];
+  I.dnbp = c->lp.bdnb[1];
+  I.status = c->status;
   I.part = c->part;
   I.colscal = c->colscal;
   I.H = c->H;
@@ -106,7 +110,12 @@ extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, do
     max_ndof = std::max(max_ndof, ctxs[i]->n_dof);
     max_band = std::max(max_band, std::max(ctxs[i]->band_u, ctxs[i]->band_p));
   }
-  for (int i = 0; i < count; ++i) BIOT_CU(ctxs[i], cudaStreamSynchronize(ctxs[i]->stream));
+  if (batched_solve_smem(max_band) > 227 * 1024)
+    return fail(c0, BIOT_E_INVALID, "biot_batch_solve: half-band %d too wide for the batched band solve", max_band);
+  for (int i = 0; i < count; ++i) {
+    BIOT_TRY(ensure_batch_dnb(ctxs[i]));
+    BIOT_CU(ctxs[i], cudaStreamSynchronize(ctxs[i]->stream));
+  }
 
   cudaStream_t s = nullptr;
   InstDev* tab_d = nullptr;

@@ -57,6 +57,8 @@ struct LowPrec {
   float* Dp = nullptr;
   float* tile[2][2] = {};        // [u, p][forward, backward]: skewed block tiles of the band solve
   int tile_ok[2] = {0, 0};       // tiles of [u, p] built from the current factors
+  float* bdnb[2] = {nullptr, nullptr};  // [u, p] compact block inverses for the batched solve
+  int bdnb_ok = 0;
 };
 
 // One instance of a batch, as the batched kernels see it (device-resident table).
@@ -89,6 +91,10 @@ struct InstDev {
   const float* Lp;
   const float* Up;
   const float* Dp;
+  const double* dsq;
+  const float* dnbu;    // compact 32 x 32 block inverses of A's and S's FP32 factors
+  const float* dnbp;
+  int32_t* status;      // the instance context's device error flag
   double* part;
   double* colscal;
   double* H;
@@ -298,6 +304,8 @@ template <typename T> biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, in
 void launch_batched_residual(const InstDev* tab, int count, cudaStream_t s);
 void launch_batched_spmm(const InstDev* tab, int count, bool bf16, int j, cudaStream_t s);
 void launch_batched_coupling(const InstDev* tab, int count, int j, cudaStream_t s);
+size_t batched_solve_smem(int max_band);  // dynamic shared memory of the batched band solve
+biot_status ensure_batch_dnb(biot_ctx* ctx);  // FP32 block inverses in the batched solve's block size
 void batched_precond_apply(const InstDev* tab, int count, int j, int max_wcap, int max_band, bool tri,
                            cudaStream_t s);
 void batched_fgmres_cycle(const InstDev* tab, int count, int n_iter, int max_wcap, int max_ndof, int max_band,
