@@ -315,22 +315,6 @@ __host__ __device__ inline int ring_rows(int b) {
   return r;
 }
 
-// Batched FP32 band solve: instance blockIdx.z, column pair blockIdx.x of its window,
-// Krylov vector j (V_j in, Z_j out).
-template <int MODE>
-__global__ void __launch_bounds__(kSolveThreads) kb_band_solve(const InstDev* __restrict__ tab, int j) {
-  const InstDev& I = tab[blockIdx.z];
-  if (!I.active || I.nf <= 0 || (int)blockIdx.x * kCols >= I.nf) return;
-  const size_t vs = (size_t)I.n_dof * I.wcap;
-  const bool u = (MODE == FWD_U_FROM_V || MODE == BWD_U_TO_Z);
-  const int N = u ? 2 * I.n_nodes : I.n_nodes;
-  const int b = u ? I.band_u : I.band_p;
-  const float* band = (MODE == FWD_U_FROM_V) ? I.Lu : (MODE == BWD_U_TO_Z) ? I.Uu
-                    : (MODE == BWD_P_TO_Z) ? I.Up : I.Lp;
-  const float* Dinv = u ? I.Du : I.Dp;
-  band_solve_body<MODE, float>(N, b, band, Dinv, I.V + j * vs, I.dsc, I.tu, I.tp, I.Z + j * vs, I.wcap, I.c0, I.nf,
-                               ring_rows(b) - 1);
-}
 
 // ---- TMA-staged variant --------------------------------------------------------
 // The band rows of the next block are copied into shared memory by the bulk-copy
@@ -426,10 +410,10 @@ __device__ __forceinline__ T reduce_pair(T a, T b, int part) {
 }
 
 template <int MODE, typename T, int NB, int THREADS>
-__global__ void __launch_bounds__(THREADS)
-k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__ Dnb, const T* __restrict__ vin,
-                 const double* __restrict__ dsq, T* __restrict__ ty, T* __restrict__ tp, T* __restrict__ z, int ld,
-                 int c0, int ncols, int ring_mask, int strip_rows, int32_t* __restrict__ err) {
+__device__ __forceinline__ void
+band_solve_tma_body(int N, int b, const T* __restrict__ band, const T* __restrict__ Dnb, const T* __restrict__ vin,
+                    const double* __restrict__ dsq, T* __restrict__ ty, T* __restrict__ tp, T* __restrict__ z, int ld,
+                    int c0, int ncols, int ring_mask, int strip_rows, int32_t* __restrict__ err) {
   constexpr bool kFwd = MODE <= FWD_P_FROM_V;
   constexpr int KS = THREADS / NB;  // lanes sharing one row
   constexpr int VQ = Vec16<T>::n;   // band entries per 16-byte load
@@ -590,6 +574,34 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
   }
 }
 
+template <int MODE, typename T, int NB, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__ Dnb, const T* __restrict__ vin,
+                 const double* __restrict__ dsq, T* __restrict__ ty, T* __restrict__ tp, T* __restrict__ z, int ld,
+                 int c0, int ncols, int ring_mask, int strip_rows, int32_t* __restrict__ err) {
+  band_solve_tma_body<MODE, T, NB, THREADS>(N, b, band, Dnb, vin, dsq, ty, tp, z, ld, c0, ncols, ring_mask, strip_rows,
+                                            err);
+}
+
+// Batched form (instance = blockIdx.z, FP32): the same solve on each active instance's
+// factors, compact block inverses and Krylov vector j (V_j in, Z_j out).
+constexpr int kBatchNB = 32;
+constexpr int kBatchThreads = 256;
+template <int MODE>
+__global__ void __launch_bounds__(kBatchThreads) kb_band_solve_tma(const InstDev* __restrict__ tab, int j) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!I.active || I.nf <= 0 || (int)blockIdx.x * kCols >= I.nf) return;
+  const size_t vs = (size_t)I.n_dof * I.wcap;
+  const bool u = (MODE == FWD_U_FROM_V || MODE == BWD_U_TO_Z);
+  const int N = u ? 2 * I.n_nodes : I.n_nodes;
+  const int b = u ? I.band_u : I.band_p;
+  const float* band = (MODE == FWD_U_FROM_V) ? I.Lu : (MODE == BWD_U_TO_Z) ? I.Uu : (MODE == BWD_P_TO_Z) ? I.Up : I.Lp;
+  const float* Dnb = u ? I.dnbu : I.dnbp;
+  band_solve_tma_body<MODE, float, kBatchNB, kBatchThreads>(N, b, band, Dnb, I.V + j * vs, I.dsq, I.tu, I.tp,
+                                                            I.Z + j * vs, I.wcap, I.c0, I.nf, ring_rows(b) - 1, 0,
+                                                            I.status);
+}
+
 __global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
     dst[k] = (float)src[k];
@@ -664,6 +676,7 @@ biot_status band_setup(biot_ctx* ctx, int kind) {
   }
   BIOT_CU(ctx, cudaGetLastError());
   ctx->lp.tile_ok[0] = ctx->lp.tile_ok[1] = 0;  // factors changed: rebuild the tiles on demand
+  ctx->lp.bdnb_ok = 0;
   for (int pi = 0; pi < 2; ++pi) {
     ctx->band_var_u[pi] = band_variant_default(pi == 0, bu);
     ctx->band_var_p[pi] = band_variant_default(pi == 0, bp);
@@ -1176,7 +1189,20 @@ template float time_band_pair<float>(biot_ctx*, bool, int, const float*, float*,
 
 template void precond_apply<double>(biot_ctx*, const double*, double*, int, int);
 
-size_t batched_solve_smem(int max_band) { return sizeof(float) * ((size_t)ring_rows(max_band) * kCols + kNB * kCols); }
+size_t batched_solve_smem(int max_band) { return tma_smem_bytes<float, kBatchNB>(max_band); }
+
+biot_status ensure_batch_dnb(biot_ctx* ctx) {
+  if (ctx->lp.bdnb_ok) return BIOT_OK;
+  for (int w = 0; w < 2; ++w) {
+    const int N = w == 0 ? 2 * ctx->n_nodes : ctx->n_nodes;
+    if (!ctx->lp.bdnb[w]) BIOT_TRY(dalloc(ctx, (void**)&ctx->lp.bdnb[w], sizeof(float) * ((size_t)N + 64) * 32));
+    BIOT_LAUNCH(k_extract_dnb<float>, 512, 256, 0, ctx->stream, w == 0 ? ctx->lp.Du : ctx->lp.Dp, N, kBatchNB,
+                ctx->lp.bdnb[w]);
+  }
+  BIOT_CU(ctx, cudaGetLastError());
+  ctx->lp.bdnb_ok = 1;
+  return BIOT_OK;
+}
 
 void batched_precond_apply(const InstDev* tab, int count, int j, int max_wcap, int max_band, bool tri,
                            cudaStream_t s) {
@@ -1184,22 +1210,22 @@ void batched_precond_apply(const InstDev* tab, int count, int j, int max_wcap, i
   const size_t smem = batched_solve_smem(max_band);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(kb_band_solve<FWD_U_FROM_V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(kb_band_solve<BWD_U_TO_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(kb_band_solve<FWD_P_FROM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(kb_band_solve<FWD_P_FROM_V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(kb_band_solve<BWD_P_TO_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(kb_band_solve_tma<FWD_U_FROM_V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(kb_band_solve_tma<BWD_U_TO_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(kb_band_solve_tma<FWD_P_FROM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(kb_band_solve_tma<FWD_P_FROM_V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(kb_band_solve_tma<BWD_P_TO_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr = true;
   }
-  BIOT_LAUNCH(kb_band_solve<FWD_U_FROM_V>, grid, kSolveThreads, smem, s, tab, j);
-  BIOT_LAUNCH(kb_band_solve<BWD_U_TO_Z>, grid, kSolveThreads, smem, s, tab, j);
+  BIOT_LAUNCH(kb_band_solve_tma<FWD_U_FROM_V>, grid, kBatchThreads, smem, s, tab, j);
+  BIOT_LAUNCH(kb_band_solve_tma<BWD_U_TO_Z>, grid, kBatchThreads, smem, s, tab, j);
   if (tri) {
     launch_batched_coupling(tab, count, j, s);
-    BIOT_LAUNCH(kb_band_solve<FWD_P_FROM_T>, grid, kSolveThreads, smem, s, tab, j);
+    BIOT_LAUNCH(kb_band_solve_tma<FWD_P_FROM_T>, grid, kBatchThreads, smem, s, tab, j);
   } else {
-    BIOT_LAUNCH(kb_band_solve<FWD_P_FROM_V>, grid, kSolveThreads, smem, s, tab, j);
+    BIOT_LAUNCH(kb_band_solve_tma<FWD_P_FROM_V>, grid, kBatchThreads, smem, s, tab, j);
   }
-  BIOT_LAUNCH(kb_band_solve<BWD_P_TO_Z>, grid, kSolveThreads, smem, s, tab, j);
+  BIOT_LAUNCH(kb_band_solve_tma<BWD_P_TO_Z>, grid, kBatchThreads, smem, s, tab, j);
 }
 template void precond_apply<float>(biot_ctx*, const float*, float*, int, int);
 
