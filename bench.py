@@ -392,7 +392,7 @@ def run_ours(args):
                                                            int(tuning.get("strips", 0)))
     achieved = flops_per_apply / (band_ms / band_n / 1e3) / 1e12
     traffic = profile_traffic(os.path.join(ROOT, "paper_2310_10430_gb300", "csrc", "band.cu"),
-                              "k_band_solve_tma" if args.precision == "fp64" else "k_band_solve_tile")
+                              "band_solve_tma_body") if args.precision == "fp64" else None
     fp64 = args.precision == "fp64"
     peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
     roofline = {"kernel": "k_band_solve* (%s band triangular solves of the P2 block solves)" % ("FP64" if fp64 else "FP32"),
@@ -502,7 +502,39 @@ def time_to_solution(case, stream):
         ep = float(np.linalg.norm(X[:, 2::3] - ref[:, 2::3]) / np.linalg.norm(ref[:, 2::3]))
         out[prec] = {"seconds": dt, "sweeps": sweeps, "status": biot.STATUS_NAMES[st], "rel_residual": rel,
                      "rel_err_u": eu, "rel_err_p": ep}
+    # The paper's own schedule (Alg. 3 with N_thread = M): every step gets exactly M FGMRES
+    # cycles while M steps are in flight, N_t + M - 1 sweeps of M columns each; the error
+    # against the converged solve decides which M reaches 1e-8.
+    paper = {}
+    for prec in ("fp64", "fp32"):
+        for M in (4, 6, 8, 10, 12, 16):
+            with biot.Context(case, stream=stream, precision=prec, window=M, schedule=biot.BIOT_SCHED_PAPER) as c:
+                biot.biot_tune(c.ctx, None)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, sweeps, rel = biot.biot_pint_solve(c.ctx, 0.0, 100000, allow_not_converged=True)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                X = biot.biot_get_state(c.ctx, 1, case.n_t)
+            eu, ep = _field_errors(np, X, ref)
+            paper[f"{prec}_M{M}"] = {"seconds": dt, "sweeps": sweeps, "rel_residual": rel, "rel_err_u": eu,
+                                     "rel_err_p": ep}
+    out["paper_schedule"] = paper
+    ok = {k: v for k, v in paper.items() if max(v["rel_err_u"], v["rel_err_p"]) <= 1e-8}
+    tol_ok = {k: out[k]["seconds"] for k in ("fp64", "fp32", "bf16")
+              if max(out[k]["rel_err_u"], out[k]["rel_err_p"]) <= 1e-8}
+    cands = {**{f"tol_{k}": v for k, v in tol_ok.items()}, **{f"paper_{k}": v["seconds"] for k, v in ok.items()}}
+    if cands:
+        best = min(cands, key=cands.get)
+        out["fastest_to_1e-8"] = {"run": best, "seconds": cands[best]}
     return out
+
+
+def _field_errors(np, X, ref):
+    eu = float(np.linalg.norm(X[:, 0::3] - ref[:, 0::3]) ** 2 + np.linalg.norm(X[:, 1::3] - ref[:, 1::3]) ** 2) ** 0.5
+    eu /= float(np.linalg.norm(ref[:, 0::3]) ** 2 + np.linalg.norm(ref[:, 1::3]) ** 2) ** 0.5
+    ep = float(np.linalg.norm(X[:, 2::3] - ref[:, 2::3]) / np.linalg.norm(ref[:, 2::3]))
+    return eu, ep
 
 
 def batched_vs_sequential(stream, count=16):

@@ -553,8 +553,19 @@ band_solve_tma_body(int N, int b, const T* __restrict__ band, const T* __restric
       const int r2 = w * (NB / 4) + (o >> 1), c2 = o & 1;
       const T* D = dbuf(bi & 1);
       T y = T(0);
+      if constexpr (sizeof(T) == 4) {
+        // the inverse is lower triangular: forward rows stop at k = r2, backward columns start
+        // there (skipping exact zeros leaves every sum bitwise unchanged). Measured faster in
+        // FP32; in FP64 the fully unrolled loop below keeps the latency-bound chains shorter.
+        if (kFwd) {
+          for (int k = h; k <= r2; k += P2L) y = fma(D[r2 * NB + k], tb[k * kCols + c2], y);
+        } else {
+          for (int k = r2 + ((h - r2) & (P2L - 1)); k < NB; k += P2L) y = fma(D[k * NB + r2], tb[k * kCols + c2], y);
+        }
+      } else {
 #pragma unroll
-      for (int k = h; k < NB; k += P2L) y = fma(kFwd ? D[r2 * NB + k] : D[k * NB + r2], tb[k * kCols + c2], y);
+        for (int k = h; k < NB; k += P2L) y = fma(kFwd ? D[r2 * NB + k] : D[k * NB + r2], tb[k * kCols + c2], y);
+      }
 #pragma unroll
       for (int off = 1; off < P2L; off <<= 1) y += __shfl_xor_sync(0xffffffffu, y, off);
       const int i2 = i0 + r2;
@@ -927,8 +938,11 @@ k_band_solve_tile(int N, int b, const float* __restrict__ tiles, const float* __
       const float* D = ddst(slot);
       const int h = lane & 3;
       float y = 0.f;
-#pragma unroll
-      for (int k = h; k < NB; k += 4) y = fmaf(kFwd ? D[orow * NB + k] : D[k * NB + orow], tb[k * kCols + ocol], y);
+      if (kFwd) {  // lower-triangular inverse: skip its exact zeros
+        for (int k = h; k <= orow; k += 4) y = fmaf(D[orow * NB + k], tb[k * kCols + ocol], y);
+      } else {
+        for (int k = orow + ((h - orow) & 3); k < NB; k += 4) y = fmaf(D[k * NB + orow], tb[k * kCols + ocol], y);
+      }
       y += __shfl_xor_sync(0xffffffffu, y, 1);
       y += __shfl_xor_sync(0xffffffffu, y, 2);
       if (owner && io < N) {
