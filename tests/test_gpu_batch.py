@@ -69,3 +69,21 @@ def test_batch_rejects_fp64_and_mixed_settings():
     finally:
         a.close()
         b.close()
+
+
+def test_batch_beside_substructured_contexts():
+    # instances from n = 32 on set up substructured block solves for their own sweeps; the
+    # batched solve keeps using their plain band factors and must still match the oracle
+    cases = [W.BiotCase(n=n, E=1e4, nu=0.3, alpha=1.0, kappa=W.lognormal_kappa(n, sigma=1.0, seed=1200 + n),
+                        tau=1e-2, n_t=nt, problem="terzaghi", precond="tri") for n, nt in ((40, 5), (33, 8))]
+    ctxs = [biot.Context(c, precision="fp32") for c in cases]
+    try:
+        st, sweeps, rels = biot.biot_batch_solve([c.ctx for c in ctxs], 1e-12, 50000, use_graph=True)
+        assert st == biot.BIOT_OK
+        for c, cx in zip(cases, ctxs):
+            X = biot.biot_get_state(cx.ctx, 0, c.n_t)
+            eu, ep = field_rel_errors(X, seq_solve(build_system(c)))
+            assert eu <= 1e-8 and ep <= 1e-8, (c.n, eu, ep)
+    finally:
+        for cx in ctxs:
+            cx.close()

@@ -121,3 +121,35 @@ def test_invalid_strip_counts():
             biot.biot_set_substructure(ctx, ok)
     finally:
         biot.biot_destroy(ctx)
+
+
+def test_bf16_values_with_strips_and_narrow_window():
+    case = W.terzaghi_small().with_(n=20, n_t=10)
+    s = build_system(case)
+    Xs = seq_solve(s)
+    for precision, window in (("bf16", 0), ("fp32", 3)):
+        with biot.Context(case, strips=4, precision=precision, window=window) as c:
+            st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-10, 100000)
+            X = biot.biot_get_state(c.ctx, 0, case.n_t)
+        eu, ep = field_rel_errors(X, Xs)
+        assert st == biot.BIOT_OK and eu < 1e-8 and ep < 1e-8, (precision, window, eu, ep)
+
+
+def test_resetup_switches_between_plain_and_strips():
+    # a second biot_precond_setup rebuilds (or drops) the substructure and frees the old one
+    case = W.terzaghi_small().with_(n=20, n_t=4)
+    s = build_system(case)
+    vin = np.random.default_rng(2).standard_normal((4, s.n_dof))
+    with biot.Context(case, strips=3) as c:
+        bytes0 = c.info.device_bytes
+        outs = []
+        for strips, kind in ((1, "tri"), (4, "diag"), (3, "tri")):
+            biot.biot_set_substructure(c.ctx, strips)
+            biot.biot_precond_setup(c.ctx, biot._PRECOND[kind])
+            z = biot.biot_precond_apply(c.ctx, vin)
+            P = BlockPreconditioner(s, kind)
+            err = max(max(field_rel_errors(z[k][None].repeat(2, 0), P.apply(vin[k])[None].repeat(2, 0)))
+                      for k in range(4))
+            assert err < 1e-9, (strips, kind, err)
+            outs.append(c.info.device_bytes)
+        assert outs[-1] <= bytes0 * 1.01, (bytes0, outs)  # no growth after returning to 3 strips
