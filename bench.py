@@ -414,6 +414,8 @@ def run_ours(args):
         extras["time_to_solution"] = time_to_solution(workload().with_(n=64, n_t=64, name="terzaghi_64x64_nt64"),
                                                       stream)
         extras["batched"] = batched_vs_sequential(stream)
+    if args.lognormal:
+        extras["lognormal_precisions"] = lognormal_precisions(stream, args.lognormal)
     out = None
     if rank == 0:
         cpu = cpu_baseline_subprocess(args.cpu_budget) if (world == 1 and not args.no_cpu) else None
@@ -554,6 +556,38 @@ def _field_errors(np, X, ref):
     return eu, ep
 
 
+def lognormal_precisions(stream, n_t):
+    """The lognormal-permeability workload (256^2, sigma 1, l = 0.1, seed 1234, P1): FP32 and
+    BF16-value sweeps with the FP64 residual and update against the FP64 solve, all to the same
+    FP64 residual tolerance 1e-10 with FGMRES(30); errors per field against an FP64 solve
+    converged to 1e-12. n_t bounds the run time (the full workload has N_t = 256)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2310_10430_gb300 import biot
+    case = W.lognormal_256().with_(n_t=n_t, n_iter=30, name=f"lognormal_256x256_nt{n_t}")
+    with biot.Context(case, stream=stream) as c:
+        biot.biot_tune(c.ctx, None)
+        st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-12, 100000, allow_not_converged=True)
+        ref = biot.biot_get_state(c.ctx, 1, case.n_t)
+    out = {"workload": f"{case.name}: n=256, N_t={n_t}, lognormal kappa sigma 1, P1, FGMRES(30), "
+                       "setup excluded", "reference": {"sweeps": sweeps, "rel_residual": rel,
+                                                       "status": biot.STATUS_NAMES[st]}}
+    for prec in ("fp64", "fp32", "bf16"):
+        with biot.Context(case, stream=stream, precision=prec) as c:
+            biot.biot_tune(c.ctx, None)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-10, 100000, allow_not_converged=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            X = biot.biot_get_state(c.ctx, 1, case.n_t)
+        eu, ep = _field_errors(np, X, ref)
+        out[prec] = {"seconds": dt, "sweeps": sweeps, "status": biot.STATUS_NAMES[st], "rel_residual": rel,
+                     "rel_err_u": eu, "rel_err_p": ep}
+    return out
+
+
 def batched_vs_sequential(stream, count=16):
     """Config-4-shaped instances (uneven n, N_t, nu, lognormal kappa sigma 1.5), FP32
     with FP64 refinement to 1e-10: one batched solve (CUDA graph) vs the same
@@ -635,6 +669,9 @@ def main():
                     help="skip the reduced-precision, time-to-solution and batched measurements")
     ap.add_argument("--n", type=int, default=None, help="override the mesh size (profiling runs only)")
     ap.add_argument("--nt", type=int, default=None, help="override N_t (profiling runs only)")
+    ap.add_argument("--lognormal", type=int, default=0, metavar="N_T",
+                    help="also solve the lognormal-permeability 256^2 workload with N_t = N_T in FP64, FP32 "
+                         "and BF16 values and report times and errors (off by default: minutes of GPU time)")
     ap.add_argument("--strips", type=int, default=None,
                     help="substructure strip count (profiling runs; default: the library's automatic choice)")
     ap.add_argument("--tune-cache", default=None,

@@ -192,7 +192,7 @@ __device__ __forceinline__ void band_solve_body(int N, int b, const T* __restric
              const T* __restrict__ vin, const double* __restrict__ dsc, T* __restrict__ ty,
              T* __restrict__ tp, T* __restrict__ z, int ld, int c0, int ncols, int ring_mask) {
   constexpr bool kFwd = MODE <= FWD_P_FROM_V;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);              // [(ring_mask + 1) * kCols]
   T* tb = ring + (size_t)(ring_mask + 1) * kCols;        // [kNB * kCols]
   const int cbase = c0 + blockIdx.x * kCols;

@@ -102,7 +102,7 @@ __global__ void k_gs_axpy(const T* __restrict__ V, size_t vstride, int nvec, con
 
 // dst[r][c] = src[r][c] * scale[c] (grid-stride).
 template <typename T>
-__device__ __forceinline__ void scale_cols_body(const T* __restrict__ src, T* __restrict__ dst,
+__device__ __forceinline__ void scale_cols_body(const T* src, T* dst,  // may alias (in-place scaling)
                                                 const double* __restrict__ scale, int nrows, int ld, int c0,
                                                 int ncols) {
   const long long total = (long long)nrows * ncols;
@@ -114,7 +114,7 @@ __device__ __forceinline__ void scale_cols_body(const T* __restrict__ src, T* __
 }
 
 template <typename T>
-__global__ void k_scale_cols(const T* __restrict__ src, T* __restrict__ dst, const double* __restrict__ scale,
+__global__ void k_scale_cols(const T* src, T* dst, const double* __restrict__ scale,
                              int nrows, int ld, int c0, int ncols) {
   scale_cols_body<T>(src, dst, scale, nrows, ld, c0, ncols);
 }

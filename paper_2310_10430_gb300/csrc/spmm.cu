@@ -321,11 +321,6 @@ template <> __device__ __forceinline__ const float* inst_val<float>(const InstDe
 template <> __device__ __forceinline__ const __nv_bfloat16* inst_val<__nv_bfloat16>(const InstDev& I) {
   return I.valbf;
 }
-template <typename VT> __device__ __forceinline__ const VT* inst_apval(const InstDev& I);
-template <> __device__ __forceinline__ const float* inst_apval<float>(const InstDev& I) { return I.apval; }
-template <> __device__ __forceinline__ const __nv_bfloat16* inst_apval<__nv_bfloat16>(const InstDev& I) {
-  return I.apvalbf;
-}
 
 // True residual in FP64 of the window, columns [0, nres) of the FP32 V_0 (equilibrated).
 __global__ void __launch_bounds__(kWarps * 32) kb_residual(const InstDev* __restrict__ tab) {
