@@ -304,10 +304,11 @@ typedef struct {
  * size, half-band and window; read first, rewritten with the new choices.
  * Requires biot_precond_setup. out (nullable) receives the choices and times.
  * With substructured block solves (biot_set_substructure) it times, for A and
- * for S, every fitting TMA variant of the strip-parallel interior solves and of the
- * separator solves instead, keeps the fastest, leaves the cache untouched, and
- * reports the interior variants, the interior + separator pair times (ms_u, ms_p)
- * and the strip count. */
+ * for S, every fitting in-place variant (TMA-staged split rows, or one row per lane
+ * with 1, 2 or 4 warps per CTA) of the strip-parallel interior solves and of the
+ * separator solves instead, keeps the fastest, caches the choices under keys
+ * "sub:" + precision, rows, half-band and window, and reports the interior variants,
+ * the interior + separator pair times (ms_u, ms_p) and the strip count. */
 biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out);
 
 /* Kernel launches issued by this library since it was loaded (all contexts). */

@@ -786,10 +786,15 @@ biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out) {
   biot_tuning res{};
   res.from_cache = 0;
   if (ctx->sub[0]) {
-    // substructured block solves: time the interior and separator variants of A and S
+    // substructured block solves: time the interior and separator variants of A and S (or
+    // take them from the cache, keyed "sub:" + precision, rows, half-band and window)
     double ms[2] = {0.0, 0.0};
-    BIOT_TRY(sub_tune(ctx, ms));
+    std::map<std::string, int> cache = read_tune_cache(cache_path);
+    int hits = 0;
+    BIOT_TRY(sub_tune(ctx, ms, &cache, &hits));
     BIOT_TRY(device_status(ctx));
+    res.from_cache = hits == 4 ? 1 : 0;
+    if (!res.from_cache) write_tune_cache(cache_path, cache);
     const SubBlock* su = ctx->sub[0];
     const SubBlock* sp = ctx->sub[1];
     res.ms_u = ms[0];

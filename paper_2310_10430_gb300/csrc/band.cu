@@ -24,6 +24,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace biot {
 
@@ -594,6 +595,182 @@ k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__
                                             err);
 }
 
+// ---- row-per-lane in-place band solve for narrow bands (strip interiors) ----
+//
+// Lane (r, cp) of a warp owns row r of a 16-row block and column pair cp (two of the warp's
+// four columns) and runs that row's whole off-block band product itself: no lane reductions,
+// and the block's 16 x 16 inverse costs 16 multiply-adds per column. The CTA's warps take
+// consecutive column groups and share each block's band rows (one bulk copy per row into rows
+// whose byte stride is 16 mod 32, so the 16 rows fall two by two on the bank pairs) and its
+// inverse (stored with row stride 17 for conflict-free row and column access); each warp keeps
+// its own solution ring. For small half-bands this issues far fewer FP64 instructions per
+// band entry than the split-row kernel.
+constexpr int kRowsNB = 16;
+constexpr int kRowsCols = 4;        // columns per warp
+constexpr int kRowsDs = kRowsNB + 1;  // row stride of the stored block inverses
+
+template <typename T> __host__ __device__ inline int rows_stride(int b) {
+  int s = band_ld(b);
+  if ((s * (int)sizeof(T)) % 32 == 0) s += 16 / (int)sizeof(T);
+  return s;
+}
+__host__ __device__ inline int rows_ring(int b) {
+  int r = 2;
+  while (r < b + kRowsNB + 1) r <<= 1;
+  return r;
+}
+template <typename T> size_t rows_smem_bytes(int b, int warps) {
+  const size_t bandb = align16((size_t)kRowsNB * rows_stride<T>(b) * sizeof(T));
+  const size_t dbb = align16((size_t)kRowsNB * kRowsDs * sizeof(T));
+  const size_t ring = (size_t)warps * 2 * rows_ring(b) * kRowsCols * sizeof(T);
+  const size_t tb = (size_t)warps * kRowsNB * kRowsCols * sizeof(T);
+  return 64 + 2 * bandb + 2 * dbb + ring + tb;
+}
+
+// 16 x 16 diagonal-block inverses with row stride 17, from the 64 x 64 ones.
+template <typename T>
+__global__ void k_extract_dnb17(const T* __restrict__ D64, int N, T* __restrict__ out) {
+  const int nblk = (N + kRowsNB - 1) / kRowsNB;
+  const long long tot = (long long)nblk * kRowsNB * kRowsDs;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(t / (kRowsNB * kRowsDs)), rk = (int)(t % (kRowsNB * kRowsDs));
+    const int r = rk / kRowsDs, k = rk % kRowsDs;
+    const int i0 = I * kRowsNB, o = i0 % 64;
+    out[t] = k < kRowsNB ? D64[(size_t)(i0 / 64) * 64 * 64 + (size_t)(o + r) * 64 + o + k] : T(0);
+  }
+}
+
+template <int MODE, typename T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_band_solve_rows(int N, int b, const T* __restrict__ band, const T* __restrict__ Dnb, T* __restrict__ buf, int ld,
+                  int c0, int ncols, int ring_mask, int strip_rows, int32_t* __restrict__ err) {
+  constexpr bool kFwd = MODE <= FWD_P_FROM_V;
+  constexpr int NB = kRowsNB;
+  static_assert(MODE == FWD_P_FROM_T || MODE == BWD_INPLACE, "in-place solves only");
+  using V2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lb = band_ld(b);
+  const int S = rows_stride<T>(b);
+  const int R = ring_mask + 1;
+  if (strip_rows > 0) {
+    const size_t r0 = (size_t)blockIdx.y * strip_rows;
+    band += r0 * lb;
+    Dnb += (r0 / NB) * NB * kRowsDs;
+    buf += r0 * ld;
+  }
+  const size_t bandb = align16((size_t)NB * S * sizeof(T));
+  constexpr size_t dbb = align16((size_t)NB * kRowsDs * sizeof(T));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  auto rows_at = [&](int slot) { return reinterpret_cast<T*>(smem_raw + 64 + slot * bandb); };
+  auto d_at = [&](int slot) { return reinterpret_cast<T*>(smem_raw + 64 + 2 * bandb + slot * dbb); };
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  T* rings = reinterpret_cast<T*>(smem_raw + 64 + 2 * bandb + 2 * dbb);
+  T* ring = rings + (size_t)warp * 2 * R * kRowsCols;                                 // [2R][4]
+  T* tb = rings + (size_t)WARPS * 2 * R * kRowsCols + (size_t)warp * NB * kRowsCols;  // [NB][4]
+  const int r = lane % NB, cp = lane / NB;
+  const int ca = c0 + (blockIdx.x * WARPS + warp) * kRowsCols + 2 * cp;  // the lane's columns ca, ca + 1
+  const bool v0 = ca < c0 + ncols, v1 = ca + 1 < c0 + ncols;
+  const int nblk = (N + NB - 1) / NB;
+  const uint32_t rowbytes = (uint32_t)(lb * sizeof(T));
+  constexpr uint32_t dbytes = (uint32_t)(NB * kRowsDs * sizeof(T));
+  auto block_of = [&](int bi) { return kFwd ? bi : (nblk - 1 - bi); };
+  auto issue = [&](int bi) {
+    const int I = block_of(bi), sl = bi & 1;
+    mbar_expect(&bar[sl], NB * rowbytes + dbytes);
+    for (int k = 0; k < NB; ++k) bulk_copy(rows_at(sl) + (size_t)k * S, band + ((size_t)I * NB + k) * lb, rowbytes, &bar[sl]);
+    bulk_copy(d_at(sl), Dnb + (size_t)I * NB * kRowsDs, dbytes, &bar[sl]);
+  };
+  auto read_rhs = [&](int i, T& a0, T& a1) {
+    a0 = (v0 && i < N) ? buf[(size_t)i * ld + ca] : T(0);
+    a1 = (v1 && i < N) ? buf[(size_t)i * ld + ca + 1] : T(0);
+  };
+
+  // rows outside 0..N-1 meet zero band entries: keep the ring finite
+  for (int k = lane; k < 2 * R * kRowsCols; k += 32) ring[k] = T(0);
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (t == 0) {
+    issue(0);
+    if (nblk > 1) issue(1);
+  }
+  T rn0, rn1;
+  read_rhs(block_of(0) * NB + r, rn0, rn1);
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int I = block_of(bi);
+    const int i = I * NB + r;
+    const T rh0 = rn0, rh1 = rn1;
+    if (bi + 1 < nblk) read_rhs(block_of(bi + 1) * NB + r, rn0, rn1);
+    const bool ok = mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), kWaitBudget);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicExch(err, 1);
+        // let copies still in flight land before the CTA's shared memory is released
+        mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), kWaitBudget);
+        if (bi + 1 < nblk) mbar_wait_bounded(&bar[(bi + 1) & 1], (uint32_t)(((bi + 1) >> 1) & 1), kWaitBudget);
+      }
+      __syncthreads();
+      return;
+    }
+    // off-block band product of row i: forward j = i - b + q < i0, backward j = i + q > i0 + NB - 1
+    T acc0 = T(0), acc1 = T(0);
+    if (i < N) {
+      const T* Lrow = rows_at(bi & 1) + (size_t)r * S;
+      const int qs = kFwd ? max(0, b - i) : NB - r;
+      const int qe = kFwd ? b - r : min(b, N - 1 - i) + 1;
+      const T* y = ring + (size_t)((kFwd ? (i - b) : i) & ring_mask) * kRowsCols + 2 * cp;
+#pragma unroll 4
+      for (int q = qs; q < qe; ++q) {
+        const T l = Lrow[q];
+        const V2 yy = *reinterpret_cast<const V2*>(y + (size_t)q * kRowsCols);
+        acc0 = fma(l, yy.x, acc0);
+        acc1 = fma(l, yy.y, acc1);
+      }
+    }
+    tb[r * kRowsCols + 2 * cp] = (i < N) ? rh0 - acc0 : T(0);
+    tb[r * kRowsCols + 2 * cp + 1] = (i < N) ? rh1 - acc1 : T(0);
+    __syncwarp();
+    // diagonal block: y = D_I t (D_I's inverse rows at stride 17, zero outside the triangle)
+    const T* D = d_at(bi & 1);
+    T y0 = T(0), y1 = T(0);
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      const T dv = kFwd ? D[r * kRowsDs + k] : D[k * kRowsDs + r];
+      const V2 tt = *reinterpret_cast<const V2*>(tb + k * kRowsCols + 2 * cp);
+      y0 = fma(dv, tt.x, y0);
+      y1 = fma(dv, tt.y, y1);
+    }
+    if (i < N) {
+      const int sl = i & ring_mask;
+      *reinterpret_cast<V2*>(ring + (size_t)sl * kRowsCols + 2 * cp) = V2{y0, y1};
+      *reinterpret_cast<V2*>(ring + (size_t)(sl + R) * kRowsCols + 2 * cp) = V2{y0, y1};
+      if (v0) buf[(size_t)i * ld + ca] = y0;
+      if (v1) buf[(size_t)i * ld + ca + 1] = y1;
+    }
+    __syncthreads();  // every warp is done with stage bi & 1 and with this block's tb
+    if (t == 0 && bi + 2 < nblk) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(bi + 2);
+    }
+  }
+}
+
+template <int MODE, typename T, int WARPS>
+static void launch_rows(biot_ctx* ctx, int N, int b, const T* band, const T* Dnb17, T* buf, int ld, int c0, int ncols,
+                        int nstrips) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_band_solve_rows<MODE, T, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr_set = true;
+  }
+  const dim3 grid(div_up(ncols, WARPS * kRowsCols), nstrips);
+  BIOT_LAUNCH((k_band_solve_rows<MODE, T, WARPS>), grid, WARPS * 32, rows_smem_bytes<T>(b, WARPS), ctx->stream, N, b,
+              band, Dnb17, buf, ld, c0, ncols, rows_ring(b) - 1, N, ctx->status);
+}
+
 // Batched form (instance = blockIdx.z, FP32): the same solve on each active instance's
 // factors, compact block inverses and Krylov vector j (V_j in, Z_j out).
 constexpr int kBatchNB = 32;
@@ -1021,7 +1198,8 @@ static void launch_legacy(biot_ctx* ctx, int N, int b, const T* band, const T* D
 // Band-solve variants the tuner chooses from: the register-streaming kernel, and
 // TMA-staged kernels with NB-row blocks and THREADS threads.
 const BandVariant kBandVariants[kBandVariantCount] = {
-    {0, 64, 256}, {1, 16, 128}, {1, 16, 256}, {1, 32, 256}, {1, 8, 128}, {1, 32, 128}, {2, kTileNB, kTileThreads}};
+    {0, 64, 256}, {1, 16, 128}, {1, 16, 256}, {1, 32, 256}, {1, 8, 128}, {1, 32, 128}, {2, kTileNB, kTileThreads},
+    {3, kRowsNB, 32}, {3, kRowsNB, 64}, {3, kRowsNB, 128}};
 
 size_t band_variant_smem(int v, bool fp64, int b) {
   const BandVariant& V = kBandVariants[v];
@@ -1034,7 +1212,16 @@ size_t band_variant_smem(int v, bool fp64, int b) {
 
 bool band_variant_ok(int v, bool fp64, int b) {
   if (fp64 && kBandVariants[v].tma == 2) return false;  // the tile solve is FP32 only
+  if (kBandVariants[v].tma == 3) return false;          // the row-per-lane solve is in-place only
   return band_variant_smem(v, fp64, b) <= 227 * 1024;
+}
+
+bool band_variant_inplace_ok(int v, bool fp64, int b) {
+  if (kBandVariants[v].tma == 3) {
+    const int w = kBandVariants[v].threads / 32;
+    return (fp64 ? rows_smem_bytes<double>(b, w) : rows_smem_bytes<float>(b, w)) <= 227 * 1024;
+  }
+  return kBandVariants[v].tma == 1 && band_variant_ok(v, fp64, b);
 }
 
 int band_variant_default(bool fp64, int b) {
@@ -1271,6 +1458,18 @@ void band_solve_inplace(biot_ctx* ctx, bool fwd, int variant, int N, int nstrips
                                              ncols, nstrips, N);                                             \
     break;
   switch (variant) {
+    case 7:
+      if (fwd) launch_rows<FWD_P_FROM_T, T, 1>(ctx, N, b, band, Dnb, buf, ld, c0, ncols, nstrips);
+      else launch_rows<BWD_INPLACE, T, 1>(ctx, N, b, band, Dnb, buf, ld, c0, ncols, nstrips);
+      break;
+    case 8:
+      if (fwd) launch_rows<FWD_P_FROM_T, T, 2>(ctx, N, b, band, Dnb, buf, ld, c0, ncols, nstrips);
+      else launch_rows<BWD_INPLACE, T, 2>(ctx, N, b, band, Dnb, buf, ld, c0, ncols, nstrips);
+      break;
+    case 9:
+      if (fwd) launch_rows<FWD_P_FROM_T, T, 4>(ctx, N, b, band, Dnb, buf, ld, c0, ncols, nstrips);
+      else launch_rows<BWD_INPLACE, T, 4>(ctx, N, b, band, Dnb, buf, ld, c0, ncols, nstrips);
+      break;
     BIOT_INPLACE_CASE(1, 16, 128)
     BIOT_INPLACE_CASE(2, 16, 256)
     BIOT_INPLACE_CASE(3, 32, 256)
@@ -1291,6 +1490,15 @@ void extract_dnb_raw(biot_ctx* ctx, const T* D64, int N, int nb, T* out) {
 }
 template void extract_dnb_raw<double>(biot_ctx*, const double*, int, int, double*);
 template void extract_dnb_raw<float>(biot_ctx*, const float*, int, int, float*);
+
+// The compact block inverses a variant reads (the row-per-lane solve: 16 x 16 at row stride 17).
+template <typename T>
+void extract_dnb_variant(biot_ctx* ctx, int variant, const T* D64, int N, T* out) {
+  if (kBandVariants[variant].tma == 3) BIOT_LAUNCH(k_extract_dnb17<T>, 512, 256, 0, ctx->stream, D64, N, out);
+  else extract_dnb_raw<T>(ctx, D64, N, kBandVariants[variant].nb, out);
+}
+template void extract_dnb_variant<double>(biot_ctx*, int, const double*, int, double*);
+template void extract_dnb_variant<float>(biot_ctx*, int, const float*, int, float*);
 
 void to_f32(biot_ctx* ctx, const double* in, float* out, size_t n) {
   BIOT_LAUNCH(k_to_f32, 1024, 256, 0, ctx->stream, in, out, n);

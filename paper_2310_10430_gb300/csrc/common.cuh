@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -248,6 +249,7 @@ template <typename T>
 void band_solve_inplace(biot_ctx* ctx, bool fwd, int variant, int N, int nstrips, int b, const T* band,
                         const T* Dnb, T* buf, int ld, int c0, int ncols);
 template <typename T> void extract_dnb_raw(biot_ctx* ctx, const T* D64, int N, int nb, T* out);
+template <typename T> void extract_dnb_variant(biot_ctx* ctx, int variant, const T* D64, int N, T* out);
 void to_f32(biot_ctx* ctx, const double* in, float* out, size_t n);
 
 // ---- substructure.cu ----
@@ -255,7 +257,7 @@ int sub_auto_strips(int n);
 biot_status sub_setup(biot_ctx* ctx);
 void sub_free(biot_ctx* ctx);
 template <typename T> void sub_apply(biot_ctx* ctx, int which, const T* vin, T* z, int c0, int ncols);
-biot_status sub_tune(biot_ctx* ctx, double* ms);
+biot_status sub_tune(biot_ctx* ctx, double* ms, std::map<std::string, int>* cache, int* hits);
 
 // ---- assembly.cu ----
 biot_status build_pattern(biot_ctx* ctx);
@@ -279,14 +281,16 @@ template <typename T> void launch_coupling(biot_ctx* ctx, const T* z, const T* v
 
 // ---- band.cu ----
 struct BandVariant {
-  int tma;      // 1: band rows staged in shared memory by bulk copies; 2: skewed block tiles (FP32)
+  int tma;      // 1: band rows staged in shared memory by bulk copies; 2: skewed block tiles (FP32);
+                // 3: row per lane, in-place strip solves only
   int nb;       // rows per block
   int threads;  // CTA size
 };
-constexpr int kBandVariantCount = 7;
+constexpr int kBandVariantCount = 10;
 extern const BandVariant kBandVariants[kBandVariantCount];
 size_t band_variant_smem(int v, bool fp64, int b);
-bool band_variant_ok(int v, bool fp64, int b);
+bool band_variant_ok(int v, bool fp64, int b);          // usable by the natural-order block solves
+bool band_variant_inplace_ok(int v, bool fp64, int b);  // usable by the in-place (substructured) solves
 int band_variant_default(bool fp64, int b);
 template <typename T> float time_band_pair(biot_ctx* ctx, bool u, int variant, const T* vin, T* z, int ncols);
 // Build the compact diagonal-block inverses a TMA variant needs (no-op if present).

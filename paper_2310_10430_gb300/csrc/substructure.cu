@@ -22,6 +22,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -245,6 +246,12 @@ __global__ void k_sub_scatter(SubArgs a, const T* __restrict__ tI2, const T* __r
   }
 }
 
+// Offset of row r0's block in a variant's compact inverses (16 x 17 per 16 rows for the
+// row-per-lane solve, nb x nb per nb rows otherwise).
+size_t dnb_offset(int v, size_t r0) {
+  return kBandVariants[v].tma == 3 ? r0 / 16 * 16 * 17 : r0 * (size_t)kBandVariants[v].nb;
+}
+
 int grid_for(long long work) { return (int)std::min<long long>(std::max<long long>((work + 255) / 256, 1), 152 * 16); }
 
 // Strip widths and separator columns for k strips of the n + 1 node columns.
@@ -262,10 +269,10 @@ void layout(int n, int k, std::vector<int>& width, std::vector<int>& start, std:
   }
 }
 
-// Largest-block TMA variant that fits, in the given order of preference.
+// First in-place variant that fits, in the given order of preference.
 int pick_variant(bool fp64, int b, std::initializer_list<int> prefs) {
   for (int v : prefs)
-    if (band_variant_ok(v, fp64, b)) return v;
+    if (band_variant_inplace_ok(v, fp64, b)) return v;
   return -1;
 }
 
@@ -354,15 +361,14 @@ biot_status setup_block(biot_ctx* ctx, int k, SubBlock*& out) {
   BIOT_CU(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), st));
   // variants: interior strips solved strip-parallel, separators as one band
   // defaults (biot_tune re-times them): 128-thread CTAs for the many small strip solves
-  sb->varI[0] = pick_variant(true, sb->bI, {5, 1, 2, 3, 4});
+  sb->varI[0] = pick_variant(true, sb->bI, {7, 5, 1, 2, 3, 4});  // 7: row per lane, one warp per CTA
   sb->varS[0] = pick_variant(true, sb->bS, {5, 1, 2, 4});
-  sb->varI[1] = pick_variant(false, sb->bI, {5, 3, 1, 2, 4});
+  sb->varI[1] = pick_variant(false, sb->bI, {7, 5, 3, 1, 2, 4});
   sb->varS[1] = pick_variant(false, sb->bS, {5, 3, 1, 2, 4});
   if (sb->varI[0] < 0 || sb->varS[0] < 0 || sb->varI[1] < 0 || sb->varS[1] < 0)
     return fail(ctx, BIOT_E_INVALID, "substructure: no band-solve variant fits half-bands %d / %d", sb->bI, sb->bS);
-  const int nbI = kBandVariants[sb->varI[0]].nb;
   BIOT_TRY(dalloc(ctx, &sb->dnbI[0], sizeof(double) * ((size_t)sb->NI + 64) * 32));
-  extract_dnb_raw<double>(ctx, sb->DI, sb->NI, nbI, (double*)sb->dnbI[0]);
+  extract_dnb_variant<double>(ctx, sb->varI[0], sb->DI, sb->NI, (double*)sb->dnbI[0]);
   // Ssep = A_SS - A_SI A_II^{-1} A_IS, strips in groups that keep A_II^{-1} A_IS under 2 GB
   if (sb->NS > 0) {
     const int ldz = 2 * sb->B;
@@ -379,10 +385,9 @@ biot_status setup_block(biot_ctx* ctx, int k, SubBlock*& out) {
       BIOT_LAUNCH(k_sub_zrhs<D>, div_up(sb->NS, 256), 256, 0, st, a, t0, g, ctx->rowptr, ctx->col, ctx->val, Z, ldz,
                   ctx->status);
       const size_t r0 = (size_t)t0 * sb->Ps;
-      band_solve_inplace<double>(ctx, true, sb->varI[0], sb->Ps, g, sb->bI, sb->LI + r0 * ldIsz,
-                                 (const double*)sb->dnbI[0] + r0 * nbI, Z, ldz, 0, ldz);
-      band_solve_inplace<double>(ctx, false, sb->varI[0], sb->Ps, g, sb->bI, sb->UI + r0 * ldIsz,
-                                 (const double*)sb->dnbI[0] + r0 * nbI, Z, ldz, 0, ldz);
+      const double* dnb = (const double*)sb->dnbI[0] + dnb_offset(sb->varI[0], r0);
+      band_solve_inplace<double>(ctx, true, sb->varI[0], sb->Ps, g, sb->bI, sb->LI + r0 * ldIsz, dnb, Z, ldz, 0, ldz);
+      band_solve_inplace<double>(ctx, false, sb->varI[0], sb->Ps, g, sb->bI, sb->UI + r0 * ldIsz, dnb, Z, ldz, 0, ldz);
       BIOT_LAUNCH(k_sub_schur_update<D>, grid_for((long long)sb->NS * (sb->bS + 1)), 256, 0, st, a, t0, g,
                   ctx->rowptr, ctx->col, ctx->val, Z, ldz, sb->LS);
     }
@@ -394,7 +399,7 @@ biot_status setup_block(biot_ctx* ctx, int k, SubBlock*& out) {
     dfree(ctx, Z);
     BIOT_TRY(band_factor(ctx, sb->NS, sb->bS, sb->LS, sb->US, sb->DS));
     BIOT_TRY(dalloc(ctx, &sb->dnbS[0], sizeof(double) * ((size_t)sb->NS + 64) * 32));
-    extract_dnb_raw<double>(ctx, sb->DS, sb->NS, kBandVariants[sb->varS[0]].nb, (double*)sb->dnbS[0]);
+    extract_dnb_variant<double>(ctx, sb->varS[0], sb->DS, sb->NS, (double*)sb->dnbS[0]);
   }
   if (ctx->prm.precision != BIOT_FP64) {
     // reduced-precision sweeps: the exact FP64 factors rounded to FP32
@@ -405,7 +410,7 @@ biot_status setup_block(biot_ctx* ctx, int k, SubBlock*& out) {
     to_f32(ctx, sb->UI, sb->UIf, szI);
     to_f32(ctx, sb->DI, sb->DIf, dI);
     BIOT_TRY(dalloc(ctx, &sb->dnbI[1], sizeof(float) * ((size_t)sb->NI + 64) * 32));
-    extract_dnb_raw<float>(ctx, sb->DIf, sb->NI, kBandVariants[sb->varI[1]].nb, (float*)sb->dnbI[1]);
+    extract_dnb_variant<float>(ctx, sb->varI[1], sb->DIf, sb->NI, (float*)sb->dnbI[1]);
     if (sb->NS > 0) {
       BIOT_TRY(dalloc(ctx, (void**)&sb->LSf, sizeof(float) * szS));
       BIOT_TRY(dalloc(ctx, (void**)&sb->USf, sizeof(float) * szS));
@@ -414,7 +419,7 @@ biot_status setup_block(biot_ctx* ctx, int k, SubBlock*& out) {
       to_f32(ctx, sb->US, sb->USf, szS);
       to_f32(ctx, sb->DS, sb->DSf, dS);
       BIOT_TRY(dalloc(ctx, &sb->dnbS[1], sizeof(float) * ((size_t)sb->NS + 64) * 32));
-      extract_dnb_raw<float>(ctx, sb->DSf, sb->NS, kBandVariants[sb->varS[1]].nb, (float*)sb->dnbS[1]);
+      extract_dnb_variant<float>(ctx, sb->varS[1], sb->DSf, sb->NS, (float*)sb->dnbS[1]);
     }
   }
   BIOT_CU(ctx, cudaGetLastError());
@@ -585,20 +590,27 @@ void set_dnb(biot_ctx* ctx, SubBlock* sb, bool interior, int v) {
   constexpr int pi = SubFactors<T>::pi;
   const T* D = (const T*)(interior ? (pi ? (const void*)sb->DIf : (const void*)sb->DI)
                                    : (pi ? (const void*)sb->DSf : (const void*)sb->DS));
-  extract_dnb_raw<T>(ctx, D, interior ? sb->NI : sb->NS, kBandVariants[v].nb,
-                     (T*)(interior ? sb->dnbI[pi] : sb->dnbS[pi]));
+  extract_dnb_variant<T>(ctx, v, D, interior ? sb->NI : sb->NS, (T*)(interior ? sb->dnbI[pi] : sb->dnbS[pi]));
 }
 
 template <typename T>
-float tune_part(biot_ctx* ctx, SubBlock* sb, bool interior) {
+float tune_part(biot_ctx* ctx, SubBlock* sb, bool interior, std::map<std::string, int>* cache, int* hits) {
   constexpr int pi = SubFactors<T>::pi;
   const bool fp64 = pi == 0;
   int& var = interior ? sb->varI[pi] : sb->varS[pi];
   const int b = interior ? sb->bI : sb->bS;
+  char key[96];
+  snprintf(key, sizeof(key), "sub:%s:N%d:b%d:w%d", fp64 ? "fp64" : "fp32", interior ? sb->NI : sb->NS, b, ctx->wcap);
+  if (cache && cache->count(key) && band_variant_inplace_ok((*cache)[key], fp64, b)) {
+    var = (*cache)[key];
+    set_dnb<T>(ctx, sb, interior, var);
+    ++*hits;
+    return time_sub_pair<T>(ctx, sb, interior, var);
+  }
   float tbest = time_sub_pair<T>(ctx, sb, interior, var);
   int best = var;
   for (int v = 1; v < kBandVariantCount; ++v) {
-    if (v == var || kBandVariants[v].tma != 1 || !band_variant_ok(v, fp64, b)) continue;
+    if (v == var || !band_variant_inplace_ok(v, fp64, b)) continue;
     set_dnb<T>(ctx, sb, interior, v);
     const float t = time_sub_pair<T>(ctx, sb, interior, v);
     if (t < tbest) {
@@ -608,6 +620,7 @@ float tune_part(biot_ctx* ctx, SubBlock* sb, bool interior) {
   }
   var = best;
   set_dnb<T>(ctx, sb, interior, best);
+  if (cache) (*cache)[key] = best;
   return tbest;
 }
 
@@ -615,14 +628,18 @@ float tune_part(biot_ctx* ctx, SubBlock* sb, bool interior) {
 
 // Times every fitting TMA variant for the strip interiors and for the separators of A and
 // S and keeps the fastest; ms[0], ms[1]: the chosen interior + separator pair times of A, S.
-biot_status sub_tune(biot_ctx* ctx, double* ms) {
+biot_status sub_tune(biot_ctx* ctx, double* ms, std::map<std::string, int>* cache, int* hits) {
   const bool fp64 = ctx->prm.precision == BIOT_FP64;
+  *hits = 0;
   for (int w = 0; w < 2; ++w) {
     SubBlock* sb = ctx->sub[w];
     ms[w] = 0.0;
     if (!sb) continue;
-    ms[w] += fp64 ? tune_part<double>(ctx, sb, true) : tune_part<float>(ctx, sb, true);
-    if (sb->NS > 0) ms[w] += fp64 ? tune_part<double>(ctx, sb, false) : tune_part<float>(ctx, sb, false);
+    ms[w] += fp64 ? tune_part<double>(ctx, sb, true, cache, hits) : tune_part<float>(ctx, sb, true, cache, hits);
+    if (sb->NS > 0)
+      ms[w] += fp64 ? tune_part<double>(ctx, sb, false, cache, hits) : tune_part<float>(ctx, sb, false, cache, hits);
+    else
+      ++*hits;  // no separators: nothing to choose
   }
   BIOT_CU(ctx, cudaGetLastError());
   return BIOT_OK;

@@ -9,6 +9,8 @@ and a converged PinT solve must match backward Euler to the FP64 parity bound 1e
 The strip counts cover uneven strip widths, the narrowest legal strips (two node columns)
 and ragged windows; the automatic choice (about 21 node columns per strip) is checked at n = 64.
 """
+import json
+
 import numpy as np
 import pytest
 
@@ -153,3 +155,31 @@ def test_resetup_switches_between_plain_and_strips():
             assert err < 1e-9, (strips, kind, err)
             outs.append(c.info.device_bytes)
         assert outs[-1] <= bytes0 * 1.01, (bytes0, outs)  # no growth after returning to 3 strips
+
+
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-9), ("fp32", 1e-3)])
+@pytest.mark.parametrize("variant", [1, 2, 3, 5, 7, 8, 9])
+def test_each_interior_variant(tmp_path, precision, bound, variant):
+    # a tuning cache naming the interior variant forces it; separators keep the tuned choice.
+    # Keys are "sub:<precision>:N<rows>:b<half-band>:w<window>"; interiors have half-bands
+    # below n + 1, separators 2 d (n + 1) - 1 above.
+    case = W.terzaghi_small().with_(n=22, n_t=6)
+    s = build_system(case)
+    vin = np.random.default_rng(variant).standard_normal((5, s.n_dof))
+    with biot.Context(case, precision=precision, strips=4) as c:
+        probe = tmp_path / "probe.json"
+        biot.biot_tune(c.ctx, str(probe))
+        entries = json.loads(probe.read_text())["band_solve_variants"]
+        for e in entries:
+            if int(e["key"].split(":b")[1].split(":")[0]) < case.n + 1:
+                e["variant"] = variant
+        forced = tmp_path / "forced.json"  # the library reads one entry per line
+        forced.write_text('{"band_solve_variants": [\n' +
+                          "".join(f'  {{"key": "{e["key"]}", "variant": {e["variant"]}}},\n' for e in entries) + "]}\n")
+        t = biot.biot_tune(c.ctx, str(forced))
+        z = biot.biot_precond_apply(c.ctx, vin)
+    assert t.variant_u == variant and t.variant_p == variant and t.from_cache == 1
+    P = BlockPreconditioner(s, case.precond)
+    for k in range(vin.shape[0]):
+        eu, ep = field_rel_errors(z[k][None].repeat(2, 0), P.apply(vin[k])[None].repeat(2, 0))
+        assert eu < bound and ep < bound, (variant, eu, ep)
