@@ -292,8 +292,12 @@ def kernel_source_hash(src_path, kernel):
 
 def profile_traffic(kernel_src, kernel):
     """DRAM bytes per launch from a committed ncu summary whose kernel-source hash matches
-    (null once the kernel has changed since the counters were taken)."""
-    sha = kernel_source_hash(kernel_src, kernel)
+    (null once the kernel has changed since the counters were taken). `kernel` may name
+    several definitions joined by '+': their hashes are chained."""
+    parts = [kernel_source_hash(kernel_src, k) for k in kernel.split("+")]
+    sha = None if None in parts else hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
+    if len(parts) == 1:
+        sha = parts[0]
     pdir = os.path.join(ROOT, "profiles")
     if sha is None or not os.path.isdir(pdir):
         return None
@@ -392,10 +396,11 @@ def run_ours(args):
                                                            int(tuning.get("strips", 0)))
     achieved = flops_per_apply / (band_ms / band_n / 1e3) / 1e12
     traffic = profile_traffic(os.path.join(ROOT, "paper_2310_10430_gb300", "csrc", "band.cu"),
-                              "band_solve_tma_body") if args.precision == "fp64" else None
+                              "k_band_solve_rows+band_solve_tma_body") if args.precision == "fp64" else None
     fp64 = args.precision == "fp64"
     peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
-    roofline = {"kernel": "k_band_solve* (%s band triangular solves of the P2 block solves)" % ("FP64" if fp64 else "FP32"),
+    roofline = {"kernel": "k_band_solve_rows + k_band_solve_tma (%s band triangular solves of the P2 block solves)"
+                          % ("FP64" if fp64 else "FP32"),
                 "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (FP64 not in MEASURED_PEAKS.json)"
