@@ -139,8 +139,9 @@ biot_status biot_assemble(biot_ctx* ctx, const biot_params* params);
 biot_status biot_precond_setup(biot_ctx* ctx, int32_t kind);
 
 /* Exact block solves by one-level substructuring (an implementation choice; the
- * paper leaves the inner solvers of Sec. 3.1 open). strips = 0: automatic (about 21
- * node columns per strip, none below n = 32); 1: plain band factorisations of A and
+ * paper leaves the inner solvers of Sec. 3.1 open). strips = 0: automatic (about 18
+ * node columns per strip in FP64 and 13 in the reduced-precision modes; none below
+ * n = 26 and 19 respectively); 1: plain band factorisations of A and
  * S in natural order; k >= 2: the n + 1 node columns are cut by k - 1 separator
  * columns into k strips, each strip's interior is factored along its short side
  * (half-band d (w + 2) - 1 for a strip w nodes wide, d = 2 for A, 1 for S), and the

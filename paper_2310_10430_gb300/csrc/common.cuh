@@ -253,7 +253,7 @@ template <typename T> void extract_dnb_variant(biot_ctx* ctx, int variant, const
 void to_f32(biot_ctx* ctx, const double* in, float* out, size_t n);
 
 // ---- substructure.cu ----
-int sub_auto_strips(int n);
+int sub_auto_strips(int n, bool fp64);
 biot_status sub_setup(biot_ctx* ctx);
 void sub_free(biot_ctx* ctx);
 template <typename T> void sub_apply(biot_ctx* ctx, int which, const T* vin, T* z, int c0, int ncols);

@@ -360,10 +360,13 @@ biot_status setup_block(biot_ctx* ctx, int k, SubBlock*& out) {
   BIOT_TRY(band_factor(ctx, sb->NI, sb->bI, sb->LI, sb->UI, sb->DI));
   BIOT_CU(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), st));
   // variants: interior strips solved strip-parallel, separators as one band
-  // defaults (biot_tune re-times them): 128-thread CTAs for the many small strip solves
-  sb->varI[0] = pick_variant(true, sb->bI, {7, 5, 1, 2, 3, 4});  // 7: row per lane, one warp per CTA
+  // defaults (biot_tune re-times them): the row-per-lane solve (7, one warp per CTA) only when
+  // its one-warp CTAs cover every SM sub-partition, i.e. at least 4 x 152 of them (four columns
+  // each, all strips); otherwise 128-thread split-row CTAs
+  const bool many = (long long)div_up(ctx->wcap, 4) * k >= 4 * 152;
+  sb->varI[0] = many ? pick_variant(true, sb->bI, {7, 5, 1, 2, 3, 4}) : pick_variant(true, sb->bI, {5, 1, 2, 3, 4});
   sb->varS[0] = pick_variant(true, sb->bS, {5, 1, 2, 4});
-  sb->varI[1] = pick_variant(false, sb->bI, {7, 5, 3, 1, 2, 4});
+  sb->varI[1] = many ? pick_variant(false, sb->bI, {7, 5, 3, 1, 2, 4}) : pick_variant(false, sb->bI, {5, 3, 1, 2, 4});
   sb->varS[1] = pick_variant(false, sb->bS, {5, 3, 1, 2, 4});
   if (sb->varI[0] < 0 || sb->varS[0] < 0 || sb->varI[1] < 0 || sb->varS[1] < 0)
     return fail(ctx, BIOT_E_INVALID, "substructure: no band-solve variant fits half-bands %d / %d", sb->bI, sb->bS);
@@ -497,10 +500,11 @@ biot_status ensure_workspace(biot_ctx* ctx, SubBlock* sb) {
 
 }  // namespace
 
-// Strips for an n x n mesh when the caller leaves the choice open: about 21 node columns per
-// strip (k = 12 at n = 256, the fastest of k = 4 .. 24 in FP64 and in FP32), none below n = 32.
-int sub_auto_strips(int n) {
-  const int k = (n + 1 + 10) / 21;
+// Strips for an n x n mesh when the caller leaves the choice open: about 18 node columns per
+// strip in FP64 (k = 14 at n = 256, the fastest of k = 4 .. 24) and about 13 in the reduced-
+// precision sweeps (k = 20 at n = 256), none below n = 26 (FP64) or 19.
+int sub_auto_strips(int n, bool fp64) {
+  const int k = fp64 ? (n + 1 + 9) / 18 : (n + 1 + 6) / 13;
   return k >= 2 ? k : 1;
 }
 
@@ -524,7 +528,7 @@ void sub_free(biot_ctx* ctx) {
 
 biot_status sub_setup(biot_ctx* ctx) {
   sub_free(ctx);
-  int k = ctx->sub_req == 0 ? sub_auto_strips(ctx->n) : ctx->sub_req;
+  int k = ctx->sub_req == 0 ? sub_auto_strips(ctx->n, ctx->prm.precision == BIOT_FP64) : ctx->sub_req;
   if (k < 2) return BIOT_OK;
   if (3 * k > ctx->n + 2) return fail(ctx, BIOT_E_INVALID, "substructure: %d strips leave fewer than 2 node columns per strip at n = %d", k, ctx->n);
   BIOT_TRY(setup_block<2>(ctx, k, ctx->sub[0]));
