@@ -197,9 +197,11 @@ def band_solve_flops(info, ncols, precond, strips=0):
     Plain band factors (strips < 2): forward + backward on A (half-band 2n+5) and on S
     (n+2). Substructured (strips >= 2, the library's layout): per block (d = 2 for A, 1 for
     S) two forward + backward pairs on every strip interior (N_t = d w_t (n + 1) rows,
-    half-band d (w_max + 2) - 1) and one pair on the separators' Schur complement
-    ((k - 1) d (n + 1) rows, half-band 2 d (n + 1) - 1), plus the two sparse couplings
-    (2 flops per separator-interior entry per column, twice)."""
+    half-band d (w_max + 2) - 1) and one pair on the separators' Schur complement, whose
+    factor is block bidiagonal with B = d (n + 1): row rho of block m > 0 has B + rho
+    off-diagonal entries, of block 0 rho (the rest of its half-band 2B - 1 is exact zeros,
+    skipped by the solve), plus the two sparse couplings (2 flops per separator-interior
+    entry per column, twice)."""
     def tri(N, b):
         return 2.0 * ncols * (N * b - b * (b + 1) / 2.0)
     n = round((info.n_nodes) ** 0.5) - 1
@@ -214,10 +216,11 @@ def band_solve_flops(info, ncols, precond, strips=0):
     for d in (2, 1):
         bI = d * (max(widths) + 2) - 1
         interior = sum(tri(d * w * C, bI) for w in widths)
-        NS, bS = (strips - 1) * d * C, 2 * d * C - 1
+        B, nb = d * C, strips - 1
+        sep = 2.0 * ncols * (B * (B - 1) / 2.0 + (nb - 1) * (B * B + B * (B - 1) / 2.0))
         # each separator node couples to its 4 interior neighbours (i +- 1 columns): d*d entries each
         coupling = 2 * 2.0 * ncols * (strips - 1) * C * 4 * d * d
-        total += 4 * interior + 2 * tri(NS, bS) + coupling
+        total += 4 * interior + 2 * sep + coupling
     # launches per block: gather, 2 x interior pair, separator pair, 2 couplings, scatter
     return total, 20
 

@@ -414,7 +414,7 @@ template <int MODE, typename T, int NB, int THREADS>
 __device__ __forceinline__ void
 band_solve_tma_body(int N, int b, const T* __restrict__ band, const T* __restrict__ Dnb, const T* __restrict__ vin,
                     const double* __restrict__ dsq, T* __restrict__ ty, T* __restrict__ tp, T* __restrict__ z, int ld,
-                    int c0, int ncols, int ring_mask, int strip_rows, int32_t* __restrict__ err) {
+                    int c0, int ncols, int ring_mask, int strip_rows, int blk, int32_t* __restrict__ err) {
   constexpr bool kFwd = MODE <= FWD_P_FROM_V;
   constexpr int KS = THREADS / NB;  // lanes sharing one row
   constexpr int VQ = Vec16<T>::n;   // band entries per 16-byte load
@@ -511,9 +511,16 @@ band_solve_tma_body(int N, int b, const T* __restrict__ band, const T* __restric
     const T* rows = buf(bi & 1);
     T acc0 = T(0), acc1 = T(0);
     if (i < N) {
-      // off-block band entries q in [qs, qe): forward j = i - b + q < i0, backward j = i + q > i0 + NB - 1
-      const int qs = kFwd ? max(0, b - i) : NB - r;
-      const int qe = kFwd ? b - r : min(b, N - 1 - i) + 1;
+      // off-block band entries q in [qs, qe): forward j = i - b + q < i0, backward j = i + q > i0 + NB - 1.
+      // blk > 0: the factor of a block-tridiagonal matrix with blk x blk blocks, whose row i has no
+      // entries left of block i / blk - 1 (forward) and whose column i none below block i / blk + 1
+      // (backward): those band entries are exact zeros and are skipped.
+      int qs = kFwd ? max(0, b - i) : NB - r;
+      int qe = kFwd ? b - r : min(b, N - 1 - i) + 1;
+      if (blk > 0) {
+        if (kFwd) qs = max(qs, max(0, (i / blk - 1) * blk) - (i - b));
+        else qe = min(qe, (i / blk + 2) * blk - i);
+      }
       if (qs < qe) {
         const T* Lrow = rows + (size_t)r * lb;
         const int qa = qs & ~(VQ - 1);  // 16-byte aligned start
@@ -590,9 +597,9 @@ template <int MODE, typename T, int NB, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 k_band_solve_tma(int N, int b, const T* __restrict__ band, const T* __restrict__ Dnb, const T* __restrict__ vin,
                  const double* __restrict__ dsq, T* __restrict__ ty, T* __restrict__ tp, T* __restrict__ z, int ld,
-                 int c0, int ncols, int ring_mask, int strip_rows, int32_t* __restrict__ err) {
+                 int c0, int ncols, int ring_mask, int strip_rows, int blk, int32_t* __restrict__ err) {
   band_solve_tma_body<MODE, T, NB, THREADS>(N, b, band, Dnb, vin, dsq, ty, tp, z, ld, c0, ncols, ring_mask, strip_rows,
-                                            err);
+                                            blk, err);
 }
 
 // ---- row-per-lane in-place band solve for narrow bands (strip interiors) ----
@@ -787,7 +794,7 @@ __global__ void __launch_bounds__(kBatchThreads) kb_band_solve_tma(const InstDev
   const float* Dnb = u ? I.dnbu : I.dnbp;
   band_solve_tma_body<MODE, float, kBatchNB, kBatchThreads>(N, b, band, Dnb, I.V + j * vs, I.dsq, I.tu, I.tp,
                                                             I.Z + j * vs, I.wcap, I.c0, I.nf, ring_rows(b) - 1, 0,
-                                                            I.status);
+                                                            0, I.status);
 }
 
 __global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
@@ -906,7 +913,7 @@ template <> struct BandBufs<float> {
 
 template <int MODE, typename T, int NB, int THREADS>
 static void launch_tma_raw(biot_ctx* ctx, int N, int b, const T* band, const T* Dnb, const T* vin, T* ty, T* tp, T* z,
-                           int ld, int c0, int ncols, int nstrips, int strip_rows) {
+                           int ld, int c0, int ncols, int nstrips, int strip_rows, int blk = 0) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_band_solve_tma<MODE, T, NB, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -917,7 +924,7 @@ static void launch_tma_raw(biot_ctx* ctx, int N, int b, const T* band, const T* 
   const size_t smem = tma_smem_bytes<T, NB>(b);
   const dim3 grid(div_up(ncols, kCols), nstrips);
   BIOT_LAUNCH((k_band_solve_tma<MODE, T, NB, THREADS>), grid, THREADS, smem, ctx->stream, N, b, band, Dnb, vin,
-              ctx->dsq, ty, tp, z, ld, c0, ncols, rr - 1, strip_rows, ctx->status);
+              ctx->dsq, ty, tp, z, ld, c0, ncols, rr - 1, strip_rows, blk, ctx->status);
 }
 
 template <int MODE, typename T, int NB, int THREADS>
@@ -1447,15 +1454,15 @@ biot_status band_factor(biot_ctx* ctx, int N, int b, double* L, double* U, doubl
 // matrix of nstrips strips of N rows each (N a multiple of 64), solved strip-parallel.
 template <typename T>
 void band_solve_inplace(biot_ctx* ctx, bool fwd, int variant, int N, int nstrips, int b, const T* band,
-                        const T* Dnb, T* buf, int ld, int c0, int ncols) {
+                        const T* Dnb, T* buf, int ld, int c0, int ncols, int blk) {
 #define BIOT_INPLACE_CASE(v, NB, TH)                                                                         \
   case v:                                                                                                    \
     if (fwd)                                                                                                 \
       launch_tma_raw<FWD_P_FROM_T, T, NB, TH>(ctx, N, b, band, Dnb, nullptr, nullptr, buf, nullptr, ld, c0,  \
-                                              ncols, nstrips, N);                                            \
+                                              ncols, nstrips, N, blk);                                       \
     else                                                                                                     \
       launch_tma_raw<BWD_INPLACE, T, NB, TH>(ctx, N, b, band, Dnb, nullptr, nullptr, buf, nullptr, ld, c0,   \
-                                             ncols, nstrips, N);                                             \
+                                             ncols, nstrips, N, blk);                                        \
     break;
   switch (variant) {
     case 7:
@@ -1480,9 +1487,9 @@ void band_solve_inplace(biot_ctx* ctx, bool fwd, int variant, int N, int nstrips
 #undef BIOT_INPLACE_CASE
 }
 template void band_solve_inplace<double>(biot_ctx*, bool, int, int, int, int, const double*, const double*, double*,
-                                         int, int, int);
+                                         int, int, int, int);
 template void band_solve_inplace<float>(biot_ctx*, bool, int, int, int, int, const float*, const float*, float*, int,
-                                        int, int);
+                                        int, int, int);
 
 template <typename T>
 void extract_dnb_raw(biot_ctx* ctx, const T* D64, int N, int nb, T* out) {

@@ -247,7 +247,7 @@ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 biot_status band_factor(biot_ctx* ctx, int N, int b, double* L, double* U, double* D);
 template <typename T>
 void band_solve_inplace(biot_ctx* ctx, bool fwd, int variant, int N, int nstrips, int b, const T* band,
-                        const T* Dnb, T* buf, int ld, int c0, int ncols);
+                        const T* Dnb, T* buf, int ld, int c0, int ncols, int blk = 0);  // blk: see the body
 template <typename T> void extract_dnb_raw(biot_ctx* ctx, const T* D64, int N, int nb, T* out);
 template <typename T> void extract_dnb_variant(biot_ctx* ctx, int variant, const T* D64, int N, T* out);
 void to_f32(biot_ctx* ctx, const double* in, float* out, size_t n);

@@ -471,8 +471,9 @@ void apply_block(biot_ctx* ctx, SubBlock* sb, bool from_t, const T* vin, const T
     // x_S = Ssep^{-1} (r_S - A_SI z1)
     BIOT_LAUNCH((k_sub_couple_S<D, T>), grid_for((long long)sb->NS * ncols), 256, 0, st, a, ctx->rowptr, ctx->col,
                 ctx->val, tI, tS, ld, c0, ncols);
-    band_solve_inplace<T>(ctx, true, sb->varS[pi], sb->NS, 1, sb->bS, F::LS(sb), dnbS, tS, ld, c0, ncols);
-    band_solve_inplace<T>(ctx, false, sb->varS[pi], sb->NS, 1, sb->bS, F::US(sb), dnbS, tS, ld, c0, ncols);
+    // Ssep is block tridiagonal with B x B blocks: its factor's band holds exact zeros to skip
+    band_solve_inplace<T>(ctx, true, sb->varS[pi], sb->NS, 1, sb->bS, F::LS(sb), dnbS, tS, ld, c0, ncols, sb->B);
+    band_solve_inplace<T>(ctx, false, sb->varS[pi], sb->NS, 1, sb->bS, F::US(sb), dnbS, tS, ld, c0, ncols, sb->B);
     // x_I = A_II^{-1} (r_I - A_IS x_S)
     BIOT_LAUNCH((k_sub_couple_I<D, T>), grid_for((long long)sb->nadj * ncols), 256, 0, st, a, sb->adjI, sb->nadj,
                 ctx->rowptr, ctx->col, ctx->val, tS, tI2, ld, c0, ncols);
@@ -576,8 +577,9 @@ float time_sub_pair(biot_ctx* ctx, SubBlock* sb, bool interior, int v) {
   float best = 1e30f;
   for (int rep = 0; rep < 3; ++rep) {
     cudaEventRecord(e0, ctx->stream);
-    band_solve_inplace<T>(ctx, true, v, N, nst, b, L, dnb, buf, ctx->wcap, 0, ctx->wcap);
-    band_solve_inplace<T>(ctx, false, v, N, nst, b, U, dnb, buf, ctx->wcap, 0, ctx->wcap);
+    const int blk = interior ? 0 : sb->B;
+    band_solve_inplace<T>(ctx, true, v, N, nst, b, L, dnb, buf, ctx->wcap, 0, ctx->wcap, blk);
+    band_solve_inplace<T>(ctx, false, v, N, nst, b, U, dnb, buf, ctx->wcap, 0, ctx->wcap, blk);
     cudaEventRecord(e1, ctx->stream);
     cudaEventSynchronize(e1);
     float ms = 0.f;
