@@ -79,6 +79,143 @@ k_dots(const T* __restrict__ V, size_t vstride, const T* __restrict__ w, int nro
   dots_body<T>(V, vstride, w, nrows, ld, c0, ncols, part);
 }
 
+// 16-byte vectors of T (four floats or two doubles).
+template <typename T> struct KVec;
+template <> struct KVec<float> {
+  using V = float4;
+  static constexpr int n = 4;
+  __device__ __forceinline__ static void get(const V& v, float* o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  __device__ __forceinline__ static V make(const float* o) { return make_float4(o[0], o[1], o[2], o[3]); }
+};
+template <> struct KVec<double> {
+  using V = double2;
+  static constexpr int n = 2;
+  __device__ __forceinline__ static void get(const V& v, double* o) { o[0] = v.x; o[1] = v.y; }
+  __device__ __forceinline__ static V make(const double* o) { return make_double2(o[0], o[1]); }
+};
+
+// dots_body for nvec vectors in one pass: w is read once per chunk of kDotChunk vectors and
+// every access is a 16-byte vector (a lane owns VEC consecutive columns; the column range is
+// widened down to a multiple of VEC). Each column's products are summed in the same order as
+// in dots_body, so the partials are identical. Needs ld % VEC == 0 and 16-byte aligned rows.
+constexpr int kDotChunk = 8;
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_dots_vec(const T* __restrict__ V, size_t vstride, int nvec, const T* __restrict__ w, int nrows, int ld, int c0,
+           int ncols, double* __restrict__ part) {
+  using VV = typename KVec<T>::V;
+  constexpr int VEC = KVec<T>::n;
+  __shared__ double sm[8][32 * VEC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = (nrows + gridDim.x - 1) / gridDim.x;
+  const int rb = blockIdx.x * per, re = min(nrows, rb + per);
+  const int ca = c0 & ~(VEC - 1), ce = c0 + ncols;
+  for (int cb = ca; cb < ce; cb += 32 * VEC) {
+    const int c = cb + lane * VEC;
+    const bool any = c < ce;
+    for (int i0 = 0; i0 < nvec; i0 += kDotChunk) {
+      const int ni = min(kDotChunk, nvec - i0);
+      T acc[kDotChunk][VEC];
+#pragma unroll
+      for (int ii = 0; ii < kDotChunk; ++ii)
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) acc[ii][q] = T(0);
+      if (any) {
+        for (int r = rb + warp; r < re; r += 8) {
+          T wv[VEC];
+          KVec<T>::get(*reinterpret_cast<const VV*>(w + (size_t)r * ld + c), wv);
+#pragma unroll
+          for (int ii = 0; ii < kDotChunk; ++ii) {
+            if (ii < ni) {
+              T v[VEC];
+              KVec<T>::get(*reinterpret_cast<const VV*>(V + (size_t)(i0 + ii) * vstride + (size_t)r * ld + c), v);
+#pragma unroll
+              for (int q = 0; q < VEC; ++q) acc[ii][q] += v[q] * wv[q];
+            }
+          }
+        }
+      }
+      for (int ii = 0; ii < ni; ++ii) {
+        // the compiler keeps acc in registers: ii is a runtime index only in this epilogue
+#pragma unroll
+        for (int k = 0; k < kDotChunk; ++k)
+          if (k == ii)
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) sm[warp][lane * VEC + q] = (double)acc[k][q];
+        __syncthreads();
+        for (int t = threadIdx.x; t < 32 * VEC; t += blockDim.x) {
+          const int col = cb + t;
+          if (col >= c0 && col < ce) {
+            double sum = 0.0;
+            for (int u = 0; u < 8; ++u) sum += sm[u][t];
+            part[((size_t)(i0 + ii) * gridDim.x + blockIdx.x) * ld + col] = sum;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// gs_axpy_body with 16-byte accesses (same per-element arithmetic order); stores only the
+// columns in [c0, c0 + ncols).
+template <typename T>
+__global__ void k_gs_axpy_vec(const T* __restrict__ V, size_t vstride, int nvec, const double* __restrict__ h,
+                              T* __restrict__ w, int nrows, int ld, int c0, int ncols) {
+  using VV = typename KVec<T>::V;
+  constexpr int VEC = KVec<T>::n;
+  const int ca = c0 & ~(VEC - 1), ce = c0 + ncols;
+  const int ngrp = (ce - ca + VEC - 1) / VEC;
+  const long long total = (long long)nrows * ngrp;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / ngrp), c = ca + (int)(idx % ngrp) * VEC;
+    T acc[VEC];
+    KVec<T>::get(*reinterpret_cast<const VV*>(w + (size_t)r * ld + c), acc);
+    for (int i = 0; i < nvec; ++i) {
+      T v[VEC];
+      KVec<T>::get(*reinterpret_cast<const VV*>(V + (size_t)i * vstride + (size_t)r * ld + c), v);
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) acc[q] -= (T)h[(size_t)i * ld + c + q] * v[q];
+    }
+    T* wr = w + (size_t)r * ld + c;
+    if (c >= c0 && c + VEC <= ce) {
+      *reinterpret_cast<VV*>(wr) = KVec<T>::make(acc);
+    } else {
+#pragma unroll
+      for (int q = 0; q < VEC; ++q)
+        if (c + q >= c0 && c + q < ce) wr[q] = acc[q];
+    }
+  }
+}
+
+// scale_cols_body with 16-byte accesses (src may alias dst).
+template <typename T>
+__global__ void k_scale_cols_vec(const T* src, T* dst, const double* __restrict__ scale, int nrows, int ld, int c0,
+                                 int ncols) {
+  using VV = typename KVec<T>::V;
+  constexpr int VEC = KVec<T>::n;
+  const int ca = c0 & ~(VEC - 1), ce = c0 + ncols;
+  const int ngrp = (ce - ca + VEC - 1) / VEC;
+  const long long total = (long long)nrows * ngrp;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / ngrp), c = ca + (int)(idx % ngrp) * VEC;
+    T v[VEC];
+    KVec<T>::get(*reinterpret_cast<const VV*>(src + (size_t)r * ld + c), v);
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) v[q] = v[q] * (T)scale[c + q];
+    T* d = dst + (size_t)r * ld + c;
+    if (c >= c0 && c + VEC <= ce) {
+      *reinterpret_cast<VV*>(d) = KVec<T>::make(v);
+    } else {
+#pragma unroll
+      for (int q = 0; q < VEC; ++q)
+        if (c + q >= c0 && c + q < ce) d[q] = v[q];
+    }
+  }
+}
+
 // w[r][c] -= sum_i h[i][c] V_i[r][c] (grid-stride over (r, c)).
 template <typename T>
 __device__ __forceinline__ void gs_axpy_body(const T* __restrict__ V, size_t vstride, int nvec,
@@ -367,8 +504,21 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
   double* h2 = ctx->hvec + (size_t)(kMaxIter + 1) * ld;
   const int cblk = div_up(ncols, 128);
   const int eblk = std::min(div_up((long long)nd * ncols, 256), 8192);
+  // FP32: 16-byte vector kernels (memory-bound; rows of every [n_dof][ld] array must start on
+  // 16-byte boundaries). FP64: the scalar kernels, which already run at the FP64 pipe's rate
+  // (one FMA per loaded element) with more CTAs in flight; the vector forms measured slower.
+  const bool vec = sizeof(T) == 4 && ld % KVec<T>::n == 0;
+  const int vblk = std::min(div_up((long long)nd * div_up(ncols + KVec<T>::n, KVec<T>::n), 256), 8192);
+  auto scale_cols = [&](const T* src, T* dst) {
+    if (vec) BIOT_LAUNCH(k_scale_cols_vec<T>, vblk, 256, 0, s, src, dst, cs + CS_INVH * ld, nd, ld, c0, ncols);
+    else BIOT_LAUNCH(k_scale_cols<T>, eblk, 256, 0, s, src, dst, cs + CS_INVH * ld, nd, ld, c0, ncols);
+  };
+  auto dots = [&](const T* Vb, int nvec, const T* w) {
+    if (vec) BIOT_LAUNCH(k_dots_vec<T>, kRedBlocks, 256, 0, s, Vb, vs, nvec, w, nd, ld, c0, ncols, ctx->part);
+    else BIOT_LAUNCH(k_dots<T>, dim3(kRedBlocks, nvec), 256, 0, s, Vb, vs, w, nd, ld, c0, ncols, ctx->part);
+  };
   BIOT_LAUNCH(k_fgmres_init, cblk, 128, 0, s, cs, ld, c0, ncols, ctx->H, ctx->kcol);
-  BIOT_LAUNCH(k_scale_cols<T>, eblk, 256, 0, s, V, V, cs + CS_INVH * ld, nd, ld, c0, ncols);
+  scale_cols(V, V);
   for (int j = 0; j < ctx->n_iter; ++j) {
     T* Vj = V + j * vs;
     T* Zj = Z + j * vs;
@@ -377,15 +527,15 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
     reduce_partials(ctx, 1, ncols, cs + CS_WN0 * ld, ld, c0);
     for (int pass = 0; pass < 2; ++pass) {
       double* h = pass == 0 ? h1 : h2;
-      BIOT_LAUNCH(k_dots<T>, dim3(kRedBlocks, j + 1), 256, 0, s, V, vs, Wv, nd, ld, c0, ncols, ctx->part);
+      dots(V, j + 1, Wv);
       reduce_partials(ctx, j + 1, ncols, h, ld, c0);
-      BIOT_LAUNCH(k_gs_axpy<T>, eblk, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0, ncols);
+      if (vec) BIOT_LAUNCH(k_gs_axpy_vec<T>, vblk, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0, ncols);
+      else BIOT_LAUNCH(k_gs_axpy<T>, eblk, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0, ncols);
     }
-    BIOT_LAUNCH(k_dots<T>, dim3(kRedBlocks, 1), 256, 0, s, Wv, vs, Wv, nd, ld, c0, ncols, ctx->part);
+    dots(Wv, 1, Wv);
     reduce_partials(ctx, 1, ncols, cs + CS_WW * ld, ld, c0);
     BIOT_LAUNCH(k_givens, cblk, 128, 0, s, j, cs, h1, h2, ld, c0, ncols, ctx->H, ctx->kcol);
-    if (j + 1 < ctx->n_iter)
-      BIOT_LAUNCH(k_scale_cols<T>, eblk, 256, 0, s, Wv, V + (j + 1) * vs, cs + CS_INVH * ld, nd, ld, c0, ncols);
+    if (j + 1 < ctx->n_iter) scale_cols(Wv, V + (j + 1) * vs);
   }
   BIOT_LAUNCH(k_backsolve, cblk, 128, 0, s, ld, c0, ncols, ctx->H, ctx->kcol);
   if (sizeof(T) == 8)
