@@ -596,6 +596,75 @@ def lognormal_precisions(stream, n_t):
     return out
 
 
+def large_mesh(args):
+    """The 1024^2 stress workload (3,151,875 DOF, N_t = 128, nu = 0.49, lognormal kappa sigma 2,
+    l = 0.1, P1): FP32 sweeps with the FP64 residual and update. One JSON line: the sweep
+    throughput over args.steps timed sweeps (the bench metric, all N_t steps active), the
+    setup time (assembly, substructured factorisations) and tuning time, the band-solve
+    roofline in FP32, and a tolerance solve to the workload's 1e-8 continued from the swept
+    state and capped at args.large_outer sweeps (0: skipped)."""
+    import torch
+    import workloads as W
+    from paper_2310_10430_gb300 import biot
+    from paper_2310_10430_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    case = W.large_1024()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with biot.Context(case, stream=stream, precision="fp32", strips=args.strips) as c:
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        tuning = biot.biot_tune(c.ctx, args.tune_cache).as_dict()
+        tune_s = time.perf_counter() - t1
+        info = c.info
+        for _ in range(args.warmup):
+            biot.biot_sweep(c.ctx, 1, case.n_t, want_rel=False)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        biot.biot_timing_enable(c.ctx, True)
+        l0 = biot.biot_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            biot.biot_sweep(c.ctx, 1, case.n_t, want_rel=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = biot.biot_launch_count() - l0
+        clk = clocks.stop()
+        band_ms, band_n = biot.biot_timing_read(c.ctx, biot.BIOT_KC_BAND_SOLVE)
+        biot.biot_timing_enable(c.ctx, False)
+        ms = e0.elapsed_time(e1) / args.steps
+        rel_swept = float(biot.biot_residual_norms(c.ctx, 1, case.n_t).max())
+        solve = None
+        if args.large_outer > 0:
+            t2 = time.perf_counter()
+            st, sweeps, rel = biot.biot_pint_solve(c.ctx, case.tol, args.large_outer, allow_not_converged=True)
+            torch.cuda.synchronize()
+            solve = {"seconds": time.perf_counter() - t2, "sweeps": sweeps, "status": biot.STATUS_NAMES[st],
+                     "rel_residual": rel, "tol": case.tol}
+        device_gb = c.info.device_bytes / 1e9
+    fl, per = band_solve_flops(info, case.n_t, case.precond, int(tuning.get("strips", 0)))
+    ach = fl / (band_ms / band_n / 1e3) / 1e12
+    out = {"metric": METRIC, "value": case.n_dof * case.n_t / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{case.name}: n=1024, N_t=128, nu=0.49, lognormal kappa sigma 2, P1, "
+                                  "FP32 sweeps with FP64 residual and update",
+                      "window": case.n_t, "n_iter": case.n_iter, "l2": "inputs larger than L2"},
+           "clocks": clk, "gpu_launches": int(launches),
+           "setup_seconds": setup_s, "tune_seconds": tune_s, "device_gb": device_gb,
+           "band_solve": {"achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "bound": "alu",
+                          "frac": ach / FP32_PEAK_TFLOPS, "avg_apply_ms": band_ms / band_n,
+                          "share_of_step": band_ms / args.steps / ms},
+           "max_rel_residual_after_sweeps": rel_swept, "tolerance_solve": solve, "tuning": tuning}
+    print(json.dumps(out))
+    return out
+
+
 def batched_vs_sequential(stream, count=16):
     """Config-4-shaped instances (uneven n, N_t, nu, lognormal kappa sigma 1.5), FP32
     with FP64 refinement to 1e-10: one batched solve (CUDA graph) vs the same
@@ -685,6 +754,11 @@ def main():
     ap.add_argument("--tune-cache", default=None,
                     help="band-solve tuning cache (JSON): read if present, written otherwise; profiling runs "
                          "use it to replay the plain run's variant choice")
+    ap.add_argument("--large", action="store_true",
+                    help="run only the 1024^2 stress workload (N_t = 128, nu = 0.49, lognormal sigma 2, P1, FP32 "
+                         "sweeps with FP64 refinement): setup, --steps timed sweeps, one JSON line")
+    ap.add_argument("--large-outer", type=int, default=0,
+                    help="with --large: also run the tolerance solve, capped at this many sweeps")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"],
                     help="sweep precision of the timed line (profiling runs; the bench line is fp64)")
     args = ap.parse_args()
@@ -699,6 +773,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.large:
+        large_mesh(args)
     else:
         run_ours(args)
 

@@ -140,16 +140,20 @@ biot_status biot_precond_setup(biot_ctx* ctx, int32_t kind);
 
 /* Exact block solves by one-level substructuring (an implementation choice; the
  * paper leaves the inner solvers of Sec. 3.1 open). strips = 0: automatic (about 18
- * node columns per strip in FP64 and 13 in the reduced-precision modes; none below
- * n = 26 and 19 respectively); 1: plain band factorisations of A and
- * S in natural order; k >= 2: the n + 1 node columns are cut by k - 1 separator
- * columns into k strips, each strip's interior is factored along its short side
- * (half-band d (w + 2) - 1 for a strip w nodes wide, d = 2 for A, 1 for S), and the
- * separators' Schur complement A_SS - A_SI A_II^{-1} A_IS (block tridiagonal, half-band
- * 2 d (n + 1) - 1) is formed and factored on the device. The solves stay exact (block
- * Gaussian elimination); only their cost and rounding order change. Takes effect at
- * the next biot_precond_setup. Errors: BIOT_E_INVALID (strips < 0, or fewer than two
- * node columns per strip: 3 strips > n + 2). */
+ * node columns per strip in FP64 and 10 in the reduced-precision modes, at most
+ * sqrt((n + 1) / 1.31) and sqrt((n + 1) / 0.38) strips; none below n = 26 and 13
+ * respectively); 1: plain band factorisations of A and S in natural order; k >= 2: the
+ * n + 1 node columns are cut by k - 1 separator columns into k strips, each strip's
+ * interior is factored along its short side (half-band d (w + 2) - 1 for a strip w nodes
+ * wide, d = 2 for A, 1 for S), and the separators' Schur complement
+ * A_SS - A_SI A_II^{-1} A_IS (block tridiagonal with d (n + 1) x d (n + 1) blocks) is
+ * formed and factored on the device; its solves run as dense block products with the
+ * inverted diagonal blocks of the factor (or as band substitutions, whichever biot_tune
+ * finds faster). The solves stay exact (block Gaussian elimination); only their cost and
+ * rounding order change. Above n = 512 a substructured context builds no natural-order
+ * factors (and cannot join biot_batch_solve). Takes effect at the next
+ * biot_precond_setup. Errors: BIOT_E_INVALID (strips < 0, or fewer than two node columns
+ * per strip: 3 strips > n + 2). */
 biot_status biot_set_substructure(biot_ctx* ctx, int32_t strips);
 
 /* Run the inverted time stepping (Alg. 3) as windowed snapshot sweeps: at sweep
@@ -293,6 +297,8 @@ typedef struct {
   double ms_u_default, ms_p_default;    /* same with the default variant */
   int32_t from_cache;                   /* 1 if both choices came from the cache file */
   int32_t strips;                       /* substructured block solves: strips (0: plain band) */
+  int32_t variant_sep_u, variant_sep_p; /* substructured: separator variants (variant_*: interiors) */
+  double ms_sep_u, ms_sep_p;            /* substructured: the separator pair's part of ms_u, ms_p */
 } biot_tuning;
 
 /* Pick the band triangular-solve kernel variant (register-streamed; TMA-staged
@@ -305,11 +311,13 @@ typedef struct {
  * size, half-band and window; read first, rewritten with the new choices.
  * Requires biot_precond_setup. out (nullable) receives the choices and times.
  * With substructured block solves (biot_set_substructure) it times, for A and
- * for S, every fitting in-place variant (TMA-staged split rows, or one row per lane
- * with 1, 2 or 4 warps per CTA) of the strip-parallel interior solves and of the
- * separator solves instead, keeps the fastest, caches the choices under keys
+ * for S, every fitting in-place variant (TMA-staged split rows with 4 to 32-row blocks,
+ * or one row per lane with 1, 2 or 4 warps per CTA) of the strip-parallel interior
+ * solves and of the separator solves instead, for the separators also the dense
+ * block products (variant 100), keeps the fastest, caches the choices under keys
  * "sub:" + precision, rows, half-band and window, and reports the interior variants,
- * the interior + separator pair times (ms_u, ms_p) and the strip count. */
+ * the separator variants, the interior + separator pair times (ms_u, ms_p), their
+ * separator parts (ms_sep_u, ms_sep_p) and the strip count. */
 biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out);
 
 /* Kernel launches issued by this library since it was loaded (all contexts). */

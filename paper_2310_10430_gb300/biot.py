@@ -55,6 +55,8 @@ class BiotTuning(ctypes.Structure):
         ("ms_u", ctypes.c_double), ("ms_p", ctypes.c_double),
         ("ms_u_default", ctypes.c_double), ("ms_p_default", ctypes.c_double),
         ("from_cache", ctypes.c_int32), ("strips", ctypes.c_int32),
+        ("variant_sep_u", ctypes.c_int32), ("variant_sep_p", ctypes.c_int32),
+        ("ms_sep_u", ctypes.c_double), ("ms_sep_p", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -788,10 +788,10 @@ biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out) {
   if (ctx->sub[0]) {
     // substructured block solves: time the interior and separator variants of A and S (or
     // take them from the cache, keyed "sub:" + precision, rows, half-band and window)
-    double ms[2] = {0.0, 0.0};
+    double ms[2] = {0.0, 0.0}, ms_sep[2] = {0.0, 0.0};
     std::map<std::string, int> cache = read_tune_cache(cache_path);
     int hits = 0;
-    BIOT_TRY(sub_tune(ctx, ms, &cache, &hits));
+    BIOT_TRY(sub_tune(ctx, ms, ms_sep, &cache, &hits));
     BIOT_TRY(device_status(ctx));
     res.from_cache = hits == 4 ? 1 : 0;
     if (!res.from_cache) write_tune_cache(cache_path, cache);
@@ -808,6 +808,10 @@ biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out) {
     res.nb_p = kBandVariants[res.variant_p].nb;
     res.threads_p = kBandVariants[res.variant_p].threads;
     res.strips = su->k;
+    res.variant_sep_u = su->varS[pi];
+    res.variant_sep_p = sp->varS[pi];
+    res.ms_sep_u = ms_sep[0];
+    res.ms_sep_p = ms_sep[1];
     if (out) *out = res;
     return BIOT_OK;
   }

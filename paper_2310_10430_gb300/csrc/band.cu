@@ -366,10 +366,16 @@ constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Ring rows R of the TMA-staged body, which indexes its ring modulo R (any R): phase 1 of a
+// block reads the b rows before (forward) or after (backward) it, plus at most VQ - 1 below an
+// aligned start, so R >= b + NB + 8 keeps every row it needs and, with each row stored at slots
+// j mod R and j mod R + R, keeps every read window contiguous inside the 2 R slots.
+__host__ __device__ constexpr int tma_ring_rows(int b, int nb) { return b + nb + 8; }
+
 template <typename T, int NB>
 __host__ __device__ inline size_t tma_smem_bytes(int b) {
   return 64 + 2 * align16((size_t)NB * band_ld(b) * sizeof(T)) + 2 * align16((size_t)NB * NB * sizeof(T)) +
-         2 * (size_t)ring_rows(b) * kCols * sizeof(T) + (size_t)NB * kCols * sizeof(T);
+         2 * (size_t)tma_ring_rows(b, NB) * kCols * sizeof(T) + (size_t)NB * kCols * sizeof(T);
 }
 
 // Compact inverses of the NB-row diagonal blocks, [block][NB][NB], taken from the
@@ -521,7 +527,46 @@ band_solve_tma_body(int N, int b, const T* __restrict__ band, const T* __restric
         if (kFwd) qs = max(qs, max(0, (i / blk - 1) * blk) - (i - b));
         else qe = min(qe, (i / blk + 2) * blk - i);
       }
-      if (qs < qe) {
+      if (qs < qe && sizeof(T) == 4) {
+        // FP32: one band entry per lane and step, so consecutive lanes read consecutive band
+        // words and ring rows (both columns of a row as one 8-byte load): no bank conflicts.
+        // Chunks of VQ entries per lane (below) read the ring at a 4-row stride across lanes,
+        // an 8-way conflict that FP32's short multiply-adds cannot hide (FP64's can).
+        const T* Lrow = rows + (size_t)r * lb;
+        int s0 = (kFwd ? (i - b + qs) : (i + qs)) % R;
+        if (s0 < 0) s0 += R;
+        s0 -= qs;  // ring slot of entry q: s0 + q, below 2 R for q < qe
+        // Four entries' loads go out before their multiply-adds, into four accumulator pairs:
+        // with one warp per SM sub-partition nothing else hides the shared-memory latency.
+        using V2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+        const V2* ring2 = reinterpret_cast<const V2*>(ring);
+        T a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a[u] = T(0);
+        int q = qs + part;
+        for (; q + 3 * KS < qe; q += 4 * KS) {
+          T l[4];
+          V2 y[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            l[u] = Lrow[q + u * KS];
+            y[u] = ring2[s0 + q + u * KS];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            a[2 * u] = fma(l[u], y[u].x, a[2 * u]);
+            a[2 * u + 1] = fma(l[u], y[u].y, a[2 * u + 1]);
+          }
+        }
+        for (; q < qe; q += KS) {
+          const T l0 = Lrow[q];
+          const V2 y0 = ring2[s0 + q];
+          a[0] = fma(l0, y0.x, a[0]);
+          a[1] = fma(l0, y0.y, a[1]);
+        }
+        acc0 = (a[0] + a[2]) + (a[4] + a[6]);
+        acc1 = (a[1] + a[3]) + (a[5] + a[7]);
+      } else if (qs < qe) {
         const T* Lrow = rows + (size_t)r * lb;
         const int qa = qs & ~(VQ - 1);  // 16-byte aligned start
         int s0 = (kFwd ? (i - b + qa) : (i + qa)) % R;
@@ -793,7 +838,7 @@ __global__ void __launch_bounds__(kBatchThreads) kb_band_solve_tma(const InstDev
   const float* band = (MODE == FWD_U_FROM_V) ? I.Lu : (MODE == BWD_U_TO_Z) ? I.Uu : (MODE == BWD_P_TO_Z) ? I.Up : I.Lp;
   const float* Dnb = u ? I.dnbu : I.dnbp;
   band_solve_tma_body<MODE, float, kBatchNB, kBatchThreads>(N, b, band, Dnb, I.V + j * vs, I.dsq, I.tu, I.tp,
-                                                            I.Z + j * vs, I.wcap, I.c0, I.nf, ring_rows(b) - 1, 0,
+                                                            I.Z + j * vs, I.wcap, I.c0, I.nf, tma_ring_rows(b, kBatchNB) - 1, 0,
                                                             0, I.status);
 }
 
@@ -822,7 +867,9 @@ biot_status band_cholesky(biot_ctx* ctx, int N, int b, double* Lb) {
 
 }  // namespace
 
-biot_status band_setup(biot_ctx* ctx, int kind) {
+// Natural-order band factors of A and S (FP64, and FP32 copies for the reduced-precision
+// sweeps) with their default solve variants and block inverses.
+static biot_status plain_band_setup(biot_ctx* ctx) {
   const int nn = ctx->n_nodes;
   const int bu = ctx->band_u, bp = ctx->band_p;
   if (bu + kNB > 8192) return fail(ctx, BIOT_E_INVALID, "mesh too large for the band solver (half-band %d)", bu);
@@ -880,6 +927,20 @@ biot_status band_setup(biot_ctx* ctx, int kind) {
     BIOT_TRY(ensure_dnb(ctx, pi == 0, true, ctx->band_var_u[pi]));
     BIOT_TRY(ensure_dnb(ctx, pi == 0, false, ctx->band_var_p[pi]));
   }
+  return BIOT_OK;
+}
+
+// Meshes above this size skip the natural-order factors when their blocks are substructured:
+// at n = 1024 A's band factor alone would hold 35 GB in FP64 and cost about 9 TFLOP to form.
+constexpr int kPlainBandMaxN = 512;
+
+biot_status band_setup(biot_ctx* ctx, int kind) {
+  ctx->plain_band = sub_strips(ctx) < 2 || ctx->n <= kPlainBandMaxN;
+  if (ctx->plain_band) {
+    BIOT_TRY(plain_band_setup(ctx));
+  } else {
+    for (int pi = 0; pi < 2; ++pi) ctx->band_var_u[pi] = ctx->band_var_p[pi] = -1;
+  }
   BIOT_TRY(sub_setup(ctx));
   ctx->precond = kind;
   return BIOT_OK;
@@ -920,7 +981,7 @@ static void launch_tma_raw(biot_ctx* ctx, int N, int b, const T* band, const T* 
                          227 * 1024);
     attr_set = true;
   }
-  const int rr = ring_rows(b);
+  const int rr = tma_ring_rows(b, NB);
   const size_t smem = tma_smem_bytes<T, NB>(b);
   const dim3 grid(div_up(ncols, kCols), nstrips);
   BIOT_LAUNCH((k_band_solve_tma<MODE, T, NB, THREADS>), grid, THREADS, smem, ctx->stream, N, b, band, Dnb, vin,
@@ -1206,7 +1267,7 @@ static void launch_legacy(biot_ctx* ctx, int N, int b, const T* band, const T* D
 // TMA-staged kernels with NB-row blocks and THREADS threads.
 const BandVariant kBandVariants[kBandVariantCount] = {
     {0, 64, 256}, {1, 16, 128}, {1, 16, 256}, {1, 32, 256}, {1, 8, 128}, {1, 32, 128}, {2, kTileNB, kTileThreads},
-    {3, kRowsNB, 32}, {3, kRowsNB, 64}, {3, kRowsNB, 128}};
+    {3, kRowsNB, 32}, {3, kRowsNB, 64}, {3, kRowsNB, 128}, {1, 4, 128}};
 
 size_t band_variant_smem(int v, bool fp64, int b) {
   const BandVariant& V = kBandVariants[v];
@@ -1214,12 +1275,13 @@ size_t band_variant_smem(int v, bool fp64, int b) {
   if (!V.tma) return es * ((size_t)ring_rows(b) * kCols + kNB * kCols);
   if (V.tma == 2) return tile_stages(b) ? tile_smem_bytes(b, tile_stages(b)) : (size_t)1 << 30;
   return 64 + 2 * align16((size_t)V.nb * band_ld(b) * es) + 2 * align16((size_t)V.nb * V.nb * es) +
-         2 * (size_t)ring_rows(b) * kCols * es + (size_t)V.nb * kCols * es;
+         2 * (size_t)tma_ring_rows(b, V.nb) * kCols * es + (size_t)V.nb * kCols * es;
 }
 
 bool band_variant_ok(int v, bool fp64, int b) {
   if (fp64 && kBandVariants[v].tma == 2) return false;  // the tile solve is FP32 only
   if (kBandVariants[v].tma == 3) return false;          // the row-per-lane solve is in-place only
+  if (v == kWideVariant) return false;                  // so is the four-row TMA solve
   return band_variant_smem(v, fp64, b) <= 227 * 1024;
 }
 
@@ -1228,7 +1290,7 @@ bool band_variant_inplace_ok(int v, bool fp64, int b) {
     const int w = kBandVariants[v].threads / 32;
     return (fp64 ? rows_smem_bytes<double>(b, w) : rows_smem_bytes<float>(b, w)) <= 227 * 1024;
   }
-  return kBandVariants[v].tma == 1 && band_variant_ok(v, fp64, b);
+  return kBandVariants[v].tma == 1 && band_variant_smem(v, fp64, b) <= 227 * 1024;
 }
 
 int band_variant_default(bool fp64, int b) {
@@ -1482,6 +1544,7 @@ void band_solve_inplace(biot_ctx* ctx, bool fwd, int variant, int N, int nstrips
     BIOT_INPLACE_CASE(3, 32, 256)
     BIOT_INPLACE_CASE(4, 8, 128)
     BIOT_INPLACE_CASE(5, 32, 128)
+    BIOT_INPLACE_CASE(10, 4, 128)
     default: break;
   }
 #undef BIOT_INPLACE_CASE

@@ -133,6 +133,12 @@ struct SubBlock {
   void* tI[2] = {nullptr, nullptr};       // workspaces [NI][wcap], [NI][wcap], [NS][wcap] per precision
   void* tI2[2] = {nullptr, nullptr};
   void* tS[2] = {nullptr, nullptr};
+  // dense-block separator solves (separator.cu): D_K^{-1}, M_K, P_K as Bp x Bp blocks
+  bool dense = false;
+  int Bp = 0;                       // B rounded up to a multiple of 64
+  double *Dinv = nullptr, *Mk = nullptr, *Pk = nullptr;
+  float *Dinvf = nullptr, *Mkf = nullptr, *Pkf = nullptr;
+  void* tZ[2] = {nullptr, nullptr};       // [NS][wcap] forward results per precision
 };
 
 struct biot_ctx {
@@ -180,6 +186,7 @@ struct biot_ctx {
   // band preconditioner
   int band_u = 0, band_p = 0;
   int precond = 0;
+  bool plain_band = true;       // natural-order band factors built (false: large substructured meshes)
   double* Lu = nullptr;         // A = L L^T, lower band rows [2 n_nodes][band_u + 1]
   double* Uu = nullptr;         // L^T band rows [2 n_nodes][band_u + 1]
   double* Lp = nullptr;         // S = L L^T, [n_nodes][band_p + 1]
@@ -254,10 +261,14 @@ void to_f32(biot_ctx* ctx, const double* in, float* out, size_t n);
 
 // ---- substructure.cu ----
 int sub_auto_strips(int n, bool fp64);
+int sub_strips(const biot_ctx* ctx);  // strips sub_setup will use (1: natural-order band solves)
 biot_status sub_setup(biot_ctx* ctx);
 void sub_free(biot_ctx* ctx);
 template <typename T> void sub_apply(biot_ctx* ctx, int which, const T* vin, T* z, int c0, int ncols);
-biot_status sub_tune(biot_ctx* ctx, double* ms, std::map<std::string, int>* cache, int* hits);
+// ---- separator.cu ----
+biot_status sep_dense_setup(biot_ctx* ctx, SubBlock* sb);  // needs sb->LS factored
+template <typename T> void sep_dense_solve(biot_ctx* ctx, SubBlock* sb, T* tS, T* tZ, int ld, int c0, int ncols);
+biot_status sub_tune(biot_ctx* ctx, double* ms, double* ms_sep, std::map<std::string, int>* cache, int* hits);
 
 // ---- assembly.cu ----
 biot_status build_pattern(biot_ctx* ctx);
@@ -286,7 +297,13 @@ struct BandVariant {
   int nb;       // rows per block
   int threads;  // CTA size
 };
-constexpr int kBandVariantCount = 10;
+constexpr int kBandVariantCount = 11;
+// Four-row blocks: the only TMA variant whose two band stages fit beside the ring at the
+// separators' half-band 4 (n + 1) - 1 of large meshes; in-place (substructured) solves only.
+constexpr int kWideVariant = 10;
+// Separator "variant" that solves with the dense diagonal-block inverses instead of a band
+// substitution (tuning caches store it like a band-solve variant).
+constexpr int kDenseSep = 100;
 extern const BandVariant kBandVariants[kBandVariantCount];
 size_t band_variant_smem(int v, bool fp64, int b);
 bool band_variant_ok(int v, bool fp64, int b);          // usable by the natural-order block solves

@@ -22,6 +22,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -123,16 +124,17 @@ __global__ void k_sub_schur_init(SubArgs a, const int32_t* __restrict__ rowptr, 
 }
 
 // Ssep[s][c2] -= sum over interior i of strips t0 .. t0+G-1: A[s][i] (A_II^{-1} A_IS)[i][c2],
-// one thread per band entry (s, q), c2 = s - bS + q.
+// one thread per band entry (s, q), c2 = s - bS + q, for the separator rows s0 <= s < s1 that
+// border those strips (no other row has an interior neighbour in them).
 template <int D>
-__global__ void k_sub_schur_update(SubArgs a, int t0, int G, const int32_t* __restrict__ rowptr,
+__global__ void k_sub_schur_update(SubArgs a, int t0, int G, int s0, int s1, const int32_t* __restrict__ rowptr,
                                    const int32_t* __restrict__ col, const double* __restrict__ val,
                                    const double* __restrict__ Z, int ldz, double* __restrict__ LS) {
   const int ld = band_ld(a.bS);
-  const long long tot = (long long)a.NS * (a.bS + 1);
+  const long long tot = (long long)(s1 - s0) * (a.bS + 1);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < tot;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(idx / (a.bS + 1)), q = (int)(idx % (a.bS + 1));
+    const int s = s0 + (int)(idx / (a.bS + 1)), q = (int)(idx % (a.bS + 1));
     const int c2 = s - a.bS + q;
     if (c2 < 0) continue;
     const int mc = c2 / a.B, qc = c2 % a.B;
@@ -363,13 +365,17 @@ biot_status setup_block(biot_ctx* ctx, int k, SubBlock*& out) {
   // defaults (biot_tune re-times them): the row-per-lane solve (7, one warp per CTA) only when
   // its one-warp CTAs cover every SM sub-partition, i.e. at least 4 x 152 of them (four columns
   // each, all strips); otherwise 128-thread split-row CTAs
+  // Separators: the dense-block solve (separator.cu) by default; band substitutions (large
+  // meshes: four-row blocks, the only staging that fits their half-band) stay available to
+  // the tuner where one fits.
   const bool many = (long long)div_up(ctx->wcap, 4) * k >= 4 * 152;
   sb->varI[0] = many ? pick_variant(true, sb->bI, {7, 5, 1, 2, 3, 4}) : pick_variant(true, sb->bI, {5, 1, 2, 3, 4});
-  sb->varS[0] = pick_variant(true, sb->bS, {5, 1, 2, 4});
+  sb->varS[0] = pick_variant(true, sb->bS, {5, 1, 2, 4, kWideVariant});
   sb->varI[1] = many ? pick_variant(false, sb->bI, {7, 5, 3, 1, 2, 4}) : pick_variant(false, sb->bI, {5, 3, 1, 2, 4});
-  sb->varS[1] = pick_variant(false, sb->bS, {5, 3, 1, 2, 4});
-  if (sb->varI[0] < 0 || sb->varS[0] < 0 || sb->varI[1] < 0 || sb->varS[1] < 0)
-    return fail(ctx, BIOT_E_INVALID, "substructure: no band-solve variant fits half-bands %d / %d", sb->bI, sb->bS);
+  sb->varS[1] = pick_variant(false, sb->bS, {5, 3, 1, 2, 4, kWideVariant});
+  const bool fp64 = ctx->prm.precision == BIOT_FP64;
+  if (sb->varI[0] < 0 || sb->varI[1] < 0)
+    return fail(ctx, BIOT_E_INVALID, "substructure: no band-solve variant fits the interiors' half-band %d", sb->bI);
   BIOT_TRY(dalloc(ctx, &sb->dnbI[0], sizeof(double) * ((size_t)sb->NI + 64) * 32));
   extract_dnb_variant<double>(ctx, sb->varI[0], sb->DI, sb->NI, (double*)sb->dnbI[0]);
   // Ssep = A_SS - A_SI A_II^{-1} A_IS, strips in groups that keep A_II^{-1} A_IS under 2 GB
@@ -391,7 +397,9 @@ biot_status setup_block(biot_ctx* ctx, int k, SubBlock*& out) {
       const double* dnb = (const double*)sb->dnbI[0] + dnb_offset(sb->varI[0], r0);
       band_solve_inplace<double>(ctx, true, sb->varI[0], sb->Ps, g, sb->bI, sb->LI + r0 * ldIsz, dnb, Z, ldz, 0, ldz);
       band_solve_inplace<double>(ctx, false, sb->varI[0], sb->Ps, g, sb->bI, sb->UI + r0 * ldIsz, dnb, Z, ldz, 0, ldz);
-      BIOT_LAUNCH(k_sub_schur_update<D>, grid_for((long long)sb->NS * (sb->bS + 1)), 256, 0, st, a, t0, g,
+      // strip t borders separators t - 1 and t
+      const int s0 = std::max(t0 - 1, 0) * sb->B, s1 = std::min(t0 + g, k - 1) * sb->B;
+      BIOT_LAUNCH(k_sub_schur_update<D>, grid_for((long long)(s1 - s0) * (sb->bS + 1)), 256, 0, st, a, t0, g, s0, s1,
                   ctx->rowptr, ctx->col, ctx->val, Z, ldz, sb->LS);
     }
     BIOT_CU(ctx, cudaGetLastError());
@@ -401,8 +409,11 @@ biot_status setup_block(biot_ctx* ctx, int k, SubBlock*& out) {
     if (e != 0) return fail(ctx, BIOT_E_CUDA, "substructure: inconsistent ordering (code %d)", e);
     dfree(ctx, Z);
     BIOT_TRY(band_factor(ctx, sb->NS, sb->bS, sb->LS, sb->US, sb->DS));
-    BIOT_TRY(dalloc(ctx, &sb->dnbS[0], sizeof(double) * ((size_t)sb->NS + 64) * 32));
-    extract_dnb_variant<double>(ctx, sb->varS[0], sb->DS, sb->NS, (double*)sb->dnbS[0]);
+    if (sb->varS[0] >= 0) {
+      BIOT_TRY(dalloc(ctx, &sb->dnbS[0], sizeof(double) * ((size_t)sb->NS + 64) * 32));
+      extract_dnb_variant<double>(ctx, sb->varS[0], sb->DS, sb->NS, (double*)sb->dnbS[0]);
+    }
+    BIOT_TRY(sep_dense_setup(ctx, sb));
   }
   if (ctx->prm.precision != BIOT_FP64) {
     // reduced-precision sweeps: the exact FP64 factors rounded to FP32
@@ -421,9 +432,17 @@ biot_status setup_block(biot_ctx* ctx, int k, SubBlock*& out) {
       to_f32(ctx, sb->LS, sb->LSf, szS);
       to_f32(ctx, sb->US, sb->USf, szS);
       to_f32(ctx, sb->DS, sb->DSf, dS);
-      BIOT_TRY(dalloc(ctx, &sb->dnbS[1], sizeof(float) * ((size_t)sb->NS + 64) * 32));
-      extract_dnb_variant<float>(ctx, sb->varS[1], sb->DSf, sb->NS, (float*)sb->dnbS[1]);
+      if (sb->varS[1] >= 0) {
+        BIOT_TRY(dalloc(ctx, &sb->dnbS[1], sizeof(float) * ((size_t)sb->NS + 64) * 32));
+        extract_dnb_variant<float>(ctx, sb->varS[1], sb->DSf, sb->NS, (float*)sb->dnbS[1]);
+      }
     }
+  }
+  if (sb->dense) {
+    sb->varS[0] = sb->varS[1] = kDenseSep;
+  } else if (sb->NS > 0 && ((fp64 && sb->varS[0] < 0) || sb->varS[1] < 0)) {
+    return fail(ctx, BIOT_E_INVALID, "substructure: no separator solve fits half-band %d in %s", sb->bS,
+                fp64 ? "FP64" : "FP32");
   }
   BIOT_CU(ctx, cudaGetLastError());
   return BIOT_OK;
@@ -471,9 +490,13 @@ void apply_block(biot_ctx* ctx, SubBlock* sb, bool from_t, const T* vin, const T
     // x_S = Ssep^{-1} (r_S - A_SI z1)
     BIOT_LAUNCH((k_sub_couple_S<D, T>), grid_for((long long)sb->NS * ncols), 256, 0, st, a, ctx->rowptr, ctx->col,
                 ctx->val, tI, tS, ld, c0, ncols);
-    // Ssep is block tridiagonal with B x B blocks: its factor's band holds exact zeros to skip
-    band_solve_inplace<T>(ctx, true, sb->varS[pi], sb->NS, 1, sb->bS, F::LS(sb), dnbS, tS, ld, c0, ncols, sb->B);
-    band_solve_inplace<T>(ctx, false, sb->varS[pi], sb->NS, 1, sb->bS, F::US(sb), dnbS, tS, ld, c0, ncols, sb->B);
+    if (sb->varS[pi] == kDenseSep) {
+      sep_dense_solve<T>(ctx, sb, tS, (T*)sb->tZ[pi], ld, c0, ncols);
+    } else {
+      // Ssep is block tridiagonal with B x B blocks: its factor's band holds exact zeros to skip
+      band_solve_inplace<T>(ctx, true, sb->varS[pi], sb->NS, 1, sb->bS, F::LS(sb), dnbS, tS, ld, c0, ncols, sb->B);
+      band_solve_inplace<T>(ctx, false, sb->varS[pi], sb->NS, 1, sb->bS, F::US(sb), dnbS, tS, ld, c0, ncols, sb->B);
+    }
     // x_I = A_II^{-1} (r_I - A_IS x_S)
     BIOT_LAUNCH((k_sub_couple_I<D, T>), grid_for((long long)sb->nadj * ncols), 256, 0, st, a, sb->adjI, sb->nadj,
                 ctx->rowptr, ctx->col, ctx->val, tS, tI2, ld, c0, ncols);
@@ -492,6 +515,10 @@ biot_status ensure_workspace(biot_ctx* ctx, SubBlock* sb) {
   BIOT_TRY(dalloc(ctx, &sb->tI[pi], sizeof(T) * (size_t)sb->NI * w));
   BIOT_TRY(dalloc(ctx, &sb->tI2[pi], sizeof(T) * (size_t)sb->NI * w));
   BIOT_TRY(dalloc(ctx, &sb->tS[pi], sizeof(T) * ((size_t)std::max(sb->NS, 1)) * w));
+  if (sb->dense) {
+    BIOT_TRY(dalloc(ctx, &sb->tZ[pi], sizeof(T) * (size_t)sb->NS * w));
+    BIOT_CU(ctx, cudaMemsetAsync(sb->tZ[pi], 0, sizeof(T) * (size_t)sb->NS * w, ctx->stream));
+  }
   // padding rows and unused columns stay finite
   BIOT_CU(ctx, cudaMemsetAsync(sb->tI[pi], 0, sizeof(T) * (size_t)sb->NI * w, ctx->stream));
   BIOT_CU(ctx, cudaMemsetAsync(sb->tI2[pi], 0, sizeof(T) * (size_t)sb->NI * w, ctx->stream));
@@ -502,10 +529,21 @@ biot_status ensure_workspace(biot_ctx* ctx, SubBlock* sb) {
 }  // namespace
 
 // Strips for an n x n mesh when the caller leaves the choice open: about 18 node columns per
-// strip in FP64 (k = 14 at n = 256, the fastest of k = 4 .. 24) and about 13 in the reduced-
-// precision sweeps (k = 20 at n = 256), none below n = 26 (FP64) or 19.
+// strip in FP64 (k = 14 at n = 256, the fastest of k = 14 .. 28 with the dense separator
+// solves) and about 10 in the reduced-precision sweeps (k = 26 at n = 256, fastest of 20 .. 40),
+// none below n = 26 (FP64) or 13. Per column the interiors cost about d^2 (n + 1)^2 (w + 2)
+// and the separators (k - 1) 1.5 d^2 (n + 1)^2, so the best k grows like sqrt(n + 1) rather
+// than n: the count is capped at sqrt((n + 1) / c), c matched to the measured optima (1.31 in
+// FP64 at n = 256; 0.38 in FP32, k = 52 at n = 1024 between the measured 40, 56 and 72).
 int sub_auto_strips(int n, bool fp64) {
-  const int k = fp64 ? (n + 1 + 9) / 18 : (n + 1 + 6) / 13;
+  const int lin = fp64 ? (n + 1 + 9) / 18 : (n + 1 + 6) / 10;
+  const int cap = (int)std::lround(std::sqrt((n + 1) / (fp64 ? 1.31 : 0.38)));
+  const int k = std::min(lin, cap);
+  return k >= 2 ? k : 1;
+}
+
+int sub_strips(const biot_ctx* ctx) {
+  const int k = ctx->sub_req == 0 ? sub_auto_strips(ctx->n, ctx->prm.precision == BIOT_FP64) : ctx->sub_req;
   return k >= 2 ? k : 1;
 }
 
@@ -520,7 +558,8 @@ void sub_free(biot_ctx* ctx) {
     if (!sb) continue;
     void* ptrs[] = {sb->pos, sb->oldI, sb->oldS, sb->adjI, sb->LI, sb->UI, sb->DI, sb->LS, sb->US, sb->DS,
                     sb->LIf, sb->UIf, sb->DIf, sb->LSf, sb->USf, sb->DSf, sb->dnbI[0], sb->dnbI[1],
-                    sb->dnbS[0], sb->dnbS[1], sb->tI[0], sb->tI[1], sb->tI2[0], sb->tI2[1], sb->tS[0], sb->tS[1]};
+                    sb->dnbS[0], sb->dnbS[1], sb->tI[0], sb->tI[1], sb->tI2[0], sb->tI2[1], sb->tS[0], sb->tS[1],
+                    sb->Dinv, sb->Mk, sb->Pk, sb->Dinvf, sb->Mkf, sb->Pkf, sb->tZ[0], sb->tZ[1]};
     for (void* p : ptrs) dfree(ctx, p);
     delete sb;
     ctx->sub[w] = nullptr;
@@ -529,7 +568,7 @@ void sub_free(biot_ctx* ctx) {
 
 biot_status sub_setup(biot_ctx* ctx) {
   sub_free(ctx);
-  int k = ctx->sub_req == 0 ? sub_auto_strips(ctx->n, ctx->prm.precision == BIOT_FP64) : ctx->sub_req;
+  const int k = sub_strips(ctx);
   if (k < 2) return BIOT_OK;
   if (3 * k > ctx->n + 2) return fail(ctx, BIOT_E_INVALID, "substructure: %d strips leave fewer than 2 node columns per strip at n = %d", k, ctx->n);
   BIOT_TRY(setup_block<2>(ctx, k, ctx->sub[0]));
@@ -578,8 +617,12 @@ float time_sub_pair(biot_ctx* ctx, SubBlock* sb, bool interior, int v) {
   for (int rep = 0; rep < 3; ++rep) {
     cudaEventRecord(e0, ctx->stream);
     const int blk = interior ? 0 : sb->B;
-    band_solve_inplace<T>(ctx, true, v, N, nst, b, L, dnb, buf, ctx->wcap, 0, ctx->wcap, blk);
-    band_solve_inplace<T>(ctx, false, v, N, nst, b, U, dnb, buf, ctx->wcap, 0, ctx->wcap, blk);
+    if (v == kDenseSep) {
+      sep_dense_solve<T>(ctx, sb, buf, (T*)sb->tZ[pi], ctx->wcap, 0, ctx->wcap);
+    } else {
+      band_solve_inplace<T>(ctx, true, v, N, nst, b, L, dnb, buf, ctx->wcap, 0, ctx->wcap, blk);
+      band_solve_inplace<T>(ctx, false, v, N, nst, b, U, dnb, buf, ctx->wcap, 0, ctx->wcap, blk);
+    }
     cudaEventRecord(e1, ctx->stream);
     cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -594,6 +637,7 @@ float time_sub_pair(biot_ctx* ctx, SubBlock* sb, bool interior, int v) {
 template <typename T>
 void set_dnb(biot_ctx* ctx, SubBlock* sb, bool interior, int v) {
   constexpr int pi = SubFactors<T>::pi;
+  if (v == kDenseSep || (!interior && !sb->dnbS[pi])) return;
   const T* D = (const T*)(interior ? (pi ? (const void*)sb->DIf : (const void*)sb->DI)
                                    : (pi ? (const void*)sb->DSf : (const void*)sb->DS));
   extract_dnb_variant<T>(ctx, v, D, interior ? sb->NI : sb->NS, (T*)(interior ? sb->dnbI[pi] : sb->dnbS[pi]));
@@ -607,7 +651,11 @@ float tune_part(biot_ctx* ctx, SubBlock* sb, bool interior, std::map<std::string
   const int b = interior ? sb->bI : sb->bS;
   char key[96];
   snprintf(key, sizeof(key), "sub:%s:N%d:b%d:w%d", fp64 ? "fp64" : "fp32", interior ? sb->NI : sb->NS, b, ctx->wcap);
-  if (cache && cache->count(key) && band_variant_inplace_ok((*cache)[key], fp64, b)) {
+  auto usable = [&](int v) {
+    if (v == kDenseSep) return !interior && sb->dense;
+    return band_variant_inplace_ok(v, fp64, b) && (interior || sb->dnbS[pi] != nullptr);
+  };
+  if (cache && cache->count(key) && usable((*cache)[key])) {
     var = (*cache)[key];
     set_dnb<T>(ctx, sb, interior, var);
     ++*hits;
@@ -615,8 +663,11 @@ float tune_part(biot_ctx* ctx, SubBlock* sb, bool interior, std::map<std::string
   }
   float tbest = time_sub_pair<T>(ctx, sb, interior, var);
   int best = var;
-  for (int v = 1; v < kBandVariantCount; ++v) {
-    if (v == var || !band_variant_inplace_ok(v, fp64, b)) continue;
+  std::vector<int> cands;
+  for (int v = 1; v < kBandVariantCount; ++v) cands.push_back(v);
+  cands.push_back(kDenseSep);
+  for (int v : cands) {
+    if (v == var || !usable(v)) continue;
     set_dnb<T>(ctx, sb, interior, v);
     const float t = time_sub_pair<T>(ctx, sb, interior, v);
     if (t < tbest) {
@@ -633,19 +684,21 @@ float tune_part(biot_ctx* ctx, SubBlock* sb, bool interior, std::map<std::string
 }  // namespace
 
 // Times every fitting TMA variant for the strip interiors and for the separators of A and
-// S and keeps the fastest; ms[0], ms[1]: the chosen interior + separator pair times of A, S.
-biot_status sub_tune(biot_ctx* ctx, double* ms, std::map<std::string, int>* cache, int* hits) {
+// S and keeps the fastest; ms[0], ms[1]: the chosen interior + separator pair times of A, S,
+// ms_sep[0], ms_sep[1]: their separator parts.
+biot_status sub_tune(biot_ctx* ctx, double* ms, double* ms_sep, std::map<std::string, int>* cache, int* hits) {
   const bool fp64 = ctx->prm.precision == BIOT_FP64;
   *hits = 0;
   for (int w = 0; w < 2; ++w) {
     SubBlock* sb = ctx->sub[w];
-    ms[w] = 0.0;
+    ms[w] = ms_sep[w] = 0.0;
     if (!sb) continue;
     ms[w] += fp64 ? tune_part<double>(ctx, sb, true, cache, hits) : tune_part<float>(ctx, sb, true, cache, hits);
     if (sb->NS > 0)
-      ms[w] += fp64 ? tune_part<double>(ctx, sb, false, cache, hits) : tune_part<float>(ctx, sb, false, cache, hits);
+      ms_sep[w] = fp64 ? tune_part<double>(ctx, sb, false, cache, hits) : tune_part<float>(ctx, sb, false, cache, hits);
     else
       ++*hits;  // no separators: nothing to choose
+    ms[w] += ms_sep[w];
   }
   BIOT_CU(ctx, cudaGetLastError());
   return BIOT_OK;

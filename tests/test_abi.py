@@ -48,6 +48,7 @@ def test_struct_layouts_match_header():
     # 8-byte aligned doubles/pointers, int32 members as declared
     assert ctypes.sizeof(biot.BiotParams) == 8 * 6 + 4 * 3 + 4 + 8 + 4 * 4
     assert ctypes.sizeof(biot.BiotInfo) == 4 * 3 + 4 + 8 + 4 * 8 + 8 + 8
+    assert ctypes.sizeof(biot.BiotTuning) == 4 * 8 + 8 * 4 + 4 * 2 + 4 * 2 + 8 * 2
 
 
 def test_invalid_arguments_rejected_on_host(L):

@@ -105,7 +105,10 @@ def lognormal_kappa(n: int, mean_log10: float = -6.0, sigma: float = 1.0,
     w = rng.standard_normal((n_features, 2)) / corr_len
     b = rng.uniform(0.0, 2.0 * np.pi, n_features)
     c = element_centroids(n, Lx, Ly)
-    z = np.sqrt(2.0 / n_features) * np.cos(c @ w.T + b).sum(axis=1)
+    # in row chunks on large meshes (the feature matrix of 1024^2 would hold 8.6 GB)
+    step = 1 << 18
+    z = np.concatenate([np.cos(c[i:i + step] @ w.T + b).sum(axis=1) for i in range(0, len(c), step)])
+    z *= np.sqrt(2.0 / n_features)
     return np.exp(mean_log10 * np.log(10.0) + sigma * z)
 
 
