@@ -32,6 +32,7 @@ if ROOT not in sys.path:
 
 METRIC = "DOF*timesteps*outer-iters/s"
 UNIT = "DOF*timesteps*outer-iters/s"
+DENSE_SEP = 100   # tuning's separator variant for the dense-block solves
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz
 
@@ -190,7 +191,7 @@ class ClockSampler:
 # roofline helpers
 # ---------------------------------------------------------------------------
 
-def band_solve_flops(info, ncols, precond, strips=0):
+def band_solve_flops(info, ncols, precond, strips=0, dense_sep=(True, True)):
     """Algorithmic FP64 flops of the exact block solves of one P apply: 2 flops per band
     entry per column of every triangular solve, tri(N, b) = 2 W (N b - b (b + 1) / 2).
 
@@ -201,7 +202,10 @@ def band_solve_flops(info, ncols, precond, strips=0):
     factor is block bidiagonal with B = d (n + 1): row rho of block m > 0 has B + rho
     off-diagonal entries, of block 0 rho (the rest of its half-band 2B - 1 is exact zeros,
     skipped by the solve), plus the two sparse couplings (2 flops per separator-interior
-    entry per column, twice)."""
+    entry per column, twice). The dense-block separator solves (dense_sep[block]) take
+    the same multiply-adds as the band substitution (block-diagonal products with the
+    inverted diagonal blocks: B^2 / 2 per block; chain products: B^2 per block but the
+    first). Also returns the launches of one apply."""
     def tri(N, b):
         return 2.0 * ncols * (N * b - b * (b + 1) / 2.0)
     n = round((info.n_nodes) ** 0.5) - 1
@@ -213,7 +217,8 @@ def band_solve_flops(info, ncols, precond, strips=0):
     ni = C - (strips - 1)
     widths = [ni // strips + (1 if t < ni % strips else 0) for t in range(strips)]
     total = 0.0
-    for d in (2, 1):
+    launches = 0
+    for blk, d in enumerate((2, 1)):
         bI = d * (max(widths) + 2) - 1
         interior = sum(tri(d * w * C, bI) for w in widths)
         B, nb = d * C, strips - 1
@@ -221,8 +226,10 @@ def band_solve_flops(info, ncols, precond, strips=0):
         # each separator node couples to its 4 interior neighbours (i +- 1 columns): d*d entries each
         coupling = 2 * 2.0 * ncols * (strips - 1) * C * 4 * d * d
         total += 4 * interior + 2 * sep + coupling
-    # launches per block: gather, 2 x interior pair, separator pair, 2 couplings, scatter
-    return total, 20
+        # gather, 2 x interior pair, 2 couplings, scatter; separators: a pair of band solves,
+        # or two block-diagonal products and two chains of nb - 1 products
+        launches += 8 + (2 * nb if dense_sep[blk] else 2)
+    return total, launches
 
 
 def nvtx_push(name):
@@ -293,14 +300,22 @@ def kernel_source_hash(src_path, kernel):
     return hashlib.sha256(txt[start:end + 3].encode()).hexdigest()[:16]
 
 
-def profile_traffic(kernel_src, kernel):
-    """DRAM bytes per launch from a committed ncu summary whose kernel-source hash matches
-    (null once the kernel has changed since the counters were taken). `kernel` may name
-    several definitions joined by '+': their hashes are chained."""
-    parts = [kernel_source_hash(kernel_src, k) for k in kernel.split("+")]
-    sha = None if None in parts else hashlib.sha256("".join(parts).encode()).hexdigest()[:16]
-    if len(parts) == 1:
-        sha = parts[0]
+# The kernels of one P apply's block solves, (source file, definition) pairs.
+APPLY_KERNELS = [("band.cu", "k_band_solve_rows"), ("band.cu", "band_solve_tma_body"),
+                 ("separator.cu", "k_sep_gemm")]
+
+
+def dense_sep_of(tuning):
+    """Which blocks (A, S) solve their separators with the dense block products."""
+    return (tuning.get("variant_sep_u") == DENSE_SEP, tuning.get("variant_sep_p") == DENSE_SEP)
+
+
+def profile_traffic(parts):
+    """DRAM bytes per unit from a committed ncu summary whose kernel-source hash matches (null
+    once a kernel has changed since the counters were taken): the hashes of the (file,
+    definition) parts under paper_2310_10430_gb300/csrc are chained."""
+    hs = [kernel_source_hash(os.path.join(ROOT, "paper_2310_10430_gb300", "csrc", f), k) for f, k in parts]
+    sha = None if None in hs else hashlib.sha256("".join(hs).encode()).hexdigest()[:16]
     pdir = os.path.join(ROOT, "profiles")
     if sha is None or not os.path.isdir(pdir):
         return None
@@ -309,7 +324,7 @@ def profile_traffic(kernel_src, kernel):
             continue
         txt = open(os.path.join(pdir, fn)).read()
         m1 = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", txt)
-        m2 = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+        m2 = re.search(r"traffic_bytes_per_unit:\s*([0-9.eE+]+)", txt)
         if m1 and m2 and m1.group(1) == sha:
             return float(m2.group(1))
     return None
@@ -396,19 +411,18 @@ def run_ours(args):
     # the band-solve timing class brackets one whole P apply (its four solve launches; for
     # P2 the solves on A and on S run concurrently on two streams)
     flops_per_apply, launches_per_apply = band_solve_flops(info, hi - lo + 1, case.precond,
-                                                           int(tuning.get("strips", 0)))
+                                                           int(tuning.get("strips", 0)), dense_sep_of(tuning))
     achieved = flops_per_apply / (band_ms / band_n / 1e3) / 1e12
-    traffic = profile_traffic(os.path.join(ROOT, "paper_2310_10430_gb300", "csrc", "band.cu"),
-                              "k_band_solve_rows+band_solve_tma_body") if args.precision == "fp64" else None
+    traffic = profile_traffic(APPLY_KERNELS) if args.precision == "fp64" else None
     fp64 = args.precision == "fp64"
     peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
-    roofline = {"kernel": "k_band_solve_rows + k_band_solve_tma (%s band triangular solves of the P2 block solves)"
-                          % ("FP64" if fp64 else "FP32"),
+    roofline = {"kernel": "k_band_solve_rows + k_sep_gemm + k_band_solve_tma (%s exact block solves of the P2 "
+                          "apply: strip interiors, dense-block and band separator solves)" % ("FP64" if fp64 else "FP32"),
                 "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (FP64 not in MEASURED_PEAKS.json)"
                                 if fp64 else "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz"),
-                "traffic": traffic, "traffic_per": "k_band_solve_tma launch (mean of the captured launches of one apply)",
+                "traffic": traffic, "traffic_per": "P apply (DRAM bytes of its band-solve and separator launches)",
                 "applies": band_n, "launches_per_apply": launches_per_apply,
                 "avg_apply_ms": band_ms / band_n, "avg_launch_ms": band_ms / band_n / launches_per_apply,
                 "share_of_step": band_ms / ms}
@@ -478,7 +492,7 @@ def sweep_variant(case, precision, steps, warmup, stream):
         band_ms, band_n = biot.biot_timing_read(c.ctx, biot.BIOT_KC_BAND_SOLVE)
         biot.biot_timing_enable(c.ctx, False)
         ms = e0.elapsed_time(e1) / steps
-        fl, per = band_solve_flops(info, case.n_t, case.precond, int(tuning.get("strips", 0)))
+        fl, per = band_solve_flops(info, case.n_t, case.precond, int(tuning.get("strips", 0)), dense_sep_of(tuning))
         ach = fl / (band_ms / band_n / 1e3) / 1e12
         return {"ms_per_step": ms, "value": case.n_dof * case.n_t / (ms / 1e3), "unit": UNIT,
                 "band_solve": {"achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "bound": "alu",
@@ -601,8 +615,8 @@ def large_mesh(args):
     l = 0.1, P1): FP32 sweeps with the FP64 residual and update. One JSON line: the sweep
     throughput over args.steps timed sweeps (the bench metric, all N_t steps active), the
     setup time (assembly, substructured factorisations) and tuning time, the band-solve
-    roofline in FP32, and a tolerance solve to the workload's 1e-8 continued from the swept
-    state and capped at args.large_outer sweeps (0: skipped)."""
+    roofline in FP32, and a tolerance solve to the workload's 1e-8 from the zero state,
+    capped at args.large_outer sweeps (0: skipped), with FGMRES(args.large_n_iter)."""
     import torch
     import workloads as W
     from paper_2310_10430_gb300 import biot
@@ -611,6 +625,8 @@ def large_mesh(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     case = W.large_1024()
+    if args.large_n_iter:
+        case = case.with_(n_iter=args.large_n_iter)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     with biot.Context(case, stream=stream, precision="fp32", strips=args.strips) as c:
@@ -641,13 +657,16 @@ def large_mesh(args):
         rel_swept = float(biot.biot_residual_norms(c.ctx, 1, case.n_t).max())
         solve = None
         if args.large_outer > 0:
+            import numpy as np
+            biot.biot_set_state(c.ctx, 0, case.n_t, np.zeros((case.n_t + 1, case.n_dof)))
+            torch.cuda.synchronize()
             t2 = time.perf_counter()
             st, sweeps, rel = biot.biot_pint_solve(c.ctx, case.tol, args.large_outer, allow_not_converged=True)
             torch.cuda.synchronize()
             solve = {"seconds": time.perf_counter() - t2, "sweeps": sweeps, "status": biot.STATUS_NAMES[st],
                      "rel_residual": rel, "tol": case.tol}
         device_gb = c.info.device_bytes / 1e9
-    fl, per = band_solve_flops(info, case.n_t, case.precond, int(tuning.get("strips", 0)))
+    fl, per = band_solve_flops(info, case.n_t, case.precond, int(tuning.get("strips", 0)), dense_sep_of(tuning))
     ach = fl / (band_ms / band_n / 1e3) / 1e12
     out = {"metric": METRIC, "value": case.n_dof * case.n_t / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -759,6 +778,8 @@ def main():
                          "sweeps with FP64 refinement): setup, --steps timed sweeps, one JSON line")
     ap.add_argument("--large-outer", type=int, default=0,
                     help="with --large: also run the tolerance solve, capped at this many sweeps")
+    ap.add_argument("--large-n-iter", type=int, default=0,
+                    help="with --large: FGMRES restart length (default: the workload's 10)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"],
                     help="sweep precision of the timed line (profiling runs; the bench line is fp64)")
     args = ap.parse_args()

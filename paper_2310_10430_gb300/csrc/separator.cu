@@ -82,7 +82,9 @@ k_sep_gemm(int B, int Bp, const T* __restrict__ A, long long a_z, const T* X, lo
   __shared__ __align__(16) T As[2][BK][BM];
   __shared__ __align__(16) T Xs[2][BK][BM];
   const int t = threadIdx.x, ty = t / 16, tx = t % 16;
-  const int n0 = blockIdx.x * BM, m0 = blockIdx.y * BM;
+  // lower-triangular A: the last row tiles take the most k tiles, so they are issued first
+  const int mt = (TRI && !TRANS) ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
+  const int n0 = blockIdx.x * BM, m0 = mt * BM;
   A += (size_t)blockIdx.z * a_z;
   X += (size_t)blockIdx.z * x_z;
   C += (size_t)blockIdx.z * c_z;
@@ -191,13 +193,15 @@ void gemm_bm(cudaStream_t st, GemmKind kind, dim3 grid, int B, int Bp, const T* 
   }
 }
 
-// 64 x 64 tiles when they give at least two CTAs per SM, 32 x 32 otherwise (Bp is a multiple of 64).
+// FP64: 32 x 32 tiles (the FP64 pipe, not shared memory, bounds even 2 x 2 outputs per thread,
+// and the smaller tiles balance better). FP32: 64 x 64 tiles (half the shared-memory reads per
+// multiply-add) when they give at least two CTAs per SM, 32 x 32 otherwise. Bp is a multiple of 64.
 template <typename T>
 void gemm(cudaStream_t st, GemmKind kind, int nz, int B, int Bp, const T* A, long long a_z, const T* X, long long x_z,
           T* C, long long c_z, int ld, int c0, int ncols) {
   if (nz < 1 || ncols < 1) return;
   const long long big = (long long)div_up(ncols, 64) * (Bp / 64) * nz;
-  if (big >= 2 * 152) {
+  if (sizeof(T) == 4 && big >= 2 * 152) {
     gemm_bm<T, 64>(st, kind, dim3(div_up(ncols, 64), Bp / 64, nz), B, Bp, A, a_z, X, x_z, C, c_z, ld, c0, ncols);
   } else {
     gemm_bm<T, 32>(st, kind, dim3(div_up(ncols, 32), Bp / 32, nz), B, Bp, A, a_z, X, x_z, C, c_z, ld, c0, ncols);
