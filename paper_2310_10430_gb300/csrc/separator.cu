@@ -220,9 +220,9 @@ biot_status sep_dense_setup(biot_ctx* ctx, SubBlock* sb) {
   BIOT_TRY(dalloc(ctx, (void**)&sb->Dinv, sizeof(double) * nD));
   BIOT_CU(ctx, cudaMemsetAsync(sb->Dinv, 0, sizeof(double) * nD, st));
   const size_t smem = sizeof(double) * kInvWarps * B;
+  if (smem > 227 * 1024) return fail(ctx, BIOT_E_INVALID, "separator blocks of %d rows too large", B);
   if (smem > 48 * 1024)
     BIOT_CU(ctx, cudaFuncSetAttribute(k_sep_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  if (smem > 227 * 1024) return fail(ctx, BIOT_E_INVALID, "separator blocks of %d rows too large", B);
   BIOT_LAUNCH(k_sep_inverse, dim3(div_up(B, kInvWarps), nsep), kInvWarps * 32, smem, st, nsep, B, Bp, sb->bS, sb->LS,
               ldS, sb->Dinv);
   if (nsep > 1) {

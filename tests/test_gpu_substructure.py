@@ -158,21 +158,22 @@ def test_resetup_switches_between_plain_and_strips():
 
 
 WIDE_VARIANT = 10  # four-row TMA blocks: the separator solve of large meshes
+DENSE_SEP = 100    # separators by dense block products with the inverted diagonal blocks
 
 
-def forced_apply(tmp_path, case, precision, variant, separators, seed):
+def forced_apply(tmp_path, case, precision, variant, separators, seed, strips=4):
     """P^{-1} apply with the interior (or separator) solves forced to one variant.
 
-    A tuning cache naming a variant forces it. Keys are "sub:<precision>:N<rows>:b<half-band>:w<window>";
-    interiors have half-bands below n + 1, separators 2 d (n + 1) - 1 above."""
+    A tuning cache naming a variant forces it. Keys are "sub:<precision>:N<rows>:b<half-band>:w<window>"."""
     s = build_system(case)
     vin = np.random.default_rng(seed).standard_normal((5, s.n_dof))
-    with biot.Context(case, precision=precision, strips=4) as c:
+    with biot.Context(case, precision=precision, strips=strips) as c:
         probe = tmp_path / "probe.json"
         biot.biot_tune(c.ctx, str(probe))
         entries = json.loads(probe.read_text())["band_solve_variants"]
         for e in entries:
-            if (int(e["key"].split(":b")[1].split(":")[0]) > case.n + 1) == separators:
+            # separators have half-band 2 d (n + 1) - 1 (d = 1, 2), strip interiors d (w + 2) - 1
+            if (int(e["key"].split(":b")[1].split(":")[0]) >= 2 * (case.n + 1) - 1) == separators:
                 e["variant"] = variant
         forced = tmp_path / "forced.json"  # the library reads one entry per line
         forced.write_text('{"band_solve_variants": [\n' +
@@ -199,27 +200,52 @@ def test_each_interior_variant(tmp_path, precision, bound, variant):
 
 @pytest.mark.parametrize("kind", ["diag", "tri"])
 @pytest.mark.parametrize("precision,bound", [("fp64", 1e-9), ("fp32", 1e-3)])
-def test_wide_separator_variant(tmp_path, kind, precision, bound):
-    # the separators solved in four-row blocks, with the block-bidiagonal skip, on a ragged
-    # set of columns (5: two column pairs and a lone column)
+@pytest.mark.parametrize("variant", [1, 4, 5, WIDE_VARIANT, DENSE_SEP])
+def test_each_separator_variant(tmp_path, kind, precision, bound, variant):
+    # band substitutions (with the block-bidiagonal skip; four-row blocks for large meshes) and
+    # the dense block products, on a ragged set of columns (5: two column pairs and a lone one)
     case = W.terzaghi_small().with_(n=23, n_t=7, precond=kind)
-    t, err = forced_apply(tmp_path, case, precision, WIDE_VARIANT, separators=True, seed=11)
-    assert err < bound, err
+    t, err = forced_apply(tmp_path, case, precision, variant, separators=True, seed=11)
+    assert t.variant_sep_u == variant and t.variant_sep_p == variant
+    assert err < bound, (variant, err)
 
 
-def test_large_mesh_without_natural_order_factors():
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-9), ("fp32", 1e-3)])
+@pytest.mark.parametrize("strips", [2, 3, 6])
+def test_dense_separators_chain_lengths(tmp_path, precision, bound, strips):
+    # one separator block (no chain products), two (one per direction) and five
+    case = W.terzaghi_small().with_(n=21, n_t=5, precond="tri")
+    t, err = forced_apply(tmp_path, case, precision, DENSE_SEP, separators=True, seed=strips, strips=strips)
+    assert t.strips == strips and t.variant_sep_u == DENSE_SEP
+    assert err < bound, (strips, err)
+
+
+def test_large_mesh_without_natural_order_factors(tmp_path):
     # Above n = 512 a substructured context builds no natural-order band factors (A's alone
-    # would hold 8.9 GB at n = 520); its separators (half-band 4 * 521 - 1 = 2083) take the
-    # four-row solve. A property that holds at any size checks the blocks' solves: P2 inverts
-    # the assembled blocks, A z_u = r_u and AA_pp z_p = r_p, checked on the host with the
-    # library's CSR (whose pattern and values match the oracle's at small sizes).
+    # would hold 8.9 GB at n = 520). Its separators (blocks of 2 * 521 rows, half-band
+    # 4 * 521 - 1 = 2083) are solved both ways: by the dense block products and by the band
+    # substitution in four-row blocks (the only staging that fits). A property that holds at
+    # any size checks the solves: P2 inverts the assembled blocks, A z_u = r_u and
+    # AA_pp z_p = r_p, checked on the host with the library's CSR (whose pattern and values
+    # match the oracle's at small sizes).
     sp = pytest.importorskip("scipy.sparse")
     case = W.terzaghi_small().with_(n=520, n_t=3, precond="diag")
+    vin = np.random.default_rng(4).standard_normal((3, case.n_dof))
+    zs = []
     with biot.Context(case) as c:
-        t = biot.biot_tune(c.ctx, None)
+        probe = tmp_path / "probe.json"
+        t = biot.biot_tune(c.ctx, str(probe))
         assert t.strips == 20  # min((n + 10) / 18, sqrt((n + 1) / 1.31)) in FP64
-        vin = np.random.default_rng(4).standard_normal((3, c.info.n_dof))
-        z = biot.biot_precond_apply(c.ctx, vin)
+        for variant in (DENSE_SEP, WIDE_VARIANT):
+            entries = json.loads(probe.read_text())["band_solve_variants"]
+            forced = tmp_path / f"forced{variant}.json"
+            forced.write_text('{"band_solve_variants": [\n' + "".join(
+                f'  {{"key": "{e["key"]}", "variant": '
+                f'{variant if int(e["key"].split(":b")[1].split(":")[0]) >= 2 * (case.n + 1) - 1 else e["variant"]}}},\n'
+                for e in entries) + "]}\n")
+            t = biot.biot_tune(c.ctx, str(forced))
+            assert t.from_cache == 1 and t.variant_sep_u == variant and t.variant_sep_p == variant
+            zs.append(biot.biot_precond_apply(c.ctx, vin))
         rowptr, col, val, _ = biot.biot_get_csr(c.ctx)
         with pytest.raises(biot.BiotError) as e:
             biot.biot_batch_solve([c.ctx], 1e-8, 10)
@@ -229,7 +255,8 @@ def test_large_mesh_without_natural_order_factors():
     u = np.flatnonzero(np.arange(nd) % 3 != 2)
     p = np.arange(2, nd, 3)
     Auu, App = K[u][:, u], K[p][:, p]
-    for k in range(vin.shape[0]):
-        ru = np.linalg.norm(Auu @ z[k, u] - vin[k, u]) / np.linalg.norm(vin[k, u])
-        rp = np.linalg.norm(App @ z[k, p] - vin[k, p]) / np.linalg.norm(vin[k, p])
-        assert ru < 1e-10 and rp < 1e-10, (k, ru, rp)
+    for z in zs:
+        for k in range(vin.shape[0]):
+            ru = np.linalg.norm(Auu @ z[k, u] - vin[k, u]) / np.linalg.norm(vin[k, u])
+            rp = np.linalg.norm(App @ z[k, p] - vin[k, p]) / np.linalg.norm(vin[k, p])
+            assert ru < 1e-10 and rp < 1e-10, (k, ru, rp)
