@@ -69,7 +69,12 @@ typedef enum {
   BIOT_BF16VAL_FP32ACC = 2   /* as BIOT_FP32 with the SpMM matrix values stored in BF16 */
 } biot_precision;
 
-typedef enum { BIOT_TERZAGHI = 0, BIOT_MMS_TRIG = 1 } biot_problem;
+typedef enum {
+  BIOT_TERZAGHI = 0,         /* consolidation column: top load, drained top, fixed bottom, roller sides */
+  BIOT_MMS_TRIG = 1,         /* manufactured cos t cos 3 pi x cos 3 pi y solution, Dirichlet on all sides (Sec. 4.1) */
+  BIOT_BARRY_MERCER = 2      /* point source -0.5 load delta_(a/4, b/4) sin(beta t), beta = (lambda + 2 mu) K / (a b);
+                                drained, zero tangential displacement on every side (Sec. 4.3) */
+} biot_problem;
 
 typedef enum {
   BIOT_BETA_H2 = 0,          /* beta = h^2 / (4 (lambda + 2 mu)) (dimensionally consistent reading) */
@@ -91,7 +96,8 @@ typedef struct {
   int32_t n_t;               /* number of time steps N_t (>= 1) */
   int32_t problem;           /* biot_problem */
   int32_t beta_mode;         /* biot_beta_mode */
-  double load;               /* Terzaghi top traction magnitude (traction (0, -load) for t >= tau) */
+  double load;               /* Terzaghi top traction magnitude (traction (0, -load) for t >= tau);
+                                Barry & Mercer source amplitude 0.5 load */
   int32_t n_iter;            /* Krylov steps per call of K (1..32) */
   int32_t window;            /* BIOT_SCHED_TOL: max active steps (0 = N_t); BIOT_SCHED_PAPER: iterations per step */
   int32_t schedule;          /* biot_schedule */

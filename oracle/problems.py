@@ -1,4 +1,4 @@
-"""Boundary data, loads and exact solutions of the two test families.
+"""Boundary data, loads and exact solutions of the three test families.
 
 Terzaghi column (reading A9; the paper's model, Sec. 2.1, with its standard
 consolidation set-up): unit square, traction (0, -load) on the top for every
@@ -11,6 +11,14 @@ state the exact solution at t = 0. The printed body force f matches the PDE; the
 printed source g carries a sign error in its first term (it must be symmetric
 under x <-> y because the solution is). Reading A3: both sources are derived
 here from the PDE (biotsys1)-(biotsys2) for the stated solution.
+
+Barry & Mercer's problem (Sec. 4.3): the domain [0, a] x [0, b] is drained on every side
+(p = 0) with zero tangential displacement there (u_y = 0 on x = 0, a; u_x = 0 on y = 0, b;
+the normal component is left free, traction-free in the normal direction: reading A14), a
+point source g(t) = -0.5 load delta_{(x0, y0)} sin(beta t) with beta = (lambda + 2 mu) K / (a b)
+at (x0, y0) = (a / 4, b / 4), no body force, x0 = 0. The source enters the pressure rows as
+-tau G^n with G^n_v = phi_v(x0, y0) g(t_n): the P1 basis functions of the triangle holding
+the point, evaluated there (the exact load of a Dirac delta).
 """
 import numpy as np
 
@@ -87,12 +95,39 @@ def top_traction_y(n, coords, ty):
     return out
 
 
+def point_source_weights(n, Lx, Ly, x0, y0):
+    """(nodes, weights): the P1 basis functions of the triangle holding (x0, y0), evaluated
+    there. Cell (i, j) is split along its "/" diagonal into the lower triangle (i,j),
+    (i+1,j), (i+1,j+1) and the upper one (i,j), (i+1,j+1), (i,j+1); with local coordinates
+    (xi, eta) in the cell, the lower one holds xi >= eta."""
+    hx, hy = Lx / n, Ly / n
+    i = min(int(np.floor(x0 / hx)), n - 1)
+    j = min(int(np.floor(y0 / hy)), n - 1)
+    xi, eta = x0 / hx - i, y0 / hy - j
+    nx = n + 1
+    v00, v10, v11, v01 = j * nx + i, j * nx + i + 1, (j + 1) * nx + i + 1, (j + 1) * nx + i
+    if xi >= eta:
+        return np.array([v00, v10, v11]), np.array([1.0 - xi, xi - eta, eta])
+    return np.array([v00, v11, v01]), np.array([1.0 - eta, xi, eta - xi])
+
+
+def barry_mercer_beta(case):
+    """beta = (lambda + 2 mu) K / (a b) of the source's sin(beta t)."""
+    lam, mu = lame(case.E, case.nu)
+    return (lam + 2.0 * mu) * float(case.kappa_elem()[0]) / (case.Lx * case.Ly)
+
+
 def dirichlet_dofs(case):
     """Sorted array of constrained DOFs for the case's boundary-condition family."""
     sides = boundary_nodes(case.n)
     if case.problem == "terzaghi":
         d = [3 * sides["bottom"], 3 * sides["bottom"] + 1,
              3 * sides["left"], 3 * sides["right"], 3 * sides["top"] + 2]
+    elif case.problem == "barry_mercer":
+        nodes = np.unique(np.concatenate(list(sides.values())))
+        d = [3 * sides["bottom"], 3 * sides["top"],            # u_x tangential on y = 0, b
+             3 * sides["left"] + 1, 3 * sides["right"] + 1,    # u_y tangential on x = 0, a
+             3 * nodes + 2]                                    # drained everywhere
     elif case.problem == "mms":
         nodes = np.unique(np.concatenate(list(sides.values())))
         d = [3 * nodes, 3 * nodes + 1, 3 * nodes + 2]
@@ -103,7 +138,7 @@ def dirichlet_dofs(case):
 
 def dirichlet_values(case, coords, dofs, t):
     """Prescribed values g_D(t) at the constrained DOFs."""
-    if case.problem == "terzaghi":
+    if case.problem in ("terzaghi", "barry_mercer"):
         return np.zeros(dofs.shape[0])
     node, field = dofs // 3, dofs % 3
     u1, u2, p = mms_exact(coords[node, 0], coords[node, 1], t)
@@ -125,6 +160,10 @@ def load_vector(case, coords, tris, t):
     out = np.zeros(3 * nn)
     if case.problem == "terzaghi":
         out[1::3] += top_traction_y(case.n, coords, -case.load)
+    elif case.problem == "barry_mercer":
+        nodes, w = point_source_weights(case.n, case.Lx, case.Ly, case.Lx / 4.0, case.Ly / 4.0)
+        g = -0.5 * case.load * np.sin(barry_mercer_beta(case) * t)
+        out[3 * nodes + 2] += -case.tau * g * w
     else:
         lam, mu = lame(case.E, case.nu)
         K = float(case.kappa_elem()[0])

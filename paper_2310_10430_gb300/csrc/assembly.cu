@@ -174,7 +174,7 @@ __global__ void k_assemble(int n, double hx, double hy, int colour, Material m, 
   }
 }
 
-// Dirichlet DOFs of the two boundary-condition families.
+// Dirichlet DOFs of the three boundary-condition families.
 __global__ void k_dirichlet_mask(int n, int problem, uint8_t* __restrict__ dmask) {
   const int nn = (n + 1) * (n + 1);
   int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -185,6 +185,10 @@ __global__ void k_dirichlet_mask(int n, int problem, uint8_t* __restrict__ dmask
     if (j == 0) m0 = m1 = 1;            // fixed bottom
     if (i == 0 || i == n) m0 = 1;       // roller sides
     if (j == n) m2 = 1;                 // drained top
+  } else if (problem == BIOT_BARRY_MERCER) {
+    m0 = (j == 0 || j == n) ? 1 : 0;    // tangential u_x on the horizontal sides
+    m1 = (i == 0 || i == n) ? 1 : 0;    // tangential u_y on the vertical sides
+    m2 = (i == 0 || i == n || j == 0 || j == n) ? 1 : 0;  // drained everywhere
   } else {
     const bool bnd = (i == 0 || i == n || j == 0 || j == n);
     m0 = m1 = m2 = bnd ? 1 : 0;
@@ -275,20 +279,31 @@ __global__ void k_lifting(int n, int n_dof, double hx, double hy, const int32_t*
   l2[r] = s2;
 }
 
-__global__ void k_time_tables(int n_t, double tau, double* __restrict__ tc, double* __restrict__ ts) {
+// cos(t_k), sin(omega t_k) for k = 0..n_t (omega = 1: manufactured case; Barry & Mercer: beta).
+__global__ void k_time_tables(int n_t, double tau, double omega, double* __restrict__ tc, double* __restrict__ ts) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k > n_t) return;
   const double t = (double)k * tau;
   tc[k] = cos(t);
-  ts[k] = sin(t);
+  ts[k] = sin(omega * t);
 }
 
+// Barry & Mercer's point source: the P1 basis of the triangle holding the point, evaluated there
+// (the load of a Dirac delta), on its three vertices; amp: the source's amplitude (g = amp sin).
+struct PointSource {
+  int v[3];
+  double w[3];
+  double amp;
+};
+
 // F[r][k] for k = 0..n_t (column 0 zero). Terzaghi: constant traction on u_y of
-// the top nodes for t_k >= tau. Manufactured case: loads, -tau G and lifting.
+// the top nodes for t_k >= tau. Manufactured case: loads, -tau G and lifting. Barry & Mercer:
+// -tau G on the pressure rows of the source triangle's vertices, G = w_v amp sin(beta t_k).
 __global__ void k_rhs(int n, int n_dof, int n_t, int ldx, int problem, double hx, double hy, double tau, double load,
                       const uint8_t* __restrict__ dmask, const double* __restrict__ su, const double* __restrict__ sg1,
                       const double* __restrict__ sg2, const double* __restrict__ l1, const double* __restrict__ l2,
-                      const double* __restrict__ tc, const double* __restrict__ ts, double* __restrict__ F) {
+                      const double* __restrict__ tc, const double* __restrict__ ts, PointSource ps,
+                      double* __restrict__ F) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_dof) return;
   const int nx = n + 1, v = r / 3, f = r % 3, i = v % nx, j = v / nx;
@@ -298,6 +313,14 @@ __global__ void k_rhs(int n, int n_dof, int n_t, int ldx, int problem, double hx
     double val = 0.0;
     if (f == 1 && j == n && !dmask[r]) val = -load * 0.5 * hx * ((i > 0 ? 1.0 : 0.0) + (i < n ? 1.0 : 0.0));
     for (int k = 1; k <= n_t; ++k) Fr[k] = val;  // Dirichlet data are zero
+    return;
+  }
+  if (problem == BIOT_BARRY_MERCER) {
+    double w = 0.0;
+    if (f == 2 && !dmask[r])
+      for (int a = 0; a < 3; ++a)
+        if (ps.v[a] == v) w += ps.w[a];
+    for (int k = 1; k <= n_t; ++k) Fr[k] = -tau * (w * ps.amp * ts[k]);
     return;
   }
   if (dmask[r]) {
@@ -410,7 +433,22 @@ biot_status assemble_system(biot_ctx* ctx) {
   lift = sg + 2 * (size_t)nn;
   tt = lift + 2 * (size_t)nd;
   BIOT_CU(ctx, cudaMemsetAsync(tmp, 0, sizeof(double) * tmp_doubles, s));
-  BIOT_LAUNCH(k_time_tables, div_up(p.n_t + 1, 256), 256, 0, s, p.n_t, p.tau, tt, tt + p.n_t + 1);
+  // Barry & Mercer: beta = (lambda + 2 mu) K / (a b), the source at (a/4, b/4)
+  PointSource ps{{-1, -1, -1}, {0.0, 0.0, 0.0}, -0.5 * p.load};
+  double omega = 1.0;
+  if (p.problem == BIOT_BARRY_MERCER) {
+    const double K = p.kappa_elem ? p.kappa_elem[0] : p.kappa_const;
+    omega = (lam + 2.0 * mu) * K / (ctx->Lx * ctx->Ly);
+    // cell of the point and its local coordinates; the "/" diagonal splits the cell into the
+    // lower triangle (xi >= eta) and the upper one
+    const double px = ctx->Lx / 4.0 / hx, py = ctx->Ly / 4.0 / hy;
+    const int ci = std::min((int)std::floor(px), n - 1), cj = std::min((int)std::floor(py), n - 1);
+    const double xi = px - ci, eta = py - cj;
+    const int nx = n + 1, v00 = cj * nx + ci, v10 = v00 + 1, v11 = v00 + nx + 1, v01 = v00 + nx;
+    if (xi >= eta) ps = {{v00, v10, v11}, {1.0 - xi, xi - eta, eta}, ps.amp};
+    else ps = {{v00, v11, v01}, {1.0 - eta, xi, eta - xi}, ps.amp};
+  }
+  BIOT_LAUNCH(k_time_tables, div_up(p.n_t + 1, 256), 256, 0, s, p.n_t, p.tau, omega, tt, tt + p.n_t + 1);
   if (p.problem == BIOT_MMS_TRIG) {
     // the manufactured case assumes a constant K (first element's value)
     double K = p.kappa_const;
@@ -422,7 +460,7 @@ biot_status assemble_system(biot_ctx* ctx) {
                 ctx->apval, ctx->dmask, lift, lift + nd);
   }
   BIOT_LAUNCH(k_rhs, div_up(nd, 128), 128, 0, s, n, nd, p.n_t, ctx->ldx, p.problem, hx, hy, p.tau, p.load, ctx->dmask,
-              su, sg, sg + nn, lift, lift + nd, tt, tt + p.n_t + 1, ctx->F);
+              su, sg, sg + nn, lift, lift + nd, tt, tt + p.n_t + 1, ps, ctx->F);
   BIOT_LAUNCH(k_init_state, div_up(nd, 128), 128, 0, s, n, nd, p.n_t, ctx->ldx, p.problem, hx, hy, ctx->X);
   BIOT_LAUNCH(k_eliminate, div_up(nd, 256), 256, 0, s, nd, ctx->rowptr, ctx->col, ctx->nodeptr, ctx->nbr, ctx->dmask,
               ctx->val, ctx->apval);

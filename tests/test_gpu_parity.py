@@ -37,6 +37,8 @@ def cases():
         "literal_beta": base.with_(n=6, beta_mode="h", n_t=3),
         "no_beta": base.with_(n=6, beta_mode="none", n_t=3),
         "tiny": base.with_(n=1, n_t=1),
+        # Barry & Mercer point source off the nodes (n = 10: (1/4, 1/4) inside a cell)
+        "barry10": W.barry_mercer(10, 6).with_(tau=1.0 / 256),
     }
 
 
@@ -89,7 +91,7 @@ def test_assembly_rhs_and_initial_state(name):
     assert np.abs(x0 - s.x0).max() <= 1e-14 * max(np.abs(s.x0).max(), 1.0)
 
 
-@pytest.mark.parametrize("name", ["terzaghi16", "mms12", "lognormal10"])
+@pytest.mark.parametrize("name", ["terzaghi16", "mms12", "lognormal10", "barry10"])
 def test_residual_window(name):
     case = cases()[name]
     s = build_system(case)
@@ -111,7 +113,7 @@ def test_residual_window(name):
 
 
 @pytest.mark.parametrize("kind", ["tri", "diag"])
-@pytest.mark.parametrize("name", ["terzaghi16", "mms12", "lognormal10"])
+@pytest.mark.parametrize("name", ["terzaghi16", "mms12", "lognormal10", "barry10"])
 def test_precond_apply(kind, name):
     case = cases()[name].with_(precond=kind)
     s = build_system(case)
@@ -175,6 +177,20 @@ def test_converged_solve_matches_sequential_to_1e10(kind):
     eu, ep = field_rel_errors(X, Xs)
     assert st == biot.BIOT_OK and eu < 1e-10 and ep < 1e-10, (eu, ep)
     assert rel < 1e-12
+
+
+@pytest.mark.parametrize("strips,precision,bound", [(1, "fp64", 1e-10), (3, "fp64", 1e-10), (3, "fp32", 1e-8)])
+def test_barry_mercer_pint_matches_sequential(strips, precision, bound):
+    # Sec. 4.3 compares the parallel-in-time solution with sequential backward Euler (P2,
+    # tol 1e-10); here converged further, on the paper's mesh h = 1/64 over its first 40 steps
+    # (tau = 1/256), plain and substructured block solves, and FP32 sweeps with FP64 refinement
+    case = W.barry_mercer(64, 256).with_(n_t=40)
+    Xs = seq_solve(build_system(case))
+    with biot.Context(case, strips=strips, precision=precision) as c:
+        st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-13, 100000)
+        X = biot.biot_get_state(c.ctx, 0, case.n_t)
+    eu, ep = field_rel_errors(X, Xs)
+    assert st == biot.BIOT_OK and eu < bound and ep < bound, (eu, ep)
 
 
 def test_mms_tol_solve_and_edge_windows():

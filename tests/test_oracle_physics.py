@@ -153,3 +153,44 @@ def test_stabilisation_removes_pressure_oscillation():
         out[mode] = X[1][2::3].reshape(n + 1, n + 1)[n - 4:n, 2:n - 1]
     assert out["h2"].min() > 0.9 and out["h2"].max() < 1.02
     assert out["none"].min() < -0.5 and out["none"].max() > 1.5
+
+
+# ---- Barry & Mercer's point source (Sec. 4.3) ----
+
+@pytest.mark.parametrize("n", [7, 10, 16, 64])
+def test_point_source_is_the_p1_delta(n):
+    # The load of a Dirac delta is the P1 basis evaluated at the point: the weights sum to one
+    # and reproduce the point as their first moment (P1 interpolates linear functions exactly),
+    # on the three vertices of one cell whatever n (the point off the nodes for n = 7, 10).
+    from oracle.problems import point_source_weights
+    for Lx, Ly in ((1.0, 1.0), (2.0, 0.5)):
+        nodes, w = point_source_weights(n, Lx, Ly, Lx / 4, Ly / 4)
+        nx = n + 1
+        xs, ys = nodes % nx * (Lx / n), nodes // nx * (Ly / n)
+        assert np.all(w >= -1e-15) and w.sum() == pytest.approx(1.0, abs=1e-15)
+        assert w @ xs == pytest.approx(Lx / 4, abs=1e-14) and w @ ys == pytest.approx(Ly / 4, abs=1e-14)
+        assert xs.max() - xs.min() <= Lx / n * (1 + 1e-12) and ys.max() - ys.min() <= Ly / n * (1 + 1e-12)
+
+
+def test_barry_mercer_symmetry_boundary_and_sign():
+    # x <-> y maps the square, its "/"-split mesh, the source at (1/4, 1/4) and the boundary
+    # conditions onto themselves (u_x tangential on the horizontal sides <-> u_y on the
+    # vertical ones), so the discrete solution has p(x, y) = p(y, x) and u_x(x, y) = u_y(y, x).
+    # On x = 0 the tangential u_y vanishes and the normal u_x does not; p vanishes on every
+    # side. An extraction (g < 0) lowers the pressure at the source in the first step.
+    case = W.barry_mercer(16, 16)
+    s = build_system(case)
+    X = seq_solve(s)
+    nx = case.n + 1
+    P = X[:, 2::3].reshape(-1, nx, nx)
+    U = X[:, 0::3].reshape(-1, nx, nx)
+    V = X[:, 1::3].reshape(-1, nx, nx)
+    assert np.abs(P - P.transpose(0, 2, 1)).max() <= 1e-12 * np.abs(P).max()
+    assert np.abs(U - V.transpose(0, 2, 1)).max() <= 1e-12 * np.abs(U).max()
+    assert np.abs(V[:, :, 0]).max() == 0.0 and np.abs(U[:, :, 0]).max() > 1e-3 * np.abs(U).max()
+    assert np.abs(P[:, 0, :]).max() == 0.0 and np.abs(P[:, :, -1]).max() == 0.0
+    from oracle.problems import barry_mercer_beta
+    g1 = -0.5 * np.sin(barry_mercer_beta(case) * case.tau)
+    src = (case.n // 4) * nx + case.n // 4
+    assert g1 < 0 and X[1, 3 * src + 2] < 0
+    assert P[1].min() == X[1, 3 * src + 2]  # the lowest pressure sits at the source

@@ -23,6 +23,7 @@ import numpy as np
 
 TERZAGHI = "terzaghi"
 MMS = "mms"
+BARRY_MERCER = "barry_mercer"
 
 
 @dataclass(frozen=True)
@@ -48,7 +49,7 @@ class BiotCase:
     precond: str = "diag"     # "diag": P2 (block diagonal); "tri": P1 (block lower triangular)
     n_iter: int = 10          # Krylov iterations per call of the inner solver K
     tol: float = 1e-10
-    load: float = 1.0         # Terzaghi top load magnitude (traction (0, -load))
+    load: float = 1.0         # Terzaghi top load (traction (0, -load)); Barry & Mercer source amplitude 0.5 load
     name: str = ""
 
     def with_(self, **kw) -> "BiotCase":
@@ -156,6 +157,13 @@ def batched_instances(count: int = 64, seed0: int = 1000) -> list:
                             problem=TERZAGHI, precond="tri", tol=1e-8,
                             name=f"batched_{i}_n{n}_nt{n_t}"))
     return out
+
+
+def barry_mercer(n: int = 64, n_t: int = 256) -> BiotCase:
+    """Barry & Mercer's point source (Sec. 4.3): unit square, h = 1/64, tau = T/256, T = 1,
+    E = 1e5, nu = 0.1, K = 1e-2, source -0.5 delta_(1/4, 1/4) sin(beta t), P2, tol 1e-10."""
+    return BiotCase(n=n, E=1e5, nu=0.1, alpha=1.0, kappa=1e-2, tau=1.0 / n_t, n_t=n_t,
+                    problem=BARRY_MERCER, precond="diag", tol=1e-10, name=f"barry_mercer_{n}x{n}_nt{n_t}")
 
 
 def large_1024() -> BiotCase:
