@@ -438,6 +438,8 @@ def run_ours(args):
         extras["batched"] = batched_vs_sequential(stream)
     if args.lognormal:
         extras["lognormal_precisions"] = lognormal_precisions(stream, args.lognormal)
+    if args.efficiency:
+        extras["efficiency"] = efficiency_study(stream)
     out = None
     if rank == 0:
         cpu = cpu_baseline_subprocess(args.cpu_budget) if (world == 1 and not args.no_cpu) else None
@@ -610,6 +612,75 @@ def lognormal_precisions(stream, n_t):
     return out
 
 
+def efficiency_study(stream, n=64, n_t=64, Ms=(1, 2, 4, 8, 16, 32, 64)):
+    """The paper's parallel-efficiency model (Sec. 3.2, Eqs. e1_theo and E2_theo) measured on the
+    GPU, Terzaghi n x n, N_t steps, FGMRES(10) cycles, P2, FP64. For each N_thread = M:
+    * inverted time stepping, the paper schedule (Alg. 3 with window M): N_t + M - 1 sweeps of at
+      most M columns, every step M cycles (N_iter = 10 M iterations);
+    * the traditional method with the same M cycles per step, one step after another (constant
+      b^n per step): N_t M single-column sweeps.
+    T_b (forming b, the fused residual) and t_iter (one Arnoldi step) are the single-column
+    sweep's split; E1 = N_t / (M + N_t - 1), E2 = (T_b / N_iter + t_iter) / (M / N_iter T_b +
+    t_iter). On the GPU the M "threads" are the columns of one multi-RHS sweep, so the measured
+    speedup is M E / rho(M), rho(M) the cost of an M-column sweep relative to one column."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2310_10430_gb300 import biot
+    case = W.terzaghi_small().with_(n=n, n_t=n_t, precond="diag", name=f"terzaghi_{n}x{n}_nt{n_t}")
+    out = {"workload": f"{case.name}: FGMRES(10) cycles, P2, FP64, setup excluded", "rows": []}
+    # single-column sweep split: T_b (residual) and t_iter
+    with biot.Context(case, stream=stream, window=1) as c:
+        biot.biot_tune(c.ctx, None)
+        for _ in range(3):
+            biot.biot_sweep(c.ctx, 1, 1, want_rel=False)
+        torch.cuda.synchronize()
+        biot.biot_timing_enable(c.ctx, True)
+        reps = 20
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            biot.biot_sweep(c.ctx, 1, 1, want_rel=False)
+        torch.cuda.synchronize()
+        t1 = (time.perf_counter() - t0) / reps
+        res_ms, res_n = biot.biot_timing_read(c.ctx, biot.BIOT_KC_RESIDUAL)
+        biot.biot_timing_enable(c.ctx, False)
+    T_b = res_ms / res_n / 1e3
+    t_iter = max(t1 - T_b, 1e-9) / case.n_iter
+    out.update({"T_b_ms": T_b * 1e3, "t_iter_ms": t_iter * 1e3, "sweep_1col_ms": t1 * 1e3})
+    for M in Ms:
+        with biot.Context(case, stream=stream, window=M, schedule=biot.BIOT_SCHED_PAPER) as c:
+            biot.biot_tune(c.ctx, None)
+            biot.biot_pint_solve(c.ctx, 0.0, 100000, allow_not_converged=True)  # warm-up
+            biot.biot_set_state(c.ctx, 0, case.n_t, np.zeros((case.n_t + 1, case.n_dof)))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, sweeps, rel_p = biot.biot_pint_solve(c.ctx, 0.0, 100000, allow_not_converged=True)
+            torch.cuda.synchronize()
+            t_pint = time.perf_counter() - t0
+        with biot.Context(case, stream=stream, window=1) as c:
+            biot.biot_tune(c.ctx, None)
+            biot.biot_sweep(c.ctx, 1, 1, want_rel=False)  # warm-up
+            biot.biot_set_state(c.ctx, 0, case.n_t, np.zeros((case.n_t + 1, case.n_dof)))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(1, case.n_t + 1):
+                for _ in range(M):
+                    biot.biot_sweep(c.ctx, k, k, want_rel=False)
+            torch.cuda.synchronize()
+            t_seq = time.perf_counter() - t0
+            rel_s = max(float(biot.biot_residual_norms(c.ctx, k, k)[0]) for k in range(1, case.n_t + 1))
+        n_iter_total = case.n_iter * M
+        E1 = case.n_t / (M + case.n_t - 1)
+        E2 = (T_b / n_iter_total + t_iter) / (M / n_iter_total * T_b + t_iter)
+        speedup = t_seq / t_pint
+        rho = (t_pint / sweeps) / t1
+        out["rows"].append({"N_thread": M, "sweeps": sweeps, "t_pint_s": t_pint, "t_seq_s": t_seq,
+                            "speedup": speedup, "E_measured": speedup / M, "E1": E1, "E2": E2, "E1E2": E1 * E2,
+                            "rho": rho, "E1E2_over_rho": E1 * E2 / rho,
+                            "max_step_residual_pint": float(rel_p), "max_step_residual_seq": rel_s})
+    return out
+
+
 def large_mesh(args):
     """The 1024^2 stress workload (3,151,875 DOF, N_t = 128, nu = 0.49, lognormal kappa sigma 2,
     l = 0.1, P1): FP32 sweeps with the FP64 residual and update. One JSON line: the sweep
@@ -773,6 +844,9 @@ def main():
     ap.add_argument("--tune-cache", default=None,
                     help="band-solve tuning cache (JSON): read if present, written otherwise; profiling runs "
                          "use it to replay the plain run's variant choice")
+    ap.add_argument("--efficiency", action="store_true",
+                    help="also measure the paper's efficiency model (E1, E2) on Terzaghi 64^2, N_t = 64, for "
+                         "N_thread = 1 .. 64 (paper schedule against the same cycles step by step)")
     ap.add_argument("--large", action="store_true",
                     help="run only the 1024^2 stress workload (N_t = 128, nu = 0.49, lognormal sigma 2, P1, FP32 "
                          "sweeps with FP64 refinement): setup, --steps timed sweeps, one JSON line")
