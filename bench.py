@@ -191,21 +191,40 @@ class ClockSampler:
 # roofline helpers
 # ---------------------------------------------------------------------------
 
+def strip_envelope(w, C, d):
+    """Off-diagonal entries of the Cholesky factor of one strip interior: the strip's nodes in
+    order (rows j outer, its w node columns inner), d fields each; row r of node (ii, j) reaches
+    back to the first field of its lowest-numbered neighbour among (ii - 1, j - 1), (ii, j - 1),
+    (ii - 1, j) and itself (the "/"-split mesh), and a factor fills its matrix's row envelope.
+    At most the half-band d (w + 2) - 1 that the band kernels sweep (the rows of a strip's first
+    node column and its first node row reach back less)."""
+    import numpy as np
+    j, ii = np.meshgrid(np.arange(C), np.arange(w), indexing="ij")
+    node = j * w + ii
+    low = node.copy()
+    low = np.where(ii >= 1, node - 1, low)                        # (ii - 1, j)
+    low = np.where(j >= 1, (j - 1) * w + ii, low)                 # (ii, j - 1)
+    low = np.where((j >= 1) & (ii >= 1), (j - 1) * w + ii - 1, low)  # (ii - 1, j - 1)
+    back = d * (node - low)                                       # field 0 of the node
+    return float(sum(back.sum() + f * back.size for f in range(d)))
+
+
 def band_solve_flops(info, ncols, precond, strips=0, dense_sep=(True, True)):
-    """Algorithmic FP64 flops of the exact block solves of one P apply: 2 flops per band
-    entry per column of every triangular solve, tri(N, b) = 2 W (N b - b (b + 1) / 2).
+    """Algorithmic FP64 flops of the exact block solves of one P apply: 2 flops per structurally
+    nonzero off-diagonal factor entry per column of every triangular solve.
 
     Plain band factors (strips < 2): forward + backward on A (half-band 2n+5) and on S
-    (n+2). Substructured (strips >= 2, the library's layout): per block (d = 2 for A, 1 for
-    S) two forward + backward pairs on every strip interior (N_t = d w_t (n + 1) rows,
-    half-band d (w_max + 2) - 1) and one pair on the separators' Schur complement, whose
-    factor is block bidiagonal with B = d (n + 1): row rho of block m > 0 has B + rho
-    off-diagonal entries, of block 0 rho (the rest of its half-band 2B - 1 is exact zeros,
-    skipped by the solve), plus the two sparse couplings (2 flops per separator-interior
-    entry per column, twice). The dense-block separator solves (dense_sep[block]) take
-    the same multiply-adds as the band substitution (block-diagonal products with the
-    inverted diagonal blocks: B^2 / 2 per block; chain products: B^2 per block but the
-    first). Also returns the launches of one apply."""
+    (n+2), tri(N, b) = 2 W (N b - b (b + 1) / 2). Substructured (strips >= 2, the library's
+    layout): per block (d = 2 for A, 1 for S) two forward + backward pairs on every strip
+    interior (its factor's row envelope, strip_envelope) and one pair on the separators' Schur
+    complement, whose factor is block bidiagonal with B = d (n + 1): a dense lower triangle per
+    block and a dense B x B block below it for every block but the first (the rest of its
+    half-band 2B - 1 is exact zeros, skipped by the solves), plus the two sparse couplings (2 flops
+    per separator-interior entry per column, twice: each separator node has four interior
+    neighbours, two fewer on the first and last node rows). The dense-block separator solves
+    (dense_sep[block]) do the same multiply-adds (block-diagonal products with the inverted
+    diagonal blocks: B (B - 1) / 2 per block; chain products: B^2 per block but the first).
+    Also returns the launches of one apply."""
     def tri(N, b):
         return 2.0 * ncols * (N * b - b * (b + 1) / 2.0)
     n = round((info.n_nodes) ** 0.5) - 1
@@ -219,12 +238,10 @@ def band_solve_flops(info, ncols, precond, strips=0, dense_sep=(True, True)):
     total = 0.0
     launches = 0
     for blk, d in enumerate((2, 1)):
-        bI = d * (max(widths) + 2) - 1
-        interior = sum(tri(d * w * C, bI) for w in widths)
+        interior = 2.0 * ncols * sum(strip_envelope(w, C, d) for w in widths)
         B, nb = d * C, strips - 1
         sep = 2.0 * ncols * (B * (B - 1) / 2.0 + (nb - 1) * (B * B + B * (B - 1) / 2.0))
-        # each separator node couples to its 4 interior neighbours (i +- 1 columns): d*d entries each
-        coupling = 2 * 2.0 * ncols * (strips - 1) * C * 4 * d * d
+        coupling = 2 * 2.0 * ncols * nb * (4 * C - 2) * d * d
         total += 4 * interior + 2 * sep + coupling
         # gather, 2 x interior pair, 2 couplings, scatter; separators: a pair of band solves,
         # or two block-diagonal products and two chains of nb - 1 products
