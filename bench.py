@@ -457,6 +457,8 @@ def run_ours(args):
         extras["lognormal_precisions"] = lognormal_precisions(stream, args.lognormal)
     if args.efficiency:
         extras["efficiency"] = efficiency_study(stream)
+    if args.barry_mercer:
+        extras["barry_mercer"] = barry_mercer_study(stream)
     out = None
     if rank == 0:
         cpu = cpu_baseline_subprocess(args.cpu_budget) if (world == 1 and not args.no_cpu) else None
@@ -698,6 +700,36 @@ def efficiency_study(stream, n=64, n_t=64, Ms=(1, 2, 4, 8, 16, 32, 64)):
     return out
 
 
+def barry_mercer_study(stream):
+    """Barry & Mercer's point source as the paper runs it (Sec. 4.3: 64^2, tau = 1/256, T = 1,
+    P2, tol 1e-10): backward Euler one step after another (window 1: each step converged before
+    the next) against the parallel-in-time sweep over all 256 steps, in FP64 and with FP32
+    sweeps and FP64 refinement; wall times (setup excluded), sweeps, per-field differences."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2310_10430_gb300 import biot
+    case = W.barry_mercer()
+    out = {"workload": f"{case.name}: P2, tol {case.tol}, setup excluded"}
+    ref = None
+    for name, window, prec in (("sequential_fp64", 1, "fp64"), ("pint_fp64", 0, "fp64"), ("pint_fp32", 0, "fp32")):
+        with biot.Context(case, stream=stream, window=window, precision=prec) as c:
+            biot.biot_tune(c.ctx, None)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, sweeps, rel = biot.biot_pint_solve(c.ctx, case.tol, 1000000, allow_not_converged=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            X = biot.biot_get_state(c.ctx, 0, case.n_t)
+        row = {"seconds": dt, "sweeps": sweeps, "status": biot.STATUS_NAMES[st], "rel_residual": rel}
+        if ref is None:
+            ref = X
+        else:
+            row["rel_diff_u"], row["rel_diff_p"] = _field_errors(np, X, ref)
+        out[name] = row
+    return out
+
+
 def large_mesh(args):
     """The 1024^2 stress workload (3,151,875 DOF, N_t = 128, nu = 0.49, lognormal kappa sigma 2,
     l = 0.1, P1): FP32 sweeps with the FP64 residual and update. One JSON line: the sweep
@@ -864,6 +896,9 @@ def main():
     ap.add_argument("--efficiency", action="store_true",
                     help="also measure the paper's efficiency model (E1, E2) on Terzaghi 64^2, N_t = 64, for "
                          "N_thread = 1 .. 64 (paper schedule against the same cycles step by step)")
+    ap.add_argument("--barry-mercer", action="store_true",
+                    help="also solve Barry & Mercer's point source (64^2, 256 steps, P2, tol 1e-10) step by "
+                         "step and parallel in time, FP64 and FP32, and report times and differences")
     ap.add_argument("--large", action="store_true",
                     help="run only the 1024^2 stress workload (N_t = 128, nu = 0.49, lognormal sigma 2, P1, FP32 "
                          "sweeps with FP64 refinement): setup, --steps timed sweeps, one JSON line")
