@@ -55,7 +55,7 @@ typedef enum {
   BIOT_E_STATE = 4,          /* call made before the step it depends on */
   BIOT_E_NOT_CONVERGED = 5,  /* max_outer sweeps done, tolerance not met; state stays readable */
   BIOT_E_DIVERGED = 6,       /* residual non-finite or grew by more than 1e6 */
-  BIOT_E_TIMEOUT = 7         /* a bounded device wait ran out (batched persistent launch) */
+  BIOT_E_TIMEOUT = 7         /* a bounded device wait ran out (band-row bulk copy of a block solve) */
 } biot_status;
 
 typedef enum {
@@ -73,7 +73,7 @@ typedef enum {
   BIOT_TERZAGHI = 0,         /* consolidation column: top load, drained top, fixed bottom, roller sides */
   BIOT_MMS_TRIG = 1,         /* manufactured cos t cos 3 pi x cos 3 pi y solution, Dirichlet on all sides (Sec. 4.1) */
   BIOT_BARRY_MERCER = 2      /* point source -0.5 load delta_(a/4, b/4) sin(beta t), beta = (lambda + 2 mu) K / (a b);
-                                drained, zero tangential displacement on every side (Sec. 4.3) */
+                                drained, zero tangential displacement on every side (Sec. 4.2) */
 } biot_problem;
 
 typedef enum {
@@ -281,8 +281,11 @@ biot_status biot_timing_read(biot_ctx* ctx, int32_t kernel_class, double* total_
  * partials it reads, so nothing needs clearing, but all calls share the array:
  * calls that overlap on the GPU (other streams, other host threads) race and
  * must be serialised by the caller. The first call on a device looks up the
- * array's device address (once per device) and should therefore be made
- * before any stream capture.
+ * array's device address and should therefore be made before any stream
+ * capture; later calls on a stream that is not capturing look it up again
+ * (no allocation), so the entry point keeps working after cudaDeviceReset,
+ * while a call on a capturing stream uses the address found by the last
+ * earlier call on that device.
  *
  * Errors: BIOT_E_INVALID for a NULL buffer, n_nodes < 1, ncols outside
  * 1..BIOT_NOALLOC_MAX_COLS, lo < 1, ldx < lo + ncols or ldr < ncols;
@@ -325,6 +328,17 @@ typedef struct {
  * the separator variants, the interior + separator pair times (ms_u, ms_p), their
  * separator parts (ms_sep_u, ms_sep_p) and the strip count. */
 biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out);
+
+/* Failure-detection test hook. Every bulk copy of band rows into shared memory is
+ * awaited with a bounded spin (clock64 budget, about 2 s by default); when the
+ * first wait of a block runs out, the kernel records the failure in the
+ * context's device status, lets every copy still in flight land (those drain
+ * waits keep the full budget) and returns, and biot_pint_solve then returns
+ * BIOT_E_TIMEOUT with the context still usable. This call sets the budget of
+ * that first wait on the current device to `cycles` SM clock cycles (a few
+ * cycles make it run out on purpose); cycles <= 0 restores the default.
+ * Synchronous; affects every context on the device. Errors: BIOT_E_CUDA. */
+biot_status biot_debug_set_wait_budget(int64_t cycles);
 
 /* Kernel launches issued by this library since it was loaded (all contexts). */
 int64_t biot_launch_count(void);

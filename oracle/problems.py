@@ -12,7 +12,7 @@ printed source g carries a sign error in its first term (it must be symmetric
 under x <-> y because the solution is). Reading A3: both sources are derived
 here from the PDE (biotsys1)-(biotsys2) for the stated solution.
 
-Barry & Mercer's problem (Sec. 4.3): the domain [0, a] x [0, b] is drained on every side
+Barry & Mercer's problem (Sec. 4.2): the domain [0, a] x [0, b] is drained on every side
 (p = 0) with zero tangential displacement there (u_y = 0 on x = 0, a; u_x = 0 on y = 0, b;
 the normal component is left free, traction-free in the normal direction: reading A14), a
 point source g(t) = -0.5 load delta_{(x0, y0)} sin(beta t) with beta = (lambda + 2 mu) K / (a b)

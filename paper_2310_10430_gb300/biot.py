@@ -104,6 +104,7 @@ _SIGNATURES = {
                                                    ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P, _P]),
     "biot_tune": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(BiotTuning)]),
     "biot_launch_count": (ctypes.c_int64, []),
+    "biot_debug_set_wait_budget": (ctypes.c_int, [ctypes.c_int64]),
     "biot_last_error": (ctypes.c_char_p, [_P]),
     "biot_destroy": (None, [_P]),
 }
@@ -308,6 +309,12 @@ def biot_tune(ctx, cache_path: Optional[str] = None) -> BiotTuning:
 
 def biot_launch_count() -> int:
     return int(lib().biot_launch_count())
+
+
+def biot_debug_set_wait_budget(cycles: int):
+    """Failure-detection test hook: budget (SM cycles) of the first bounded wait of every
+    band-solve block on the current device; cycles <= 0 restores the default."""
+    _check(lib().biot_debug_set_wait_budget(int(cycles)), None, "biot_debug_set_wait_budget")
 
 
 def biot_last_error(ctx=None) -> str:

@@ -369,12 +369,17 @@ biot_status tol_schedule(biot_ctx* ctx, double tol, int max_sweeps, int stall_ca
     const int nc = hi - lo + 1;
     if (sizeof(T) == 8) BIOT_TRY(residual_window(ctx, lo, nc, rel.data()));
     else BIOT_TRY(residual_window_lp(ctx, lo, nc, rel.data()));
+    // a timed-out device wait leaves partial solves behind: report it before the divergence it causes
     for (int c = 0; c < nc; ++c)
-      if (!std::isfinite(rel[c]))
+      if (!std::isfinite(rel[c])) {
+        BIOT_TRY(device_status(ctx));
         return fail(ctx, BIOT_E_DIVERGED, "non-finite residual at step %d, sweep %d", lo + c, w);
+      }
     if (first < 0.0) first = rel[0];
-    if (first > 0.0 && rel[0] > 1e6 * std::max(first, 1.0))
+    if (first > 0.0 && rel[0] > 1e6 * std::max(first, 1.0)) {
+      BIOT_TRY(device_status(ctx));
       return fail(ctx, BIOT_E_DIVERGED, "residual of step %d grew to %.3g", lo, rel[0]);
+    }
     int k = 0;
     while (k < nc && (rel[k] <= tol || (k == 0 && stall_cap > 0 && w - lo_since >= stall_cap))) ++k;
     BIOT_TRY(fgmres_cycle<T>(ctx, lo, k, nc - k));
@@ -625,6 +630,9 @@ biot_status biot_pint_solve(biot_ctx* ctx, double tol, int32_t max_outer, int32_
   const int n_t = ctx->n_t;
   int w = 0;
   biot_status result = BIOT_OK;
+  // every solve starts with a clear device status (a timed-out wait of an earlier call
+  // does not carry over)
+  BIOT_CU(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(int32_t), ctx->stream));
   if (ctx->prm.schedule == BIOT_SCHED_PAPER) {
     const int M = ctx->prm.window > 0 ? ctx->prm.window : n_t;
     if (M > ctx->wcap) return fail(ctx, BIOT_E_INVALID, "paper schedule needs window <= %d", ctx->wcap);

@@ -364,6 +364,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
 
+// Budget of the first wait of every block (the one that can report a timeout). Equal to
+// kWaitBudget unless a test shortens it with biot_debug_set_wait_budget; the waits that drain
+// copies still in flight before a CTA exits always keep the full kWaitBudget, so no CTA
+// releases shared memory that a bulk copy is still writing.
+__constant__ long long c_first_wait_budget = kWaitBudget;
+
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Ring rows R of the TMA-staged body, which indexes its ring modulo R (any R): phase 1 of a
@@ -503,7 +509,7 @@ band_solve_tma_body(int N, int b, const T* __restrict__ band, const T* __restric
       rhs_next = (part < ncl && in < N) ? read_rhs(in, cbase + part) : T(0);
     }
     // band rows of this block: wait for the bulk copy (bounded)
-    const bool ok = mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), kWaitBudget);
+    const bool ok = mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), c_first_wait_budget);
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
         atomicExch(err, 1);
@@ -756,7 +762,7 @@ k_band_solve_rows(int N, int b, const T* __restrict__ band, const T* __restrict_
     const int i = I * NB + r;
     const T rh0 = rn0, rh1 = rn1;
     if (bi + 1 < nblk) read_rhs(block_of(bi + 1) * NB + r, rn0, rn1);
-    const bool ok = mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), kWaitBudget);
+    const bool ok = mbar_wait_bounded(&bar[bi & 1], (uint32_t)((bi >> 1) & 1), c_first_wait_budget);
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
         atomicExch(err, 1);
@@ -1138,7 +1144,7 @@ k_band_solve_tile(int N, int b, const float* __restrict__ tiles, const float* __
       const int in = block_of(bi + 1) * NB + orow;
       rhs_next = (owner && ocol < ncl && in < N) ? read_rhs(in, cbase + ocol) : 0.f;
     }
-    const bool ok = mbar_wait_bounded(&bar[slot], phase, kWaitBudget);
+    const bool ok = mbar_wait_bounded(&bar[slot], phase, c_first_wait_budget);
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
         atomicExch(err, 1);
@@ -1575,3 +1581,11 @@ void to_f32(biot_ctx* ctx, const double* in, float* out, size_t n) {
 }
 
 }  // namespace biot
+
+extern "C" biot_status biot_debug_set_wait_budget(int64_t cycles) {
+  const long long v = cycles <= 0 ? biot::kWaitBudget : std::min<long long>(cycles, biot::kWaitBudget);
+  cudaError_t e = cudaMemcpyToSymbol(biot::c_first_wait_budget, &v, sizeof(v));
+  if (e != cudaSuccess)
+    return biot::fail(nullptr, BIOT_E_CUDA, "biot_debug_set_wait_budget: %s", cudaGetErrorString(e));
+  return BIOT_OK;
+}

@@ -39,14 +39,20 @@ __global__ void k_rel_from_partials(const double* __restrict__ part, int nblocks
   rel[c] = q > 0.0 ? r / q : (r == 0.0 ? 0.0 : INFINITY);
 }
 
-// Device address of g_noalloc_partials on the current device (looked up once per device).
-biot_status scratch_address(void** out) {
+// Device address of g_noalloc_partials on the current device. Looked up on the first call
+// per device; looked up again on every call whose stream is not capturing, so that a
+// device reset (which reloads the module at a possibly different address) is followed.
+// A capturing stream uses the address cached by an earlier call.
+biot_status scratch_address(cudaStream_t s, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(nullptr, BIOT_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, BIOT_E_CUDA, "device ordinal %d unsupported", dev);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return fail(nullptr, BIOT_E_CUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
   std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (!g_addr[dev]) {
+  if (!g_addr[dev] || cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess || p == nullptr)
@@ -73,11 +79,12 @@ extern "C" biot_status biot_residual_norms_noalloc(int32_t n_nodes, const int32_
   if (ncols < 1 || ncols > kNoAllocMaxCols)
     return fail(nullptr, BIOT_E_INVALID, "biot_residual_norms_noalloc: ncols = %d outside 1..%d (fixed scratch size)",
                 ncols, kNoAllocMaxCols);
-  if (lo < 1 || ldx < lo + ncols || ldr < ncols)
+  // in 64 bits: lo + ncols overflows int32 for lo near INT32_MAX
+  if (lo < 1 || (int64_t)ldx < (int64_t)lo + ncols || ldr < ncols)
     return fail(nullptr, BIOT_E_INVALID, "biot_residual_norms_noalloc: need lo >= 1, ldx >= lo + ncols, ldr >= ncols");
-  void* part = nullptr;
-  BIOT_TRY(scratch_address(&part));
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  void* part = nullptr;
+  BIOT_TRY(scratch_address(s, &part));
   double* p = static_cast<double*>(part);
   launch_residual_raw(n_nodes, nodeptr, nbr, rowptr, val, ap_pp, dscale, X, F, ldx, lo, ncols, R, ldr, p,
                       kNoAllocMaxCols, s);

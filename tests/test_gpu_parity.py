@@ -181,7 +181,7 @@ def test_converged_solve_matches_sequential_to_1e10(kind):
 
 @pytest.mark.parametrize("strips,precision,bound", [(1, "fp64", 1e-10), (3, "fp64", 1e-10), (3, "fp32", 1e-8)])
 def test_barry_mercer_pint_matches_sequential(strips, precision, bound):
-    # Sec. 4.3 compares the parallel-in-time solution with sequential backward Euler (P2,
+    # Sec. 4.2 compares the parallel-in-time solution with sequential backward Euler (P2,
     # tol 1e-10); here converged further, on the paper's mesh h = 1/64 over its first 40 steps
     # (tau = 1/256), plain and substructured block solves, and FP32 sweeps with FP64 refinement
     case = W.barry_mercer(64, 256).with_(n_t=40)

@@ -155,7 +155,7 @@ def test_stabilisation_removes_pressure_oscillation():
     assert out["none"].min() < -0.5 and out["none"].max() > 1.5
 
 
-# ---- Barry & Mercer's point source (Sec. 4.3) ----
+# ---- Barry & Mercer's point source (Sec. 4.2) ----
 
 @pytest.mark.parametrize("n", [7, 10, 16, 64])
 def test_point_source_is_the_p1_delta(n):
@@ -194,3 +194,19 @@ def test_barry_mercer_symmetry_boundary_and_sign():
     src = (case.n // 4) * nx + case.n // 4
     assert g1 < 0 and X[1, 3 * src + 2] < 0
     assert P[1].min() == X[1, 3 * src + 2]  # the lowest pressure sits at the source
+
+
+def test_barry_mercer_beta_against_hand_worked_value():
+    # The source frequency beta = (lambda + 2 mu) K / (a b) of Sec. 4.2, worked by hand at
+    # the paper's E = 1e5, nu = 0.1, K = 1e-2 on the unit square (fractions in the golden
+    # file). A slip such as lambda + mu, a dropped K or a missing 1 / (a b) moves it by 45 %,
+    # 100x or the domain area; a rectangle checks the 1 / (a b) factor.
+    from oracle.problems import barry_mercer_beta
+    g = json.load(open(os.path.join(GOLDEN, "barry_mercer_beta.json")))
+    case = W.barry_mercer(16, 16)
+    assert (case.E, case.nu, float(case.kappa_elem()[0])) == (g["E"], g["nu"], g["K"])
+    lam, mu = lame(case.E, case.nu)
+    assert lam == pytest.approx(g["lambda"], rel=1e-14) and mu == pytest.approx(g["mu"], rel=1e-14)
+    assert barry_mercer_beta(case) == pytest.approx(g["beta"], rel=1e-14)
+    assert barry_mercer_beta(case.with_(Lx=2.0, Ly=0.5)) == pytest.approx(g["beta"], rel=1e-14)
+    assert barry_mercer_beta(case.with_(Lx=2.0, Ly=2.0)) == pytest.approx(g["beta"] / 4.0, rel=1e-14)

@@ -65,11 +65,16 @@ def test_noalloc_matches_context_entry_point(name, lo):
     for call in range(2):
         Rd = torch.full((case.n_dof, ldr), np.nan, dtype=torch.float64, device="cuda")
         reld = torch.full((ncols,), np.nan, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         biot.biot_residual_norms_noalloc(case.n_nodes, sysd["nodeptr"].data_ptr(), sysd["nbr"].data_ptr(),
                                          sysd["rowptr"].data_ptr(), sysd["val"].data_ptr(), sysd["ap"].data_ptr(),
                                          sysd["dsc"].data_ptr(), Xd.data_ptr(), Fd.data_ptr(), ldx, lo, ncols,
                                          Rd.data_ptr(), ldr, reld.data_ptr(), stream)
         torch.cuda.synchronize()
+        if call == 1:
+            # the defining property: a call after the first takes no device memory
+            assert torch.cuda.mem_get_info()[0] == free_before
         rel = reld.cpu().numpy()
         R = Rd.cpu().numpy()[:, :ncols].T / dsc                      # undo the equilibration
         np.testing.assert_allclose(rel, rel_ref, rtol=1e-12, atol=0)
@@ -84,3 +89,12 @@ def test_noalloc_rejects_oversized_window():
         biot.biot_residual_norms_noalloc(4, p, p, p, p, p, p, p, p, 600, 1, 513, p, 513, p)
     assert e.value.status == biot.BIOT_E_INVALID
     assert "1..512" in biot.biot_last_error(None)
+
+
+def test_noalloc_rejects_window_past_int32():
+    # lo + ncols beyond 2^31 - 1 must be rejected, not wrapped around
+    z = torch.zeros(8, dtype=torch.float64, device="cuda")
+    p = z.data_ptr()
+    with pytest.raises(biot.BiotError) as e:
+        biot.biot_residual_norms_noalloc(4, p, p, p, p, p, p, p, p, 100, 2**31 - 10, 20, p, 20, p)
+    assert e.value.status == biot.BIOT_E_INVALID

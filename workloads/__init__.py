@@ -160,7 +160,7 @@ def batched_instances(count: int = 64, seed0: int = 1000) -> list:
 
 
 def barry_mercer(n: int = 64, n_t: int = 256) -> BiotCase:
-    """Barry & Mercer's point source (Sec. 4.3): unit square, h = 1/64, tau = T/256, T = 1,
+    """Barry & Mercer's point source (Sec. 4.2): unit square, h = 1/64, tau = T/256, T = 1,
     E = 1e5, nu = 0.1, K = 1e-2, source -0.5 delta_(1/4, 1/4) sin(beta t), P2, tol 1e-10."""
     return BiotCase(n=n, E=1e5, nu=0.1, alpha=1.0, kappa=1e-2, tau=1.0 / n_t, n_t=n_t,
                     problem=BARRY_MERCER, precond="diag", tol=1e-10, name=f"barry_mercer_{n}x{n}_nt{n_t}")
