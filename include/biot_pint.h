@@ -84,7 +84,9 @@ typedef enum {
 
 typedef enum {
   BIOT_SCHED_TOL = 0,        /* retire the oldest active step once its relative residual <= tol */
-  BIOT_SCHED_PAPER = 1       /* every step gets exactly `window` outer iterations (N_thread of Alg. 3) */
+  BIOT_SCHED_PAPER = 1,      /* every step gets exactly `window` outer iterations (N_thread of Alg. 3) */
+  BIOT_SCHED_EAGER = 2       /* as BIOT_SCHED_TOL with every step active from the first sweep (up to the
+                                window capacity) instead of step n from sweep n */
 } biot_schedule;
 
 typedef struct {
@@ -167,8 +169,9 @@ biot_status biot_set_substructure(biot_ctx* ctx, int32_t strips);
  * step n becomes active at sweep n, which reproduces Alg. 3's iterates
  * X^{n,m}, m = w - n + 1. Tol schedule: the oldest active step retires once its
  * predecessor is retired and |D^{-1/2} r_n| <= tol |D^{-1/2} b_n| (D = |diag AA|);
- * paper schedule: every step gets `window` outer iterations, tol is ignored.
- * With precision BIOT_FP32/BF16, the sweep runs in reduced precision as the
+ * paper schedule: every step gets `window` outer iterations, tol is ignored;
+ * eager schedule: the tol schedule with every step (up to the window capacity)
+ * active from the first sweep. With precision BIOT_FP32/BF16, the sweep runs in reduced precision as the
  * correction solver of an FP64 iterative refinement on the space-time system.
  * Outputs (nullable): sweeps_done, final_rel_res = relative equilibrated
  * space-time residual |D^{-1/2}(F - calA X)| / |D^{-1/2} F| in FP64.
@@ -176,6 +179,13 @@ biot_status biot_set_substructure(biot_ctx* ctx, int32_t strips);
  * (state readable), BIOT_E_DIVERGED, BIOT_E_STATE (no preconditioner). */
 biot_status biot_pint_solve(biot_ctx* ctx, double tol, int32_t max_outer,
                             int32_t* sweeps_done, double* final_rel_res);
+
+/* Change the schedule of later biot_pint_solve calls (biot_schedule) without
+ * reassembling, e.g. to continue from a state set by biot_set_state with the
+ * eager start. BIOT_SCHED_PAPER keeps the `window` given at assembly as its
+ * iterations per step. Errors: BIOT_E_STATE (before biot_assemble),
+ * BIOT_E_INVALID (unknown schedule, paper window above the capacity). */
+biot_status biot_set_schedule(biot_ctx* ctx, int32_t schedule);
 
 /* Solve `count` independent instances together (batched form of biot_pint_solve).
  * Each context is created, assembled (precision BIOT_FP32 or

@@ -190,7 +190,7 @@ class SweepLog:
     retired_upto: list = field(default_factory=list)
 
 
-def pint_sweeps(sys, P, n_iter, mode="tol", M=None, tol=1e-10, w_max=None, max_sweeps=100000):
+def pint_sweeps(sys, P, n_iter, mode="tol", M=None, tol=1e-10, w_max=None, max_sweeps=100000, X0=None):
     """Windowed snapshot sweeps (reading A5). Returns (X, n_sweeps, converged, SweepLog).
 
     mode "paper": step n is updated at sweeps n .. n + M - 1 (M = N_thread of
@@ -200,10 +200,14 @@ def pint_sweeps(sys, P, n_iter, mode="tol", M=None, tol=1e-10, w_max=None, max_s
     steps are formed from the snapshot; starting at lo, steps whose residual is
     <= tol retire (no update), stopping at the first that is not. The solve ends
     when every step has retired.
+    mode "eager": as "tol" with every step active from the first sweep, window
+    [lo, min(N_t, lo + w_max - 1)] (the start that suits a state that is already
+    close to the solution, e.g. a continuation).
+    X0 (optional): starting state [N_t + 1, N_dof] (row 0 is replaced by x0); zero otherwise.
     """
     n_t = sys.F.shape[0] - 1
     d = sys.dscale()
-    X = np.zeros((n_t + 1, sys.n_dof))
+    X = np.zeros((n_t + 1, sys.n_dof)) if X0 is None else np.array(X0, dtype=np.float64)
     X[0] = sys.x0
     log = SweepLog()
     if w_max is None:
@@ -220,7 +224,7 @@ def pint_sweeps(sys, P, n_iter, mode="tol", M=None, tol=1e-10, w_max=None, max_s
             if lo > n_t:
                 return X, w, True, log
             w += 1
-            a, z = lo, min(w, n_t, lo + w_max - 1)
+            a, z = lo, min(n_t if mode == "eager" else w, n_t, lo + w_max - 1)
         Xs = X.copy()
         rel = []
         res = {}
@@ -233,7 +237,7 @@ def pint_sweeps(sys, P, n_iter, mode="tol", M=None, tol=1e-10, w_max=None, max_s
         log.lo.append(a)
         log.hi.append(z)
         log.rel.append(rel)
-        if mode == "tol":
+        if mode in ("tol", "eager"):
             while lo <= z and rel[lo - a] <= tol:
                 lo += 1
             a = lo

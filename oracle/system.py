@@ -64,10 +64,13 @@ def eliminate(M, dofs, diag_values):
     return M
 
 
-def build_system(case) -> BiotSystem:
+def build_system(case, beta=None) -> BiotSystem:
+    """The eliminated system of `case`. beta (optional) overrides the stabilisation factor
+    of the case's own mesh size (the coarse levels of the multigrid keep the fine one)."""
     coords, tris = structured_mesh(case.n, case.Lx, case.Ly)
     h = max(case.Lx, case.Ly) / case.n
-    beta = stabilisation_beta(case.E, case.nu, h, case.beta_mode)
+    if beta is None:
+        beta = stabilisation_beta(case.E, case.nu, h, case.beta_mode)
     AA_full, Ap_full = assemble(coords, tris, case.E, case.nu, case.alpha,
                                 case.kappa_elem(), case.tau, beta)
     n_dof = AA_full.shape[0]

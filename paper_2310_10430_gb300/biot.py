@@ -23,7 +23,7 @@ BIOT_PRECOND_TRI, BIOT_PRECOND_DIAG = 1, 2
 BIOT_FP64, BIOT_FP32, BIOT_BF16VAL_FP32ACC = 0, 1, 2
 BIOT_TERZAGHI, BIOT_MMS_TRIG, BIOT_BARRY_MERCER = 0, 1, 2
 BIOT_BETA_H2, BIOT_BETA_H, BIOT_BETA_NONE = 0, 1, 2
-BIOT_SCHED_TOL, BIOT_SCHED_PAPER = 0, 1
+BIOT_SCHED_TOL, BIOT_SCHED_PAPER, BIOT_SCHED_EAGER = 0, 1, 2
 BIOT_KC_RESIDUAL, BIOT_KC_SPMM, BIOT_KC_BAND_SOLVE = 0, 1, 2
 
 
@@ -86,6 +86,7 @@ _SIGNATURES = {
     "biot_precond_setup": (ctypes.c_int, [_P, ctypes.c_int32]),
     "biot_set_substructure": (ctypes.c_int, [_P, ctypes.c_int32]),
     "biot_pint_solve": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int32, _I32, _D]),
+    "biot_set_schedule": (ctypes.c_int, [_P, ctypes.c_int32]),
     "biot_sweep": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _D]),
     "biot_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                         ctypes.c_int32, _I32, _D]),
@@ -185,6 +186,10 @@ def biot_precond_setup(ctx, kind: int):
 
 def biot_set_substructure(ctx, strips: int):
     _check(lib().biot_set_substructure(ctx, int(strips)), ctx, "biot_set_substructure")
+
+
+def biot_set_schedule(ctx, schedule: int):
+    _check(lib().biot_set_schedule(ctx, int(schedule)), ctx, "biot_set_schedule")
 
 
 def biot_pint_solve(ctx, tol: float, max_outer: int, allow_not_converged: bool = False):

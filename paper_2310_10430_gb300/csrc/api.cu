@@ -365,7 +365,9 @@ biot_status tol_schedule(biot_ctx* ctx, double tol, int max_sweeps, int stall_ca
       return BIOT_OK;
     }
     ++w;
-    const int hi = std::min(std::min(w, n_t), lo + ctx->wcap - 1);
+    // causal start: step n becomes active at sweep n; eager start: every step from sweep 1
+    const int top = ctx->prm.schedule == BIOT_SCHED_EAGER ? n_t : std::min(w, n_t);
+    const int hi = std::min(top, lo + ctx->wcap - 1);
     const int nc = hi - lo + 1;
     if (sizeof(T) == 8) BIOT_TRY(residual_window(ctx, lo, nc, rel.data()));
     else BIOT_TRY(residual_window_lp(ctx, lo, nc, rel.data()));
@@ -544,7 +546,8 @@ biot_status biot_assemble(biot_ctx* ctx, const biot_params* p) {
   if (p->problem != BIOT_TERZAGHI && p->problem != BIOT_MMS_TRIG && p->problem != BIOT_BARRY_MERCER)
     return fail(ctx, BIOT_E_INVALID, "problem");
   if (p->beta_mode < BIOT_BETA_H2 || p->beta_mode > BIOT_BETA_NONE) return fail(ctx, BIOT_E_INVALID, "beta_mode");
-  if (p->schedule != BIOT_SCHED_TOL && p->schedule != BIOT_SCHED_PAPER) return fail(ctx, BIOT_E_INVALID, "schedule");
+  if (p->schedule != BIOT_SCHED_TOL && p->schedule != BIOT_SCHED_PAPER && p->schedule != BIOT_SCHED_EAGER)
+    return fail(ctx, BIOT_E_INVALID, "schedule");
   if (p->precision < BIOT_FP64 || p->precision > BIOT_BF16VAL_FP32ACC)
     return fail(ctx, BIOT_E_INVALID, "precision %d", p->precision);
   if (p->window < 0) return fail(ctx, BIOT_E_INVALID, "window must be >= 0");
@@ -620,12 +623,23 @@ biot_status biot_residual_norms(biot_ctx* ctx, int32_t lo, int32_t hi, double* r
   return residual_window(ctx, lo, hi - lo + 1, rel_out);
 }
 
+biot_status biot_set_schedule(biot_ctx* ctx, int32_t schedule) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  BIOT_TRY(need_assembled(ctx));
+  if (schedule != BIOT_SCHED_TOL && schedule != BIOT_SCHED_PAPER && schedule != BIOT_SCHED_EAGER)
+    return fail(ctx, BIOT_E_INVALID, "schedule %d", schedule);
+  if (schedule == BIOT_SCHED_PAPER && ctx->prm.window > ctx->wcap)
+    return fail(ctx, BIOT_E_INVALID, "paper schedule needs window <= %d", ctx->wcap);
+  ctx->prm.schedule = schedule;
+  return BIOT_OK;
+}
+
 biot_status biot_pint_solve(biot_ctx* ctx, double tol, int32_t max_outer, int32_t* sweeps_done,
                             double* final_rel_res) {
   if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
   BIOT_TRY(need_precond(ctx));
   if (max_outer < 1) return fail(ctx, BIOT_E_INVALID, "max_outer must be >= 1");
-  if (ctx->prm.schedule == BIOT_SCHED_TOL && !(tol >= 0.0))
+  if (ctx->prm.schedule != BIOT_SCHED_PAPER && !(tol >= 0.0))
     return fail(ctx, BIOT_E_INVALID, "tol must be >= 0");
   const int n_t = ctx->n_t;
   int w = 0;

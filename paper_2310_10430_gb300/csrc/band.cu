@@ -354,12 +354,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for phase `parity` of *bar for at most ~budget SM cycles; false on timeout.
+// Wait for phase `parity` of *bar for at most ~budget SM cycles; false on timeout. The clock
+// is checked before every probe, so a budget of a cycle or two runs out before the first
+// probe even when the copy has already landed (the failure-detection test relies on it).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long budget) {
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > budget) return false;
-  return true;
+  for (;;) {
+    if (clock64() - t0 >= budget) return false;
+    if (mbar_try_wait(bar, parity)) return true;
+  }
 }
 
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz

@@ -176,3 +176,25 @@ def test_pint_converges_to_sequential(kind):
         r, b = step_residual(s, X, n)
         d = s.dscale()
         assert np.linalg.norm(d * r) <= 1e-12 * np.linalg.norm(d * b) * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("kind", ["tri", "diag"])
+def test_eager_start_converges_to_sequential_and_continues(kind):
+    # The eager start (every step active from the first sweep) solves the same space-time
+    # system, so it converges to the backward-Euler solution too (P4), also when it continues
+    # from a state converged to 1e-6 only. Its first sweep updates every step. (It saves few
+    # sweeps: A' couples each step to its predecessor at full strength, so a change made at
+    # one step needs one sweep per step to reach the last, whatever the start.)
+    s = build_system(W.terzaghi_small().with_(n=8, n_t=8))
+    P = BlockPreconditioner(s, kind)
+    X, nsw, conv, log = pint_sweeps(s, P, 10, mode="eager", tol=1e-12)
+    assert conv and log.lo[0] == 1 and log.hi[0] == 8
+    ref = seq_solve(s)
+    eu, ep = field_rel_errors(X, ref)
+    assert eu < 1e-10 and ep < 1e-10
+    X6, n6, conv6, _ = pint_sweeps(s, P, 10, mode="tol", tol=1e-6)
+    assert conv6 and max(field_rel_errors(X6, ref)) > 1e-9
+    X12, n12, conv12, log12 = pint_sweeps(s, P, 10, mode="eager", tol=1e-12, X0=X6)
+    assert conv12 and log12.hi[0] == 8
+    eu, ep = field_rel_errors(X12, ref)
+    assert eu < 1e-10 and ep < 1e-10
