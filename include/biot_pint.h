@@ -117,8 +117,16 @@ typedef struct {
   int32_t precond;           /* biot_precond_kind set up, 0 if none */
   int32_t precision;         /* biot_precision in use */
   double beta;               /* stabilisation factor actually used */
-  int64_t device_bytes;      /* device memory held by the context */
+  int64_t device_bytes;      /* device memory held by the context (multigrid levels: their own) */
+  int32_t inner;             /* biot_inner_solver of the block solves */
+  int32_t gmg_levels;        /* multigrid levels set up (0: exact block solves) */
+  double gmg_lam_u, gmg_lam_p;  /* power-method estimates of lam_max(M^{-1} A), lam_max(M^{-1} S) on level 0 */
 } biot_info;
+
+typedef enum {
+  BIOT_INNER_EXACT = 0,      /* exact block solves: band Cholesky, or substructured (default) */
+  BIOT_INNER_GMG = 1         /* geometric multigrid V-cycles (inexact; FGMRES is flexible) */
+} biot_inner_solver;
 
 /* ---- context life cycle ------------------------------------------------- */
 
@@ -163,6 +171,23 @@ biot_status biot_precond_setup(biot_ctx* ctx, int32_t kind);
  * biot_precond_setup. Errors: BIOT_E_INVALID (strips < 0, or fewer than two node columns
  * per strip: 3 strips > n + 2). */
 biot_status biot_set_substructure(biot_ctx* ctx, int32_t strips);
+
+/* Choose how the block solves with A and S of P1/P2 are done (Sec. 3.1 leaves it
+ * open); takes effect at the next biot_precond_setup. BIOT_INNER_EXACT (default):
+ * band Cholesky / substructured factorisations, exact up to rounding.
+ * BIOT_INNER_GMG: `cycles` geometric-multigrid V-cycles per block solve on the
+ * nested meshes n, n/2, n/4, ... (Sec. 4 builds its meshes by joining edge
+ * midpoints; levels 0 = coarsen while n is even and above 16, else up to
+ * `levels` levels while n is even and the coarse mesh keeps two cells), with `smooth` Chebyshev steps before and after each coarse
+ * correction (node-block Jacobi, interval [lam/8, 1.1 lam] from 20 power steps),
+ * restriction P^T, linear prolongation, coarse operators assembled on the coarse
+ * meshes with the element permeability averaged over the four children and the
+ * fine beta (the Galerkin operators for P1 on nested meshes), and an exact band
+ * solve on the coarsest level. P^{-1} is then inexact; the flexible Krylov cycle
+ * still converges to the same solution. Errors: BIOT_E_INVALID (kind; levels 1 or
+ * negative, cycles outside 1..16, smooth outside 1..8; a mesh that cannot be
+ * coarsened: n odd, or n <= 16 with levels 0). */
+biot_status biot_set_inner_solver(biot_ctx* ctx, int32_t kind, int32_t levels, int32_t cycles, int32_t smooth);
 
 /* Run the inverted time stepping (Alg. 3) as windowed snapshot sweeps: at sweep
  * w every active step n uses x_{n-1} and x_n from the state after sweep w-1;

@@ -24,6 +24,7 @@ BIOT_FP64, BIOT_FP32, BIOT_BF16VAL_FP32ACC = 0, 1, 2
 BIOT_TERZAGHI, BIOT_MMS_TRIG, BIOT_BARRY_MERCER = 0, 1, 2
 BIOT_BETA_H2, BIOT_BETA_H, BIOT_BETA_NONE = 0, 1, 2
 BIOT_SCHED_TOL, BIOT_SCHED_PAPER, BIOT_SCHED_EAGER = 0, 1, 2
+BIOT_INNER_EXACT, BIOT_INNER_GMG = 0, 1
 BIOT_KC_RESIDUAL, BIOT_KC_SPMM, BIOT_KC_BAND_SOLVE = 0, 1, 2
 
 
@@ -43,7 +44,8 @@ class BiotInfo(ctypes.Structure):
         ("nnz", ctypes.c_int64), ("n_pairs", ctypes.c_int32), ("n_t", ctypes.c_int32),
         ("window_cap", ctypes.c_int32), ("band_u", ctypes.c_int32), ("band_p", ctypes.c_int32),
         ("precond", ctypes.c_int32), ("precision", ctypes.c_int32), ("beta", ctypes.c_double),
-        ("device_bytes", ctypes.c_int64),
+        ("device_bytes", ctypes.c_int64), ("inner", ctypes.c_int32), ("gmg_levels", ctypes.c_int32),
+        ("gmg_lam_u", ctypes.c_double), ("gmg_lam_p", ctypes.c_double),
     ]
 
 
@@ -87,6 +89,7 @@ _SIGNATURES = {
     "biot_set_substructure": (ctypes.c_int, [_P, ctypes.c_int32]),
     "biot_pint_solve": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int32, _I32, _D]),
     "biot_set_schedule": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "biot_set_inner_solver": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "biot_sweep": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _D]),
     "biot_batch_solve": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                         ctypes.c_int32, _I32, _D]),
@@ -186,6 +189,11 @@ def biot_precond_setup(ctx, kind: int):
 
 def biot_set_substructure(ctx, strips: int):
     _check(lib().biot_set_substructure(ctx, int(strips)), ctx, "biot_set_substructure")
+
+
+def biot_set_inner_solver(ctx, kind: int, levels: int = 0, cycles: int = 1, smooth: int = 2):
+    _check(lib().biot_set_inner_solver(ctx, int(kind), int(levels), int(cycles), int(smooth)), ctx,
+           "biot_set_inner_solver")
 
 
 def biot_set_schedule(ctx, schedule: int):
@@ -342,7 +350,8 @@ class Context:
     """Owns one biot_ctx built from an object with the attributes of workloads.BiotCase."""
 
     def __init__(self, case, stream=None, window: int = 0, schedule: int = BIOT_SCHED_TOL,
-                 precision: str = "fp64", precond: Optional[str] = None, strips: Optional[int] = None):
+                 precision: str = "fp64", precond: Optional[str] = None, strips: Optional[int] = None,
+                 gmg: Optional[dict] = None):
         self.case = case
         self.ctx = biot_mesh_create(case.n, case.Lx, case.Ly, stream)
         try:
@@ -354,6 +363,8 @@ class Context:
             del keep
             if strips is not None:
                 biot_set_substructure(self.ctx, strips)
+            if gmg is not None:  # multigrid block solves: dict(levels=, cycles=, smooth=)
+                biot_set_inner_solver(self.ctx, BIOT_INNER_GMG, **gmg)
             biot_precond_setup(self.ctx, _PRECOND[precond or case.precond])
         except Exception:
             biot_destroy(self.ctx)

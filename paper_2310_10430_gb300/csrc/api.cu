@@ -593,8 +593,31 @@ biot_status biot_precond_setup(biot_ctx* ctx, int32_t kind) {
   BIOT_TRY(need_assembled(ctx));
   if (kind != BIOT_PRECOND_TRI && kind != BIOT_PRECOND_DIAG) return fail(ctx, BIOT_E_INVALID, "precond kind %d", kind);
   ctx->precond = 0;
-  BIOT_TRY(band_setup(ctx, kind));
+  if (ctx->inner == BIOT_INNER_GMG) {
+    BIOT_TRY(gmg_setup(ctx));
+    ctx->precond = kind;
+  } else {
+    gmg_free(ctx);
+    BIOT_TRY(band_setup(ctx, kind));
+  }
   BIOT_CU(ctx, cudaStreamSynchronize(ctx->stream));
+  return BIOT_OK;
+}
+
+biot_status biot_set_inner_solver(biot_ctx* ctx, int32_t kind, int32_t levels, int32_t cycles, int32_t smooth) {
+  if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
+  if (kind != BIOT_INNER_EXACT && kind != BIOT_INNER_GMG) return fail(ctx, BIOT_E_INVALID, "inner solver %d", kind);
+  if (kind == BIOT_INNER_GMG) {
+    if (levels < 0 || levels == 1 || cycles < 1 || cycles > 16 || smooth < 1 || smooth > 8)
+      return fail(ctx, BIOT_E_INVALID, "multigrid: levels 0 or >= 2, cycles 1..16, smoothing steps 1..8");
+    if (gmg_levels_for(ctx->n, levels) < 2)
+      return fail(ctx, BIOT_E_INVALID, "multigrid: n = %d cannot be coarsened (%s)", ctx->n,
+                  levels == 0 ? "automatic depth needs an even n above 16" : "n odd or below 4");
+    ctx->gmg_levels_req = levels;
+    ctx->gmg_cycles = cycles;
+    ctx->gmg_smooth = smooth;
+  }
+  ctx->inner = kind;
   return BIOT_OK;
 }
 
@@ -771,6 +794,8 @@ biot_status biot_get_info(const biot_ctx* ctx, biot_info* out) {
   out->precision = ctx->prm.precision;
   out->beta = ctx->beta;
   out->device_bytes = ctx->device_bytes;
+  out->inner = ctx->inner;
+  gmg_info(ctx, &out->gmg_levels, &out->gmg_lam_u, &out->gmg_lam_p);
   return BIOT_OK;
 }
 
@@ -801,6 +826,10 @@ biot_status biot_timing_read(biot_ctx* ctx, int32_t kc, double* total_ms, int64_
 biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out) {
   if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
   BIOT_TRY(need_precond(ctx));
+  if (ctx->gmg) {  // multigrid block solves: no band-solve variants to choose
+    if (out) *out = biot_tuning{};
+    return BIOT_OK;
+  }
   const bool fp64 = !low_precision(ctx);
   const int pi = fp64 ? 0 : 1;
   const int nc = ctx->wcap;
@@ -906,6 +935,7 @@ const char* biot_last_error(const biot_ctx* ctx) {
 void biot_destroy(biot_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  gmg_free(ctx);  // destroys the multigrid level contexts
   sub_free(ctx);  // synchronises both streams: before the side stream is destroyed
   if (ctx->side) {
     cudaStreamSynchronize(ctx->side);

@@ -412,6 +412,7 @@ biot_status assemble_system(biot_ctx* ctx) {
   double beta = 0.0;
   if (p.beta_mode == BIOT_BETA_H2) beta = h * h / (4.0 * (lam + 2.0 * mu));
   if (p.beta_mode == BIOT_BETA_H) beta = h / (4.0 * (lam + 2.0 * mu));
+  if (ctx->beta_force >= 0.0) beta = ctx->beta_force;  // a multigrid level keeps the fine beta
   ctx->beta = beta;
   Material m{lam, mu, p.alpha, p.tau, beta};
 

@@ -1384,6 +1384,10 @@ template <typename T>
 void precond_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols) {
   using B = BandBufs<T>;
   KTimer tm(ctx, BIOT_KC_BAND_SOLVE);
+  if (ctx->gmg) {
+    gmg_apply<T>(ctx, vin, z, c0, ncols);
+    return;
+  }
   const int nn = ctx->n_nodes;
   const int pi = sizeof(T) == 8 ? 0 : 1;
   const int vu = ctx->band_var_u[pi], vp = ctx->band_var_p[pi];

@@ -100,8 +100,9 @@ extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, do
     if (c->prm.precision != c0->prm.precision || c->n_iter != c0->n_iter || c->precond != c0->precond)
       return fail(c, BIOT_E_INVALID, "biot_batch_solve: contexts differ in precision, n_iter or preconditioner");
     if (c->wcap != c->n_t) return fail(c, BIOT_E_INVALID, "biot_batch_solve: context %d needs window = N_t", i);
-    if (!c->plain_band)
-      return fail(c, BIOT_E_INVALID, "biot_batch_solve: context %d has no natural-order band factors (n > 512)", i);
+    if (!c->plain_band || c->gmg)
+      return fail(c, BIOT_E_INVALID, "biot_batch_solve: context %d has no natural-order band factors (n > 512 or "
+                  "multigrid block solves)", i);
   }
   const bool bf16 = c0->prm.precision == BIOT_BF16VAL_FP32ACC;
   const bool tri = c0->precond == BIOT_PRECOND_TRI;

@@ -16,6 +16,8 @@
 
 namespace biot {
 
+struct Gmg;  // multigrid hierarchy of the block solves (gmg.cu)
+
 // Kernel launches issued by the library (reported by biot_launch_count).
 extern std::atomic<int64_t> g_launches;
 
@@ -203,6 +205,11 @@ struct biot_ctx {
   void* dnb_p[2] = {nullptr, nullptr};  // same for S
   int dnb_nb_u[2] = {0, 0};     // NB they were built for (0: none)
   int dnb_nb_p[2] = {0, 0};
+  // inner solver of the block solves: exact (band / substructured) or multigrid V-cycles
+  int inner = BIOT_INNER_EXACT;
+  int gmg_levels_req = 0, gmg_cycles = 1, gmg_smooth = 2;
+  biot::Gmg* gmg = nullptr;
+  double beta_force = -1.0;     // >= 0: stabilisation factor to use instead of the mesh's own
   // params
   biot_params prm{};
   double beta = 0.0;
@@ -269,6 +276,13 @@ template <typename T> void sub_apply(biot_ctx* ctx, int which, const T* vin, T* 
 biot_status sep_dense_setup(biot_ctx* ctx, SubBlock* sb);  // needs sb->LS factored
 template <typename T> void sep_dense_solve(biot_ctx* ctx, SubBlock* sb, T* tS, T* tZ, int ld, int c0, int ncols);
 biot_status sub_tune(biot_ctx* ctx, double* ms, double* ms_sep, std::map<std::string, int>* cache, int* hits);
+
+// ---- gmg.cu ----
+biot_status gmg_setup(biot_ctx* ctx);
+void gmg_free(biot_ctx* ctx);
+int gmg_levels_for(int n, int req);
+template <typename T> void gmg_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols);
+void gmg_info(const biot_ctx* ctx, int* levels, double* lam_u, double* lam_p);
 
 // ---- assembly.cu ----
 biot_status build_pattern(biot_ctx* ctx);

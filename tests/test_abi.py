@@ -47,7 +47,8 @@ def test_binding_covers_the_header():
 def test_struct_layouts_match_header():
     # 8-byte aligned doubles/pointers, int32 members as declared
     assert ctypes.sizeof(biot.BiotParams) == 8 * 6 + 4 * 3 + 4 + 8 + 4 * 4
-    assert ctypes.sizeof(biot.BiotInfo) == 4 * 3 + 4 + 8 + 4 * 8 + 8 + 8
+    # ... + inner, gmg_levels (int32) and the two power-method estimates (double)
+    assert ctypes.sizeof(biot.BiotInfo) == 4 * 3 + 4 + 8 + 4 * 8 + 8 + 8 + 4 * 2 + 8 * 2
     assert ctypes.sizeof(biot.BiotTuning) == 4 * 8 + 8 * 4 + 4 * 2 + 4 * 2 + 8 * 2
 
 
