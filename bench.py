@@ -505,7 +505,7 @@ def sources_hash(files):
 
 
 # The sources of every kernel one reduced-precision sweep launches.
-SWEEP_SOURCES = ["band.cu", "krylov.cu", "separator.cu", "spmm.cu", "substructure.cu"]
+SWEEP_SOURCES = ["band.cu", "gmg.cu", "krylov.cu", "separator.cu", "spmm.cu", "substructure.cu"]
 
 
 def profile_traffic_sha(sha, unit_tag):
@@ -565,7 +565,8 @@ def run_ours(args):
     case = workload()
     stream = torch.cuda.current_stream()
     W_ = case.n_t
-    ctx = biot.Context(case, stream=stream, window=W_, precision=args.precision, strips=args.strips)
+    ctx = biot.Context(case, stream=stream, window=W_, precision=args.precision, strips=args.strips,
+                       gmg=GMG if args.gmg else None)
     info = ctx.info
     lo, hi = 1, case.n_t
     tuning = biot.biot_tune(ctx.ctx, args.tune_cache).as_dict()
@@ -1194,6 +1195,8 @@ def main():
                          "solves until the per-field error (not the residual) is at most 1e-8")
     ap.add_argument("--large-n-iter", type=int, default=0,
                     help="with --large: FGMRES restart length (default: the workload's 10)")
+    ap.add_argument("--gmg", action="store_true",
+                    help="multigrid block solves in the timed line (profiling runs; the bench line is exact)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"],
                     help="sweep precision of the timed line (profiling runs; the bench line is fp64)")
     args = ap.parse_args()

@@ -332,7 +332,8 @@ template <typename T> void precond_apply(biot_ctx* ctx, const T* vin, T* z, int 
 
 // ---- krylov.cu ----
 enum ColScalar { CS_RR = 0, CS_BB, CS_BETA0, CS_WN0, CS_WW, CS_INVH, CS_ACTIVE, kColScalars };
-void reduce_partials(biot_ctx* ctx, int nslots, int ncols, double* out, int ldo, int c0);
+// out[s][c] = sum over nblocks per-block partials (fixed order), s < nslots.
+void reduce_partials(biot_ctx* ctx, int nslots, int ncols, double* out, int ldo, int c0, int nblocks = kRedBlocks);
 template <typename T> biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols);
 
 // ---- batched launches (batch.cu drives them) ----

@@ -32,8 +32,10 @@ namespace biot {
 
 namespace {
 
-constexpr int kCoef = 40;         // per node: A 7 x 2 x 2, S 7, M_u^{-1} 2 x 2, M_p^{-1}
-constexpr int kCoefP = 28, kCoefMu = 35, kCoefMp = 39;
+// Per node (160 bytes in FP32, read as ten 16-byte vectors): A's 7 blocks 2 x 2 at 0..27,
+// M_u^{-1} (2 x 2) at 28..31, S's 7 entries at 32..38, M_p^{-1} at 39.
+constexpr int kCoef = 40;
+constexpr int kCoefMu = 28, kCoefP = 32, kCoefMp = 39;
 constexpr int kMinCoarse = 16;    // coarsen while n is even and above this
 constexpr double kChebLowDiv = 8.0;
 constexpr int kPowerIters = 20;
@@ -206,21 +208,48 @@ __global__ void k_gmg_norm_fin(const double* __restrict__ part, int nb, double* 
 // ---- the V-cycle's kernels: FM = fields (1: A's rows 3v, 3v+1; 2: S's rows 3v+2; 3: both) ----
 
 // Level-0 right-hand side from the Krylov vector (scaled by |diag AA|^{1/2}); mode 0: A rows
-// b = vin dsq; 1: S rows b = -vin dsq (P2's z_p = -S^{-1} r_p); 2: S rows b = tp (P1).
+// b = vin dsq; 1: S rows b = -vin dsq (P2's z_p = -S^{-1} r_p); 2: S rows b = tp (P1); 3: 0 and 1.
+// A thread owns one node and 16 bytes of columns of b (all ldg columns: those outside
+// [c0, c0 + ncols) are set to zero, which keeps the level buffers finite).
 template <typename T>
-__global__ void k_gmg_prep(int nn, int mode, const T* __restrict__ vin, const double* __restrict__ dsq,
-                           const T* __restrict__ tp, T* __restrict__ b, int ld, int ldg, int c0, int ncols) {
-  const long long total = (long long)nn * ncols;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(q / ncols), c = c0 + (int)(q % ncols);
-    if (mode == 0) {
-      b[(size_t)(3 * v) * ldg + c] = (T)((double)vin[(size_t)(3 * v) * ld + c] * dsq[3 * v]);
-      b[(size_t)(3 * v + 1) * ldg + c] = (T)((double)vin[(size_t)(3 * v + 1) * ld + c] * dsq[3 * v + 1]);
-    } else if (mode == 1) {
-      b[(size_t)(3 * v + 2) * ldg + c] = (T)(-(double)vin[(size_t)(3 * v + 2) * ld + c] * dsq[3 * v + 2]);
-    } else {
-      b[(size_t)(3 * v + 2) * ldg + c] = tp[(size_t)v * ld + c];
+__global__ void __launch_bounds__(kThreads)
+k_gmg_prep(int nn, int mode, const T* __restrict__ vin, const double* __restrict__ dsq, const T* __restrict__ tp,
+           T* __restrict__ b, int ld, int ldg, int c0, int ncols) {
+  constexpr int VEC = V16<T>::n;
+  const int nch = ldg / VEC;
+  const int total = nn * nch;
+  const bool vec_in = ld % VEC == 0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const int v = q / nch, c = (q - v * nch) * VEC;
+    const bool full = vec_in && c >= c0 && c + VEC <= c0 + ncols;
+    auto load = [&](const T* row, T* o) {
+      if (full) {
+        ldv(row + c, o);
+      } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) o[k] = (c + k >= c0 && c + k < c0 + ncols) ? row[c + k] : T(0);
+      }
+    };
+    T a[VEC];
+    if (mode == 0 || mode == 3) {
+      for (int f = 0; f < 2; ++f) {
+        load(vin + (size_t)(3 * v + f) * ld, a);
+        const T sc = (T)dsq[3 * v + f];  // one conversion per row: FP64 work per element is slow here
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) a[k] *= sc;
+        stv(b + (size_t)(3 * v + f) * ldg + c, a);
+      }
+    }
+    if (mode == 1 || mode == 3) {
+      load(vin + (size_t)(3 * v + 2) * ld, a);
+      const T sc = -(T)dsq[3 * v + 2];
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) a[k] *= sc;
+      stv(b + (size_t)(3 * v + 2) * ldg + c, a);
+    }
+    if (mode == 2) {
+      load(tp + (size_t)v * ld, a);
+      stv(b + (size_t)(3 * v + 2) * ldg + c, a);
     }
   }
 }
@@ -240,6 +269,30 @@ __global__ void k_gmg_finish(int nn, const T* __restrict__ x, T* __restrict__ z,
   }
 }
 
+// Columns c .. c + VEC - 1 of one row of z (row start `row`): a 16-byte store when the chunk lies
+// inside [c0, c0 + ncols) and ldo keeps rows 16-byte aligned, else element by element.
+template <typename T>
+__device__ __forceinline__ void store_out(T* row, const T* x, int c, int ldo, int c0, int ncols) {
+  constexpr int VEC = V16<T>::n;
+  if (ldo % VEC == 0 && c >= c0 && c + VEC <= c0 + ncols) {
+    stv(row + c, x);
+  } else {
+#pragma unroll
+    for (int q = 0; q < VEC; ++q)
+      if (c + q >= c0 && c + q < c0 + ncols) row[c + q] = x[q];
+  }
+}
+
+// Four consecutive coefficients (16-byte aligned) as one or two vector loads.
+template <typename T> __device__ __forceinline__ void ld4(const T* p, T* o) {
+  if (sizeof(T) == 4) {
+    ldv(p, o);
+  } else {
+    ldv(p, o);
+    ldv(p + 2, o + 2);
+  }
+}
+
 // K x for the rows in FM of node v (i, j), columns c .. c + VEC - 1.
 template <typename T, int FM>
 __device__ __forceinline__ void stencil_apply(const T* __restrict__ cf, const T* __restrict__ x, int i, int j, int n,
@@ -247,16 +300,22 @@ __device__ __forceinline__ void stencil_apply(const T* __restrict__ cf, const T*
   constexpr int VEC = V16<T>::n;
 #pragma unroll
   for (int q = 0; q < VEC; ++q) y0[q] = y1[q] = y2[q] = T(0);
+  T sp[8];
+  if (FM & 2) {
+    ld4(cf + kCoefP, sp);
+    ld4(cf + kCoefP + 4, sp + 4);
+  }
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
     const int m = nbr_of(k, i, j, n);
     if (m < 0) continue;
     const T* xm = x + (size_t)(3 * m) * ldg + c;
     if (FM & 1) {
-      T a[VEC], b[VEC];
+      T a[VEC], b[VEC], cc[4];
       ldv(xm, a);
       ldv(xm + ldg, b);
-      const T c00 = cf[4 * k], c01 = cf[4 * k + 1], c10 = cf[4 * k + 2], c11 = cf[4 * k + 3];
+      ld4(cf + 4 * k, cc);
+      const T c00 = cc[0], c01 = cc[1], c10 = cc[2], c11 = cc[3];
 #pragma unroll
       for (int q = 0; q < VEC; ++q) {
         y0[q] += c00 * a[q] + c01 * b[q];
@@ -266,7 +325,7 @@ __device__ __forceinline__ void stencil_apply(const T* __restrict__ cf, const T*
     if (FM & 2) {
       T p[VEC];
       ldv(xm + 2 * ldg, p);
-      const T cp = cf[kCoefP + k];
+      const T cp = sp[k];
 #pragma unroll
       for (int q = 0; q < VEC; ++q) y2[q] += cp * p[q];
     }
@@ -275,11 +334,13 @@ __device__ __forceinline__ void stencil_apply(const T* __restrict__ cf, const T*
 
 // One Chebyshev step on the rows in FM: s = M^{-1} (b - K x_in) (x_in = 0: ZERO), d = c1 d + c2 s
 // (READD false: c1 d dropped), x_out = x_in + d; Dirichlet rows x_out = b, d = 0.
-template <typename T, int FM, bool ZERO, bool READD>
+// OUTZ: x_out is the preconditioner's output z (leading dimension ldo, only the columns
+// [c0, c0 + ncols) written, 16-byte stores when ldo allows) instead of a level buffer.
+template <typename T, int FM, bool ZERO, bool READD, bool OUTZ = false>
 __global__ void __launch_bounds__(kThreads)
 k_gmg_smooth(int n, const T* __restrict__ coef, const uint8_t* __restrict__ dmask, const T* __restrict__ xin,
              const T* __restrict__ b, T* __restrict__ d, T* __restrict__ xout, T cu1, T cu2, T cp1, T cp2, int ldg,
-             int ca, int nch) {
+             int ca, int nch, int ldo = 0, int c0 = 0, int ncols = 0) {
   constexpr int VEC = V16<T>::n;
   const int nx = n + 1;
   const long long total = (long long)nx * nx * nch;
@@ -308,7 +369,9 @@ k_gmg_smooth(int n, const T* __restrict__ coef, const uint8_t* __restrict__ dmas
         ldv(d + r0, d0);
         ldv(d + r0 + ldg, d1);
       }
-      const T m00 = cf[kCoefMu], m01 = cf[kCoefMu + 1], m10 = cf[kCoefMu + 2], m11 = cf[kCoefMu + 3];
+      T mu[4];
+      ld4(cf + kCoefMu, mu);
+      const T m00 = mu[0], m01 = mu[1], m10 = mu[2], m11 = mu[3];
       const bool dir0 = dmask[3 * v] != 0, dir1 = dmask[3 * v + 1] != 0;
 #pragma unroll
       for (int k = 0; k < VEC; ++k) {
@@ -325,8 +388,13 @@ k_gmg_smooth(int n, const T* __restrict__ coef, const uint8_t* __restrict__ dmas
         d0[k] = dir0 ? T(0) : e0;
         d1[k] = dir1 ? T(0) : e1;
       }
-      stv(xout + r0, x0);
-      stv(xout + r0 + ldg, x1);
+      if (OUTZ) {
+        store_out(xout + (size_t)(3 * v) * ldo, x0, c, ldo, c0, ncols);
+        store_out(xout + (size_t)(3 * v + 1) * ldo, x1, c, ldo, c0, ncols);
+      } else {
+        stv(xout + r0, x0);
+        stv(xout + r0 + ldg, x1);
+      }
       stv(d + r0, d0);
       stv(d + r0 + ldg, d1);
     }
@@ -346,7 +414,8 @@ k_gmg_smooth(int n, const T* __restrict__ coef, const uint8_t* __restrict__ dmas
         x2[k] = dir2 ? b2[k] : xa + e;
         d2[k] = dir2 ? T(0) : e;
       }
-      stv(xout + r2, x2);
+      if (OUTZ) store_out(xout + (size_t)(3 * v + 2) * ldo, x2, c, ldo, c0, ncols);
+      else stv(xout + r2, x2);
       stv(d + r2, d2);
     }
   }
@@ -506,8 +575,8 @@ __global__ void k_gmg_coarse_prep(int nn, const T* __restrict__ b, const double*
     for (int f = 0; f < 3; ++f) {
       const size_t o = (size_t)(3 * v + f) * ldg + c;
       const bool on = f < 2 ? (FM & 1) : (FM & 2);
-      const double s = f < 2 ? dsc[3 * v + f] : -dsc[3 * v + f];
-      vin[o] = on ? (T)((double)b[o] * s) : T(0);
+      const T s = (T)(f < 2 ? dsc[3 * v + f] : -dsc[3 * v + f]);
+      vin[o] = on ? b[o] * s : T(0);
     }
   }
 }
@@ -632,13 +701,30 @@ biot_status level_buffers(biot_ctx* ctx, GmgLevel& L, int ldg, bool fp64, bool w
 
 // ---- the cycle (all launches on the fine context's stream) ----
 
+// The level-0 cycle's last smoothing step writes the preconditioner's output z directly.
+struct OutZ {
+  void* z = nullptr;
+  int ld = 0, c0 = 0, ncols = 0;
+};
+
 template <typename T, int FM>
-void smooth_step(const Gmg& g, GmgLevel& L, cudaStream_t s, int k, bool zero, const T* xin, const T* b, T* xout) {
+void smooth_step(const Gmg& g, GmgLevel& L, cudaStream_t s, int k, bool zero, const T* xin, const T* b, T* xout,
+                 const OutZ* oz = nullptr) {
   constexpr int VEC = V16<T>::n;
   const T cu1 = (T)L.c1[0][k], cu2 = (T)L.c2[0][k], cp1 = (T)L.c1[1][k], cp2 = (T)L.c2[1][k];
   const int nch = g.ldg / VEC;  // every column chunk of the level buffers: unused columns stay finite
   const int grid = grid_for((long long)L.nn * nch);
   T* d = buf_of<T>(L, GB_D);
+  if (oz) {  // never the first step of a cycle (k >= 1 or a post-smoothing step)
+    T* z = static_cast<T*>(oz->z);
+    if (k == 0)
+      BIOT_LAUNCH((k_gmg_smooth<T, FM, false, false, true>), grid, kThreads, 0, s, L.n, coef_of<T>(L), L.dmask, xin,
+                  b, d, z, cu1, cu2, cp1, cp2, g.ldg, 0, nch, oz->ld, oz->c0, oz->ncols);
+    else
+      BIOT_LAUNCH((k_gmg_smooth<T, FM, false, true, true>), grid, kThreads, 0, s, L.n, coef_of<T>(L), L.dmask, xin,
+                  b, d, z, cu1, cu2, cp1, cp2, g.ldg, 0, nch, oz->ld, oz->c0, oz->ncols);
+    return;
+  }
   if (zero)
     BIOT_LAUNCH((k_gmg_smooth<T, FM, true, false>), grid, kThreads, 0, s, L.n, coef_of<T>(L), L.dmask, xin, b, d,
                 xout, cu1, cu2, cp1, cp2, g.ldg, 0, nch);
@@ -652,7 +738,7 @@ void smooth_step(const Gmg& g, GmgLevel& L, cudaStream_t s, int k, bool zero, co
 
 // One V-cycle on level l for the fields FM: x_out ~ K_l^{-1} b.
 template <typename T, int FM>
-void vcycle(Gmg& g, int l, cudaStream_t s, const T* b, T* xout, int c0, int ncols) {
+void vcycle(Gmg& g, int l, cudaStream_t s, const T* b, T* xout, int c0, int ncols, const OutZ* oz = nullptr) {
   constexpr int VEC = V16<T>::n;
   GmgLevel& L = g.lv[l];
   const int nch = g.ldg / VEC;
@@ -684,20 +770,25 @@ void vcycle(Gmg& g, int l, cudaStream_t s, const T* b, T* xout, int c0, int ncol
               g.ldg, 0, nch);
   // post-smoothing: the last step writes x_out
   for (int k = 0; k < g.smooth; ++k) {
-    T* dst = k == g.smooth - 1 ? xout : xb;
-    smooth_step<T, FM>(g, L, s, k, false, xa, b, dst);
+    const bool last = k == g.smooth - 1;
+    smooth_step<T, FM>(g, L, s, k, false, xa, b, last ? xout : xb, last ? oz : nullptr);
     std::swap(xa, xb);
   }
 }
 
 // `cycles` V-cycles on level 0 from zero: x <- V(b); x <- x + V(b - K x).
+// Returns true when the result went straight into oz (one cycle), false when it is in the X buffer.
 template <typename T, int FM>
-void solve_level0(Gmg& g, cudaStream_t s, int c0, int ncols) {
+bool solve_level0(Gmg& g, cudaStream_t s, int c0, int ncols, const OutZ* oz) {
   constexpr int VEC = V16<T>::n;
   GmgLevel& L = g.lv[0];
   const int nch = g.ldg / VEC;
   T* b = buf_of<T>(L, GB_B);
   T* x = buf_of<T>(L, GB_X);
+  if (g.cycles == 1 && g.L > 1) {
+    vcycle<T, FM>(g, 0, s, b, x, c0, ncols, oz);
+    return true;
+  }
   vcycle<T, FM>(g, 0, s, b, x, c0, ncols);
   for (int k = 1; k < g.cycles; ++k) {
     // e = b - K x; correction V(e) into the R buffer (the cycle's own residual there is
@@ -709,6 +800,7 @@ void solve_level0(Gmg& g, cudaStream_t s, int c0, int ncols) {
     vcycle<T, FM>(g, 0, s, e, corr, c0, ncols);
     BIOT_LAUNCH((k_gmg_axpy<T, FM>), grid_for((long long)L.nn * nch), kThreads, 0, s, L.nn, corr, x, g.ldg, 0, nch);
   }
+  return false;
 }
 
 template <typename T> T* gmg_tp(biot_ctx* ctx);
@@ -767,6 +859,9 @@ biot_status gmg_setup(biot_ctx* ctx) {
   g->cycles = ctx->gmg_cycles;
   g->smooth = ctx->gmg_smooth;
   g->ldg = (ctx->wcap + 3) & ~3;
+  if ((long long)ctx->n_nodes * (g->ldg / 2) >= (1LL << 31))  // 32-bit work indices of the level-0 kernels
+    return fail(ctx, BIOT_E_INVALID, "multigrid: mesh x window too large (%d nodes x %d columns)", ctx->n_nodes,
+                g->ldg);
   g->fp64 = ctx->prm.precision == BIOT_FP64;
   g->lv.resize(L);
   double* kprev = ctx->kappa;
@@ -821,22 +916,27 @@ void gmg_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols) {
   cudaStream_t s = ctx->stream;
   const int nn = ctx->n_nodes, ld = ctx->wcap;
   const int ge = grid_for((long long)nn * ncols);
+  const int gp = grid_for((long long)nn * (g.ldg / V16<T>::n));
   T* b = buf_of<T>(L0, GB_B);
   T* x = buf_of<T>(L0, GB_X);
+  OutZ oz;
+  oz.z = z;
+  oz.ld = ld;
+  oz.c0 = c0;
+  oz.ncols = ncols;
   if (ctx->precond == BIOT_PRECOND_DIAG) {
-    BIOT_LAUNCH(k_gmg_prep<T>, ge, kThreads, 0, s, nn, 0, vin, ctx->dsq, (const T*)nullptr, b, ld, g.ldg, c0, ncols);
-    BIOT_LAUNCH(k_gmg_prep<T>, ge, kThreads, 0, s, nn, 1, vin, ctx->dsq, (const T*)nullptr, b, ld, g.ldg, c0, ncols);
-    solve_level0<T, 3>(g, s, c0, ncols);
-    BIOT_LAUNCH((k_gmg_finish<T, 3>), ge, kThreads, 0, s, nn, x, z, ld, g.ldg, c0, ncols);
+    BIOT_LAUNCH(k_gmg_prep<T>, gp, kThreads, 0, s, nn, 3, vin, ctx->dsq, (const T*)nullptr, b, ld, g.ldg, c0, ncols);
+    if (!solve_level0<T, 3>(g, s, c0, ncols, &oz))
+      BIOT_LAUNCH((k_gmg_finish<T, 3>), ge, kThreads, 0, s, nn, x, z, ld, g.ldg, c0, ncols);
   } else {
-    BIOT_LAUNCH(k_gmg_prep<T>, ge, kThreads, 0, s, nn, 0, vin, ctx->dsq, (const T*)nullptr, b, ld, g.ldg, c0, ncols);
-    solve_level0<T, 1>(g, s, c0, ncols);
-    BIOT_LAUNCH((k_gmg_finish<T, 1>), ge, kThreads, 0, s, nn, x, z, ld, g.ldg, c0, ncols);
+    BIOT_LAUNCH(k_gmg_prep<T>, gp, kThreads, 0, s, nn, 0, vin, ctx->dsq, (const T*)nullptr, b, ld, g.ldg, c0, ncols);
+    if (!solve_level0<T, 1>(g, s, c0, ncols, &oz))
+      BIOT_LAUNCH((k_gmg_finish<T, 1>), ge, kThreads, 0, s, nn, x, z, ld, g.ldg, c0, ncols);
     T* tp = gmg_tp<T>(ctx);
     launch_coupling<T>(ctx, z, vin, tp, c0, ncols);  // tp = B^T z_u - vin_p / d
-    BIOT_LAUNCH(k_gmg_prep<T>, ge, kThreads, 0, s, nn, 2, (const T*)nullptr, ctx->dsq, tp, b, ld, g.ldg, c0, ncols);
-    solve_level0<T, 2>(g, s, c0, ncols);
-    BIOT_LAUNCH((k_gmg_finish<T, 2>), ge, kThreads, 0, s, nn, x, z, ld, g.ldg, c0, ncols);
+    BIOT_LAUNCH(k_gmg_prep<T>, gp, kThreads, 0, s, nn, 2, (const T*)nullptr, ctx->dsq, tp, b, ld, g.ldg, c0, ncols);
+    if (!solve_level0<T, 2>(g, s, c0, ncols, &oz))
+      BIOT_LAUNCH((k_gmg_finish<T, 2>), ge, kThreads, 0, s, nn, x, z, ld, g.ldg, c0, ncols);
   }
 }
 template void gmg_apply<double>(biot_ctx*, const double*, double*, int, int);

@@ -44,6 +44,24 @@ __global__ void k_reduce(const double* __restrict__ part, int nblocks, int nslot
   reduce_body(part, nblocks, nslots, ld, c0, ncols, out, ldo);
 }
 
+// The same sums with one warp per column: lane l adds blocks l, l + 32, l + 64, ... in order,
+// then the 32 lane sums are combined by a fixed butterfly (a fixed tree: deterministic).
+// Block: 8 warps = 8 columns.
+__global__ void __launch_bounds__(256) k_reduce_warp(const double* __restrict__ part, int nblocks, int nslots, int ld,
+                                                     int c0, int ncols, double* __restrict__ out, int ldo) {
+  const int lane = threadIdx.x & 31;
+  const int cc = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int s = blockIdx.y;
+  if (cc >= ncols) return;  // whole warps leave together
+  const int c = c0 + cc;
+  const double* p = part + (size_t)s * nblocks * ld + c;
+  double acc = 0.0;
+  for (int b = lane; b < nblocks; b += 32) acc += p[(size_t)b * ld];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[(size_t)s * ldo + c] = acc;
+}
+
 // Partial dot products part[i][block][c] = sum_{rows of block} V_i[r][c] * w[r][c]
 // (products accumulated in T within a thread, combined in FP64 across threads and blocks).
 template <typename T>
@@ -185,6 +203,79 @@ __global__ void k_gs_axpy_vec(const T* __restrict__ V, size_t vstride, int nvec,
 #pragma unroll
       for (int q = 0; q < VEC; ++q)
         if (c + q >= c0 && c + q < ce) wr[q] = acc[q];
+    }
+  }
+}
+
+// w -= V h on the columns [c0, c0 + ncols) with the blocks owning row ranges (warps stride
+// the rows, a lane owns VEC consecutive columns, so every row access is one coalesced 16-byte
+// vector per lane) and the coefficients h[i][c] staged in shared memory per 32 VEC columns.
+// Same per-element arithmetic order as k_gs_axpy_vec. NORM: also the per-block partial sums
+// of |w|^2 after the update, in part[block][c] (the layout k_dots_vec writes for one vector),
+// which saves the separate norm pass of the second Gram-Schmidt sweep.
+template <typename T, bool NORM>
+__global__ void __launch_bounds__(256)
+k_gs_axpy_rows_vec(const T* __restrict__ V, size_t vstride, int nvec, const double* __restrict__ h,
+                   T* __restrict__ w, int nrows, int ld, int c0, int ncols, double* __restrict__ part) {
+  using VV = typename KVec<T>::V;
+  constexpr int VEC = KVec<T>::n;
+  __shared__ __align__(16) T sh[kMaxIter + 1][32 * VEC];
+  __shared__ double sm[NORM ? 8 : 1][NORM ? 32 * VEC : 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = (nrows + gridDim.x - 1) / gridDim.x;
+  const int rb = blockIdx.x * per, re = min(nrows, rb + per);
+  const int ca = c0 & ~(VEC - 1), ce = c0 + ncols;
+  for (int cb = ca; cb < ce; cb += 32 * VEC) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < nvec * 32 * VEC; t += blockDim.x) {
+      const int i = t / (32 * VEC), q = t % (32 * VEC), col = cb + q;
+      sh[i][q] = col < ld ? (T)h[(size_t)i * ld + col] : T(0);
+    }
+    __syncthreads();
+    const int c = cb + lane * VEC;
+    const bool any = c < ce;
+    const bool full = c >= c0 && c + VEC <= ce;
+    T nrm[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) nrm[q] = T(0);
+    if (any) {
+      for (int r = rb + warp; r < re; r += 8) {
+        T* wr = w + (size_t)r * ld + c;
+        T acc[VEC];
+        KVec<T>::get(*reinterpret_cast<const VV*>(wr), acc);
+#pragma unroll 4
+        for (int i = 0; i < nvec; ++i) {
+          T v[VEC], hq[VEC];
+          KVec<T>::get(*reinterpret_cast<const VV*>(V + (size_t)i * vstride + (size_t)r * ld + c), v);
+          KVec<T>::get(*reinterpret_cast<const VV*>(&sh[i][lane * VEC]), hq);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) acc[q] -= hq[q] * v[q];
+        }
+        if (full) {
+          *reinterpret_cast<VV*>(wr) = KVec<T>::make(acc);
+        } else {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q)
+            if (c + q >= c0 && c + q < ce) wr[q] = acc[q];
+        }
+        if (NORM)
+#pragma unroll
+          for (int q = 0; q < VEC; ++q)
+            if (c + q >= c0 && c + q < ce) nrm[q] += acc[q] * acc[q];
+      }
+    }
+    if (NORM) {
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) sm[warp][lane * VEC + q] = (double)nrm[q];
+      __syncthreads();
+      for (int t = threadIdx.x; t < 32 * VEC; t += blockDim.x) {
+        const int col = cb + t;
+        if (col >= c0 && col < ce) {
+          double sum = 0.0;
+          for (int u = 0; u < 8; ++u) sum += sm[u][t];
+          part[(size_t)blockIdx.x * ld + col] = sum;
+        }
+      }
     }
   }
 }
@@ -398,6 +489,38 @@ __global__ void k_update_x_mixed(const float* __restrict__ Z, size_t zstride, co
   update_x_mixed_body(Z, zstride, rec, kcol, X, ldx, lo, nrows, ld, c0, ncols);
 }
 
+// The same update with the columns' coefficients y converted to FP32 once per block (shared
+// memory) instead of once per element, blocks owning row ranges and threads the columns
+// (same per-element arithmetic: acc += y_i z_i in FP32, i ascending, then X += acc in FP64).
+// Needs ncols <= kUpdCols.
+constexpr int kUpdCols = 256;
+__global__ void __launch_bounds__(256)
+k_update_x_mixed_rows(const float* __restrict__ Z, size_t zstride, const double* __restrict__ rec,
+                      const int32_t* __restrict__ kcol, double* __restrict__ X, int ldx, int lo, int nrows, int ld,
+                      int c0, int ncols) {
+  __shared__ float ys[kMaxIter][kUpdCols];
+  __shared__ int ks[kUpdCols];
+  for (int t = threadIdx.x; t < ncols; t += blockDim.x) {
+    const int k = kcol[c0 + t];
+    ks[t] = k;
+    const double* y = rec + (size_t)(c0 + t) * kRec + kRecY;
+    for (int i = 0; i < k; ++i) ys[i][t] = (float)y[i];
+  }
+  __syncthreads();
+  const int per = (nrows + gridDim.x - 1) / gridDim.x;
+  const int rb = blockIdx.x * per, re = min(nrows, rb + per);
+  for (int r = rb; r < re; ++r) {
+    for (int t = threadIdx.x; t < ncols; t += blockDim.x) {
+      const int k = ks[t];
+      if (k == 0) continue;
+      const int c = c0 + t;
+      float acc = 0.f;
+      for (int i = 0; i < k; ++i) acc += ys[i][t] * Z[(size_t)i * zstride + (size_t)r * ld + c];
+      X[(size_t)r * ldx + lo + c] += (double)acc;
+    }
+  }
+}
+
 // ---- batched variants: instance = blockIdx.z, arguments from the instance table ----
 
 enum RedDst { RD_RES = 0, RD_WN0, RD_H1, RD_H2, RD_WW };
@@ -473,9 +596,9 @@ __global__ void kb_update_x(const InstDev* __restrict__ tab) {
 
 int krylov_record_doubles() { return kRec; }
 
-void reduce_partials(biot_ctx* ctx, int nslots, int ncols, double* out, int ldo, int c0) {
-  dim3 grid(div_up(ncols, 128), nslots);
-  BIOT_LAUNCH(k_reduce, grid, 128, 0, ctx->stream, ctx->part, kRedBlocks, nslots, ctx->wcap, c0, ncols, out, ldo);
+void reduce_partials(biot_ctx* ctx, int nslots, int ncols, double* out, int ldo, int c0, int nblocks) {
+  dim3 grid(div_up(ncols, 8), nslots);
+  BIOT_LAUNCH(k_reduce_warp, grid, 256, 0, ctx->stream, ctx->part, nblocks, nslots, ctx->wcap, c0, ncols, out, ldo);
 }
 
 template <typename T> struct KBufs;
@@ -529,11 +652,17 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
       double* h = pass == 0 ? h1 : h2;
       dots(V, j + 1, Wv);
       reduce_partials(ctx, j + 1, ncols, h, ld, c0);
-      if (vec) BIOT_LAUNCH(k_gs_axpy_vec<T>, vblk, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0, ncols);
+      if (vec && pass == 0)
+        BIOT_LAUNCH((k_gs_axpy_rows_vec<T, false>), 2 * kRedBlocks, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0,
+                    ncols, ctx->part);
+      else if (vec)  // the second sweep also forms the partial norms of the new w (2 x kRedBlocks
+                     // partials: the first two slots of the partial-sum buffer)
+        BIOT_LAUNCH((k_gs_axpy_rows_vec<T, true>), 2 * kRedBlocks, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0,
+                    ncols, ctx->part);
       else BIOT_LAUNCH(k_gs_axpy<T>, eblk, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0, ncols);
     }
-    dots(Wv, 1, Wv);
-    reduce_partials(ctx, 1, ncols, cs + CS_WW * ld, ld, c0);
+    if (!vec) dots(Wv, 1, Wv);
+    reduce_partials(ctx, 1, ncols, cs + CS_WW * ld, ld, c0, vec ? 2 * kRedBlocks : kRedBlocks);
     BIOT_LAUNCH(k_givens, cblk, 128, 0, s, j, cs, h1, h2, ld, c0, ncols, ctx->H, ctx->kcol);
     if (j + 1 < ctx->n_iter) scale_cols(Wv, V + (j + 1) * vs);
   }
@@ -541,6 +670,9 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
   if (sizeof(T) == 8)
     BIOT_LAUNCH(k_update_x<double>, eblk, 256, 0, s, (const double*)Z, vs, ctx->H, ctx->kcol, ctx->X, ctx->ldx, lo, nd,
                 ld, c0, ncols);
+  else if (ncols <= kUpdCols)
+    BIOT_LAUNCH(k_update_x_mixed_rows, 4 * 152, 256, 0, s, (const float*)Z, vs, ctx->H, ctx->kcol, ctx->X, ctx->ldx,
+                lo, nd, ld, c0, ncols);
   else
     BIOT_LAUNCH(k_update_x_mixed, eblk, 256, 0, s, (const float*)Z, vs, ctx->H, ctx->kcol, ctx->X, ctx->ldx, lo, nd,
                 ld, c0, ncols);
