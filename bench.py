@@ -738,7 +738,9 @@ def sweep_variant(case, precision, steps, warmup, stream, gmg=None):
                 "roofline": {"bound": "hbm", "unit": "GB/s", "peak": hbm, "peak_source": src,
                              # ncu DRAM read + write of one sweep, from the committed summary whose
                              # source hash matches these sources (null once they changed)
-                             "traffic": profile_traffic_sha(sources_hash(SWEEP_SOURCES), "sweep"),
+                             "traffic": (profile_traffic_sha(sources_hash(SWEEP_SOURCES),
+                                                             "gmg_sweep" if gmg else "exact_sweep")
+                                         if precision == "fp32" else None),
                              "traffic_per": "one FP32 sweep",
                              "achieved": by["total"] / (ms / 1e3) / 1e9,
                              "frac": by["total"] / (ms / 1e3) / 1e9 / hbm,
