@@ -218,8 +218,13 @@ biot_status biot_set_schedule(biot_ctx* ctx, int32_t schedule);
  * and set up (same preconditioner kind) on its own; meshes, material, K field
  * and N_t may differ. Every sweep kernel processes all instances in one launch
  * (device table of per-instance buffers and windows); with use_graph != 0 the
- * FGMRES cycle of a sweep is captured once in a CUDA graph and replayed. The
- * FP64 refinement and its tolerance are per instance, as in biot_pint_solve.
+ * FGMRES cycle of a sweep is captured once in a CUDA graph and replayed. Block
+ * solves: every context's plain band factors (batched band solves), or, when
+ * every context was set up with multigrid block solves (biot_set_inner_solver,
+ * the same smoothing steps, one cycle), every instance's V-cycles in the same
+ * launches: their levels (of any depth) and coarsest band solves are read from
+ * device tables. The FP64 refinement and its tolerance are per instance, as in
+ * biot_pint_solve; an instance set to the eager schedule starts eagerly.
  * Work runs on a private stream; the contexts' streams are synchronised first.
  * sweeps_done[count] and final_rel_res[count] (host, nullable) receive each
  * instance's FP32 sweeps and final relative space-time residual. Returns the

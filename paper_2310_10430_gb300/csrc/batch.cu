@@ -35,7 +35,10 @@ struct BatchState {
   biot_status st = BIOT_OK;
 };
 
-InstDev describe(biot_ctx* c) {
+}  // namespace
+
+// The batched kernels' view of one context (FP32 sweep buffers and factors).
+InstDev inst_describe(biot_ctx* c) {
   InstDev I{};
   I.n_nodes = c->n_nodes;
   I.n_dof = c->n_dof;
@@ -80,7 +83,6 @@ InstDev describe(biot_ctx* c) {
   return I;
 }
 
-}  // namespace
 }  // namespace biot
 
 using namespace biot;
@@ -100,10 +102,16 @@ extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, do
     if (c->prm.precision != c0->prm.precision || c->n_iter != c0->n_iter || c->precond != c0->precond)
       return fail(c, BIOT_E_INVALID, "biot_batch_solve: contexts differ in precision, n_iter or preconditioner");
     if (c->wcap != c->n_t) return fail(c, BIOT_E_INVALID, "biot_batch_solve: context %d needs window = N_t", i);
-    if (!c->plain_band || c->gmg)
-      return fail(c, BIOT_E_INVALID, "biot_batch_solve: context %d has no natural-order band factors (n > 512 or "
-                  "multigrid block solves)", i);
+    if (c0->gmg) {
+      if (!gmg_batchable(c, c0))
+        return fail(c, BIOT_E_INVALID, "biot_batch_solve: context %d: every context needs multigrid block solves "
+                    "with the same smoothing steps and one cycle", i);
+    } else if (!c->plain_band || c->gmg) {
+      return fail(c, BIOT_E_INVALID, "biot_batch_solve: context %d has no natural-order band factors (n > 512, or "
+                  "multigrid block solves mixed with exact ones)", i);
+    }
   }
+  const bool use_gmg = c0->gmg != nullptr;
   const bool bf16 = c0->prm.precision == BIOT_BF16VAL_FP32ACC;
   const bool tri = c0->precond == BIOT_PRECOND_TRI;
   const int n_iter = c0->n_iter;
@@ -113,10 +121,10 @@ extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, do
     max_ndof = std::max(max_ndof, ctxs[i]->n_dof);
     max_band = std::max(max_band, std::max(ctxs[i]->band_u, ctxs[i]->band_p));
   }
-  if (batched_solve_smem(max_band) > 227 * 1024)
+  if (!use_gmg && batched_solve_smem(max_band) > 227 * 1024)
     return fail(c0, BIOT_E_INVALID, "biot_batch_solve: half-band %d too wide for the batched band solve", max_band);
   for (int i = 0; i < count; ++i) {
-    BIOT_TRY(ensure_batch_dnb(ctxs[i]));
+    if (!use_gmg) BIOT_TRY(ensure_batch_dnb(ctxs[i]));
     BIOT_CU(ctxs[i], cudaStreamSynchronize(ctxs[i]->stream));
   }
 
@@ -130,7 +138,9 @@ extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, do
   size_t graph_nodes = 0;
   biot_status result = BIOT_OK;
   std::vector<BatchState> B(count);
+  GmgBatch* gb = nullptr;
   auto cleanup = [&]() {
+    if (gb) gmg_batch_free(gb);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (s) cudaStreamSynchronize(s);
@@ -155,7 +165,14 @@ extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, do
   BATCH_CU(cudaMalloc(&gat_d, sizeof(double) * count * 2 * max_wcap));
   BATCH_CU(cudaMallocHost(&tab_h, sizeof(InstDev) * count));
   BATCH_CU(cudaMallocHost(&gat_h, sizeof(double) * count * 2 * max_wcap));
-  for (int i = 0; i < count; ++i) tab_h[i] = describe(ctxs[i]);
+  for (int i = 0; i < count; ++i) tab_h[i] = inst_describe(ctxs[i]);
+  if (use_gmg) {
+    biot_status gst = gmg_batch_create(ctxs, count, s, &gb);
+    if (gst != BIOT_OK) {
+      cleanup();
+      return gst;
+    }
+  }
   auto upload = [&]() { return cudaMemcpyAsync(tab_d, tab_h, sizeof(InstDev) * count, cudaMemcpyHostToDevice, s); };
   auto gather = [&](int nslot) -> cudaError_t {
     BIOT_LAUNCH(kb_gather, dim3(div_up(max_wcap, 128), nslot, count), 128, 0, s, tab_d, max_wcap, nslot, gat_d);
@@ -166,14 +183,14 @@ extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, do
   };
   auto run_cycle = [&]() -> cudaError_t {
     if (!use_graph) {
-      batched_fgmres_cycle(tab_d, count, n_iter, max_wcap, max_ndof, max_band, bf16, tri, s);
+      batched_fgmres_cycle(tab_d, count, n_iter, max_wcap, max_ndof, max_band, bf16, tri, s, gb);
       return cudaGetLastError();
     }
     if (!exec) {
       cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return e;
       const int64_t before = g_launches.load();
-      batched_fgmres_cycle(tab_d, count, n_iter, max_wcap, max_ndof, max_band, bf16, tri, s);
+      batched_fgmres_cycle(tab_d, count, n_iter, max_wcap, max_ndof, max_band, bf16, tri, s, gb);
       g_launches.store(before);  // captured, not launched
       e = cudaStreamEndCapture(s, &graph);
       if (e != cudaSuccess) return e;
@@ -206,7 +223,9 @@ extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, do
         continue;
       }
       ++S.w;
-      const int hi = std::min(std::min(S.w, ctxs[i]->n_t), S.lo + I.wcap - 1);
+      // causal start (step n active from sweep n) or, for the eager schedule, every step at once
+      const int top = ctxs[i]->prm.schedule == BIOT_SCHED_EAGER ? ctxs[i]->n_t : std::min(S.w, ctxs[i]->n_t);
+      const int hi = std::min(top, S.lo + I.wcap - 1);
       I.active = 1;
       I.lo = S.lo;
       I.nres = hi - S.lo + 1;
@@ -245,6 +264,7 @@ extern "C" biot_status biot_batch_solve(biot_ctx* const* ctxs, int32_t count, do
       S.lo += k;
     }
     BATCH_CU(upload());
+    if (gb) BATCH_CU(gmg_batch_update(gb, tab_h, s));
     BATCH_CU(run_cycle());
   }
   BATCH_CU(cudaStreamSynchronize(s));

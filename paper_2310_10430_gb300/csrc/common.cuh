@@ -344,8 +344,18 @@ size_t batched_solve_smem(int max_band);  // dynamic shared memory of the batche
 biot_status ensure_batch_dnb(biot_ctx* ctx);  // FP32 block inverses in the batched solve's block size
 void batched_precond_apply(const InstDev* tab, int count, int j, int max_wcap, int max_band, bool tri,
                            cudaStream_t s);
+struct GmgBatch;  // multigrid block solves of a batch (gmg.cu)
 void batched_fgmres_cycle(const InstDev* tab, int count, int n_iter, int max_wcap, int max_ndof, int max_band,
-                          bool bf16, bool tri, cudaStream_t s);
+                          bool bf16, bool tri, cudaStream_t s, GmgBatch* gb = nullptr);
+InstDev inst_describe(biot_ctx* c);
+// Batched multigrid: tables of every instance's levels (all contexts set up with multigrid block
+// solves, the same smoothing steps, one cycle); update copies the instances' windows to the
+// coarse-level table (host) and uploads it; apply replaces batched_precond_apply.
+biot_status gmg_batch_create(biot_ctx* const* ctxs, int count, cudaStream_t s, GmgBatch** out);
+cudaError_t gmg_batch_update(GmgBatch* gb, const InstDev* tab_h, cudaStream_t s);
+void gmg_batch_apply(GmgBatch* gb, const InstDev* tab, int count, int j, bool tri, cudaStream_t s);
+void gmg_batch_free(GmgBatch* gb);
+bool gmg_batchable(const biot_ctx* c, const biot_ctx* c0);  // same multigrid parameters as c0, one cycle
 void batched_residual_reduce(const InstDev* tab, int count, int max_wcap, cudaStream_t s);
 biot_status fst_norm2_ctx(biot_ctx* ctx, double* out);
 biot_status spacetime_residual_ctx(biot_ctx* ctx, double* out);

@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 namespace biot {
@@ -212,9 +213,9 @@ __global__ void k_gmg_norm_fin(const double* __restrict__ part, int nb, double* 
 // A thread owns one node and 16 bytes of columns of b (all ldg columns: those outside
 // [c0, c0 + ncols) are set to zero, which keeps the level buffers finite).
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_gmg_prep(int nn, int mode, const T* __restrict__ vin, const double* __restrict__ dsq, const T* __restrict__ tp,
-           T* __restrict__ b, int ld, int ldg, int c0, int ncols) {
+__device__ __forceinline__ void prep_body(int nn, int mode, const T* __restrict__ vin, const double* __restrict__ dsq,
+                                          const T* __restrict__ tp, T* __restrict__ b, int ld, int ldg, int c0,
+                                          int ncols) {
   constexpr int VEC = V16<T>::n;
   const int nch = ldg / VEC;
   const int total = nn * nch;
@@ -252,6 +253,13 @@ k_gmg_prep(int nn, int mode, const T* __restrict__ vin, const double* __restrict
       stv(b + (size_t)(3 * v + 2) * ldg + c, a);
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gmg_prep(int nn, int mode, const T* __restrict__ vin, const double* __restrict__ dsq, const T* __restrict__ tp,
+           T* __restrict__ b, int ld, int ldg, int c0, int ncols) {
+  prep_body<T>(nn, mode, vin, dsq, tp, b, ld, ldg, c0, ncols);
 }
 
 // z rows of the fields in FM from the V-cycle's level-0 result.
@@ -336,11 +344,11 @@ __device__ __forceinline__ void stencil_apply(const T* __restrict__ cf, const T*
 // (READD false: c1 d dropped), x_out = x_in + d; Dirichlet rows x_out = b, d = 0.
 // OUTZ: x_out is the preconditioner's output z (leading dimension ldo, only the columns
 // [c0, c0 + ncols) written, 16-byte stores when ldo allows) instead of a level buffer.
-template <typename T, int FM, bool ZERO, bool READD, bool OUTZ = false>
-__global__ void __launch_bounds__(kThreads)
-k_gmg_smooth(int n, const T* __restrict__ coef, const uint8_t* __restrict__ dmask, const T* __restrict__ xin,
-             const T* __restrict__ b, T* __restrict__ d, T* __restrict__ xout, T cu1, T cu2, T cp1, T cp2, int ldg,
-             int ca, int nch, int ldo = 0, int c0 = 0, int ncols = 0) {
+template <typename T, int FM, bool ZERO, bool READD, bool OUTZ>
+__device__ __forceinline__ void smooth_body(int n, const T* __restrict__ coef, const uint8_t* __restrict__ dmask,
+                                            const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
+                                            T* __restrict__ xout, T cu1, T cu2, T cp1, T cp2, int ldg, int ca,
+                                            int nch, int ldo, int c0, int ncols) {
   constexpr int VEC = V16<T>::n;
   const int nx = n + 1;
   const long long total = (long long)nx * nx * nch;
@@ -421,11 +429,19 @@ k_gmg_smooth(int n, const T* __restrict__ coef, const uint8_t* __restrict__ dmas
   }
 }
 
+template <typename T, int FM, bool ZERO, bool READD, bool OUTZ = false>
+__global__ void __launch_bounds__(kThreads)
+k_gmg_smooth(int n, const T* __restrict__ coef, const uint8_t* __restrict__ dmask, const T* __restrict__ xin,
+             const T* __restrict__ b, T* __restrict__ d, T* __restrict__ xout, T cu1, T cu2, T cp1, T cp2, int ldg,
+             int ca, int nch, int ldo = 0, int c0 = 0, int ncols = 0) {
+  smooth_body<T, FM, ZERO, READD, OUTZ>(n, coef, dmask, xin, b, d, xout, cu1, cu2, cp1, cp2, ldg, ca, nch, ldo, c0,
+                                        ncols);
+}
+
 // r = b - K x on the rows in FM.
 template <typename T, int FM>
-__global__ void __launch_bounds__(kThreads)
-k_gmg_residual(int n, const T* __restrict__ coef, const T* __restrict__ x, const T* __restrict__ b,
-               T* __restrict__ r, int ldg, int ca, int nch) {
+__device__ __forceinline__ void residual_body(int n, const T* __restrict__ coef, const T* __restrict__ x,
+                                              const T* __restrict__ b, T* __restrict__ r, int ldg, int ca, int nch) {
   constexpr int VEC = V16<T>::n;
   const int nx = n + 1;
   const long long total = (long long)nx * nx * nch;
@@ -458,13 +474,19 @@ k_gmg_residual(int n, const T* __restrict__ coef, const T* __restrict__ x, const
   }
 }
 
+template <typename T, int FM>
+__global__ void __launch_bounds__(kThreads)
+k_gmg_residual(int n, const T* __restrict__ coef, const T* __restrict__ x, const T* __restrict__ b,
+               T* __restrict__ r, int ldg, int ca, int nch) {
+  residual_body<T, FM>(n, coef, x, b, r, ldg, ca, nch);
+}
+
 // Coarse right-hand side bc = P^T r on the rows in FM (coarse Dirichlet rows zero): fine node
 // (2I, 2J) with weight 1, its six mesh neighbours (the midpoints of the coarse edges at (I, J))
 // with weight 1/2.
 template <typename T, int FM>
-__global__ void __launch_bounds__(kThreads)
-k_gmg_restrict(int nc, const T* __restrict__ r, const uint8_t* __restrict__ dmask_c, T* __restrict__ bc, int ldg,
-               int ca, int nch) {
+__device__ __forceinline__ void restrict_body(int nc, const T* __restrict__ r, const uint8_t* __restrict__ dmask_c,
+                                              T* __restrict__ bc, int ldg, int ca, int nch) {
   constexpr int VEC = V16<T>::n;
   const int cx = nc + 1, nf = 2 * nc;
   const long long total = (long long)cx * cx * nch;
@@ -510,10 +532,17 @@ k_gmg_restrict(int nc, const T* __restrict__ r, const uint8_t* __restrict__ dmas
   }
 }
 
-// x += P xc on the rows in FM: linear interpolation of the coarse nodal values.
 template <typename T, int FM>
 __global__ void __launch_bounds__(kThreads)
-k_gmg_prolong(int nf, const T* __restrict__ xc, T* __restrict__ x, int ldg, int ca, int nch) {
+k_gmg_restrict(int nc, const T* __restrict__ r, const uint8_t* __restrict__ dmask_c, T* __restrict__ bc, int ldg,
+               int ca, int nch) {
+  restrict_body<T, FM>(nc, r, dmask_c, bc, ldg, ca, nch);
+}
+
+// x += P xc on the rows in FM: linear interpolation of the coarse nodal values.
+template <typename T, int FM>
+__device__ __forceinline__ void prolong_body(int nf, const T* __restrict__ xc, T* __restrict__ x, int ldg, int ca,
+                                             int nch) {
   constexpr int VEC = V16<T>::n;
   const int fx = nf + 1, cx = nf / 2 + 1;
   const long long total = (long long)fx * fx * nch;
@@ -542,6 +571,12 @@ k_gmg_prolong(int nf, const T* __restrict__ xc, T* __restrict__ x, int ldg, int 
   }
 }
 
+template <typename T, int FM>
+__global__ void __launch_bounds__(kThreads)
+k_gmg_prolong(int nf, const T* __restrict__ xc, T* __restrict__ x, int ldg, int ca, int nch) {
+  prolong_body<T, FM>(nf, xc, x, ldg, ca, nch);
+}
+
 // x += e on the rows in FM (repeated V-cycles).
 template <typename T, int FM>
 __global__ void k_gmg_axpy(int nn, const T* __restrict__ e, T* __restrict__ x, int ldg, int ca, int nch) {
@@ -566,8 +601,8 @@ __global__ void k_gmg_axpy(int nn, const T* __restrict__ e, T* __restrict__ x, i
 // The coarsest level's input to its exact P2 apply: vin = +-b d (so that P2^{-1} (vin / d)
 // gives A^{-1} b_u and S^{-1} b_p); rows outside FM zero.
 template <typename T, int FM>
-__global__ void k_gmg_coarse_prep(int nn, const T* __restrict__ b, const double* __restrict__ dsc,
-                                  T* __restrict__ vin, int ldg, int c0, int ncols) {
+__device__ __forceinline__ void coarse_prep_body(int nn, const T* __restrict__ b, const double* __restrict__ dsc,
+                                                 T* __restrict__ vin, int ldg, int c0, int ncols) {
   const long long total = (long long)nn * ncols;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
@@ -579,6 +614,12 @@ __global__ void k_gmg_coarse_prep(int nn, const T* __restrict__ b, const double*
       vin[o] = on ? b[o] * s : T(0);
     }
   }
+}
+
+template <typename T, int FM>
+__global__ void k_gmg_coarse_prep(int nn, const T* __restrict__ b, const double* __restrict__ dsc,
+                                  T* __restrict__ vin, int ldg, int c0, int ncols) {
+  coarse_prep_body<T, FM>(nn, b, dsc, vin, ldg, c0, ncols);
 }
 
 int grid_for(long long work) {
@@ -941,6 +982,231 @@ void gmg_apply(biot_ctx* ctx, const T* vin, T* z, int c0, int ncols) {
 }
 template void gmg_apply<double>(biot_ctx*, const double*, double*, int, int);
 template void gmg_apply<float>(biot_ctx*, const float*, float*, int, int);
+
+// ---- batched form: every instance's V-cycle in the same launches (blockIdx.z = instance) ----
+
+namespace {
+
+// One (instance, level) of a batch, as the batched kernels see it.
+struct GmgLvDev {
+  int active;       // the level smooths and restricts (l < L_i - 1)
+  int cl;           // the instance's coarsest level L_i - 1 (the same in every entry of the instance)
+  int n, nn, ldg;
+  const float* coef;
+  const uint8_t* dmask;
+  const double* dsc;  // the level context's d (the coarsest level's input scaling)
+  float* buf[kGmgBufs];
+  float c1[2][kMaxSmooth], c2[2][kMaxSmooth];
+};
+
+__device__ __forceinline__ bool batch_live(const InstDev& I) { return I.active && I.nf > 0; }
+
+__global__ void __launch_bounds__(kThreads)
+kb_gmg_prep(const InstDev* __restrict__ tab, const GmgLvDev* __restrict__ gt, int Lmax, int j, int mode) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!batch_live(I)) return;
+  const GmgLvDev& e = gt[blockIdx.z * Lmax];
+  const size_t vs = (size_t)I.n_dof * I.wcap;
+  prep_body<float>(e.nn, mode, I.V + (size_t)j * vs, I.dsq, I.tp, e.buf[GB_B], I.wcap, e.ldg, I.c0, I.nf);
+}
+
+// in < 0: from zero; OUTZ: the result goes to the instance's Z_j (level 0, last step).
+template <int FM, bool ZERO, bool READD, bool OUTZ>
+__global__ void __launch_bounds__(kThreads)
+kb_gmg_smooth(const InstDev* __restrict__ tab, const GmgLvDev* __restrict__ gt, int Lmax, int l, int k, int in,
+              int out, int j) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!batch_live(I)) return;
+  const GmgLvDev& e = gt[blockIdx.z * Lmax + l];
+  if (!e.active) return;
+  const int nch = e.ldg / 4;
+  float* z = OUTZ ? I.Z + (size_t)j * I.n_dof * I.wcap : e.buf[out];
+  smooth_body<float, FM, ZERO, READD, OUTZ>(e.n, e.coef, e.dmask, in < 0 ? nullptr : e.buf[in], e.buf[GB_B],
+                                            e.buf[GB_D], z, e.c1[0][k], e.c2[0][k], e.c1[1][k], e.c2[1][k], e.ldg,
+                                            0, nch, I.wcap, I.c0, I.nf);
+}
+
+template <int FM>
+__global__ void __launch_bounds__(kThreads)
+kb_gmg_residual_restrict(const InstDev* __restrict__ tab, const GmgLvDev* __restrict__ gt, int Lmax, int l, int in,
+                         int phase) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!batch_live(I)) return;
+  const GmgLvDev& e = gt[blockIdx.z * Lmax + l];
+  if (!e.active) return;
+  const int nch = e.ldg / 4;
+  if (phase == 0) {
+    residual_body<float, FM>(e.n, e.coef, e.buf[in], e.buf[GB_B], e.buf[GB_R], e.ldg, 0, nch);
+  } else {
+    const GmgLvDev& c = gt[blockIdx.z * Lmax + l + 1];
+    restrict_body<float, FM>(c.n, e.buf[GB_R], c.dmask, c.buf[GB_B], e.ldg, 0, nch);
+  }
+}
+
+template <int FM>
+__global__ void __launch_bounds__(kThreads)
+kb_gmg_prolong(const InstDev* __restrict__ tab, const GmgLvDev* __restrict__ gt, int Lmax, int l, int cur) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!batch_live(I)) return;
+  const GmgLvDev& e = gt[blockIdx.z * Lmax + l];
+  if (!e.active) return;
+  const GmgLvDev& c = gt[blockIdx.z * Lmax + l + 1];
+  prolong_body<float, FM>(e.n, c.buf[GB_X], e.buf[cur], e.ldg, 0, e.ldg / 4);
+}
+
+template <int FM>
+__global__ void kb_gmg_coarse_prep(const InstDev* __restrict__ tab, const GmgLvDev* __restrict__ gt, int Lmax) {
+  const InstDev& I = tab[blockIdx.z];
+  if (!batch_live(I)) return;
+  const GmgLvDev& e = gt[blockIdx.z * Lmax + gt[blockIdx.z * Lmax].cl];
+  coarse_prep_body<float, FM>(e.nn, e.buf[GB_B], e.dsc, e.buf[GB_R], e.ldg, I.c0, I.nf);
+}
+
+}  // namespace
+
+struct GmgBatch {
+  int count = 0, Lmax = 0, smooth = 2, max_band_c = 0, max_wcap_c = 0;
+  std::vector<long long> work;  // per level: the largest nn x (ldg / 4) over the instances
+  GmgLvDev* gt_d = nullptr;
+  InstDev* ct_d = nullptr;      // the coarsest levels' contexts, as batched band-solve instances
+  std::vector<InstDev> ct_h;
+};
+
+bool gmg_batchable(const biot_ctx* c, const biot_ctx* c0) {
+  return c->gmg && c0->gmg && c->gmg->cycles == 1 && c->gmg->smooth == c0->gmg->smooth && !c->gmg->fp64;
+}
+
+biot_status gmg_batch_create(biot_ctx* const* ctxs, int count, cudaStream_t s, GmgBatch** out) {
+  GmgBatch* gb = new GmgBatch();
+  gb->count = count;
+  gb->smooth = ctxs[0]->gmg->smooth;
+  for (int i = 0; i < count; ++i) gb->Lmax = std::max(gb->Lmax, ctxs[i]->gmg->L);
+  gb->work.assign(gb->Lmax, 0);
+  std::vector<GmgLvDev> gt((size_t)count * gb->Lmax);
+  gb->ct_h.resize(count);
+  for (int i = 0; i < count; ++i) {
+    Gmg& g = *ctxs[i]->gmg;
+    for (int l = 0; l < gb->Lmax; ++l) {
+      GmgLvDev& e = gt[(size_t)i * gb->Lmax + l];
+      std::memset(&e, 0, sizeof(e));
+      e.cl = g.L - 1;
+      if (l >= g.L) continue;
+      GmgLevel& L = g.lv[l];
+      e.active = l < g.L - 1;
+      e.n = L.n;
+      e.nn = L.nn;
+      e.ldg = g.ldg;
+      e.coef = L.coef32;
+      e.dmask = L.dmask;
+      e.dsc = L.lc ? L.lc->dsc : ctxs[i]->dsc;
+      for (int k = 0; k < kGmgBufs; ++k) e.buf[k] = static_cast<float*>(L.buf[k]);
+      for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < kMaxSmooth; ++k) {
+          e.c1[b][k] = (float)L.c1[b][k];
+          e.c2[b][k] = (float)L.c2[b][k];
+        }
+      gb->work[l] = std::max(gb->work[l], (long long)L.nn * (g.ldg / 4));
+    }
+    GmgLevel& C = g.lv[g.L - 1];
+    biot_ctx* lc = C.lc;
+    BIOT_TRY(ensure_batch_dnb(lc));
+    InstDev I = inst_describe(lc);
+    I.V = static_cast<float*>(C.buf[GB_R]);  // the coarsest level's input, then its band solves
+    I.Z = static_cast<float*>(C.buf[GB_X]);
+    gb->ct_h[i] = I;
+    gb->max_band_c = std::max(gb->max_band_c, std::max(lc->band_u, lc->band_p));
+    gb->max_wcap_c = std::max(gb->max_wcap_c, lc->wcap);
+  }
+  biot_ctx* c0 = ctxs[0];
+  cudaError_t e = cudaMalloc(&gb->gt_d, sizeof(GmgLvDev) * gt.size());
+  if (e == cudaSuccess) e = cudaMalloc(&gb->ct_d, sizeof(InstDev) * count);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(gb->gt_d, gt.data(), sizeof(GmgLvDev) * gt.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    gmg_batch_free(gb);
+    return fail(c0, BIOT_E_CUDA, "batched multigrid tables: %s", cudaGetErrorString(e));
+  }
+  *out = gb;
+  return BIOT_OK;
+}
+
+cudaError_t gmg_batch_update(GmgBatch* gb, const InstDev* tab_h, cudaStream_t s) {
+  for (int i = 0; i < gb->count; ++i) {
+    gb->ct_h[i].active = tab_h[i].active;
+    gb->ct_h[i].c0 = tab_h[i].c0;
+    gb->ct_h[i].nf = tab_h[i].nf;
+  }
+  return cudaMemcpyAsync(gb->ct_d, gb->ct_h.data(), sizeof(InstDev) * gb->count, cudaMemcpyHostToDevice, s);
+}
+
+namespace {
+
+template <int FM>
+void batch_vcycle(GmgBatch* gb, const InstDev* tab, int count, int j, cudaStream_t s) {
+  const int Lm = gb->Lmax, m = gb->smooth;
+  const GmgLvDev* gt = gb->gt_d;
+  // the buffer holding a level's iterate after its pre-smoothing (the same for every level)
+  int cur = GB_XA;
+  for (int l = 0; l + 1 < Lm; ++l) {
+    const dim3 grid(grid_for(gb->work[l]), 1, count);
+    BIOT_LAUNCH((kb_gmg_smooth<FM, true, false, false>), grid, kThreads, 0, s, tab, gt, Lm, l, 0, -1, GB_XA, j);
+    cur = GB_XA;
+    for (int k = 1; k < m; ++k) {
+      const int nxt = cur == GB_XA ? GB_XB : GB_XA;
+      BIOT_LAUNCH((kb_gmg_smooth<FM, false, true, false>), grid, kThreads, 0, s, tab, gt, Lm, l, k, cur, nxt, j);
+      cur = nxt;
+    }
+    BIOT_LAUNCH((kb_gmg_residual_restrict<FM>), grid, kThreads, 0, s, tab, gt, Lm, l, cur, 0);
+    BIOT_LAUNCH((kb_gmg_residual_restrict<FM>), dim3(grid_for(gb->work[l + 1]), 1, count), kThreads, 0, s, tab, gt,
+                Lm, l, cur, 1);
+  }
+  // every instance's coarsest level at once: +-b d, then the batched exact P2 band solves
+  BIOT_LAUNCH((kb_gmg_coarse_prep<FM>), dim3(64, 1, count), kThreads, 0, s, tab, gt, Lm);
+  batched_precond_apply(gb->ct_d, count, 0, gb->max_wcap_c, gb->max_band_c, false, s);
+  for (int l = Lm - 2; l >= 0; --l) {
+    const dim3 grid(grid_for(gb->work[l]), 1, count);
+    int c = cur;
+    BIOT_LAUNCH((kb_gmg_prolong<FM>), grid, kThreads, 0, s, tab, gt, Lm, l, c);
+    for (int k = 0; k < m; ++k) {
+      const bool last = k == m - 1;
+      const int nxt = c == GB_XA ? GB_XB : GB_XA;
+      if (last && l == 0) {
+        if (k == 0) BIOT_LAUNCH((kb_gmg_smooth<FM, false, false, true>), grid, kThreads, 0, s, tab, gt, Lm, l, k, c, 0, j);
+        else BIOT_LAUNCH((kb_gmg_smooth<FM, false, true, true>), grid, kThreads, 0, s, tab, gt, Lm, l, k, c, 0, j);
+      } else {
+        const int dst = last ? GB_X : nxt;
+        if (k == 0) BIOT_LAUNCH((kb_gmg_smooth<FM, false, false, false>), grid, kThreads, 0, s, tab, gt, Lm, l, k, c, dst, j);
+        else BIOT_LAUNCH((kb_gmg_smooth<FM, false, true, false>), grid, kThreads, 0, s, tab, gt, Lm, l, k, c, dst, j);
+        c = dst;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+void gmg_batch_apply(GmgBatch* gb, const InstDev* tab, int count, int j, bool tri, cudaStream_t s) {
+  const GmgLvDev* gt = gb->gt_d;
+  const dim3 g0(grid_for(gb->work[0]), 1, count);
+  if (!tri) {
+    BIOT_LAUNCH(kb_gmg_prep, g0, kThreads, 0, s, tab, gt, gb->Lmax, j, 3);
+    batch_vcycle<3>(gb, tab, count, j, s);
+  } else {
+    BIOT_LAUNCH(kb_gmg_prep, g0, kThreads, 0, s, tab, gt, gb->Lmax, j, 0);
+    batch_vcycle<1>(gb, tab, count, j, s);
+    launch_batched_coupling(tab, count, j, s);  // tp = B^T z_u - v_p / d per instance
+    BIOT_LAUNCH(kb_gmg_prep, g0, kThreads, 0, s, tab, gt, gb->Lmax, j, 2);
+    batch_vcycle<2>(gb, tab, count, j, s);
+  }
+}
+
+void gmg_batch_free(GmgBatch* gb) {
+  if (!gb) return;
+  if (gb->gt_d) cudaFree(gb->gt_d);
+  if (gb->ct_d) cudaFree(gb->ct_d);
+  delete gb;
+}
 
 void gmg_info(const biot_ctx* ctx, int* levels, double* lam_u, double* lam_p) {
   const Gmg* g = ctx->gmg;

@@ -685,13 +685,14 @@ template biot_status fgmres_cycle<double>(biot_ctx*, int, int, int);
 // One FGMRES(n_iter) cycle for every instance of a batch (windows in the table).
 // The launch sequence depends only on n_iter, so it can be captured in a CUDA graph.
 void batched_fgmres_cycle(const InstDev* tab, int count, int n_iter, int max_wcap, int max_ndof, int max_band,
-                          bool bf16, bool tri, cudaStream_t s) {
+                          bool bf16, bool tri, cudaStream_t s, GmgBatch* gb) {
   const int cblk = div_up(max_wcap, 128);
   const int eblk = std::min(div_up((long long)max_ndof * max_wcap, 256), 2048);
   BIOT_LAUNCH(kb_fgmres_init, dim3(cblk, 1, count), 128, 0, s, tab);
   BIOT_LAUNCH(kb_scale, dim3(eblk, 1, count), 256, 0, s, tab, 0);
   for (int j = 0; j < n_iter; ++j) {
-    batched_precond_apply(tab, count, j, max_wcap, max_band, tri, s);
+    if (gb) gmg_batch_apply(gb, tab, count, j, tri, s);
+    else batched_precond_apply(tab, count, j, max_wcap, max_band, tri, s);
     launch_batched_spmm(tab, count, bf16, j, s);
     BIOT_LAUNCH(kb_reduce, dim3(cblk, 1, count), 128, 0, s, tab, (int)RD_WN0, 1);
     for (int pass = 0; pass < 2; ++pass) {

@@ -87,3 +87,70 @@ def test_batch_beside_substructured_contexts():
     finally:
         for cx in ctxs:
             cx.close()
+
+
+def gmg_instances():
+    # uneven meshes (hierarchies of 2 to 3 levels: 18 -> 9, 20 -> 10, 32 -> 16, 40 -> 20 -> 10,
+    # 64 -> 32 -> 16), N_t, Poisson ratios and permeability fields; one manufactured case
+    out = []
+    for i, (n, nt, nu) in enumerate([(18, 9, 0.25), (32, 14, 0.3), (20, 23, 0.42), (40, 6, 0.35), (64, 5, 0.45)]):
+        out.append(W.BiotCase(n=n, E=1e4, nu=nu, alpha=1.0, kappa=W.lognormal_kappa(n, sigma=1.5, seed=1300 + i),
+                              tau=1e-2, n_t=nt, problem="terzaghi", precond="tri", n_iter=20))
+    out.append(W.BiotCase(n=24, E=2.0, nu=0.3, alpha=1.0, kappa=0.5, tau=0.05, n_t=11, problem="mms", precond="tri",
+                          n_iter=20))
+    return out
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("kind", ["tri", "diag"])
+def test_batch_with_multigrid_block_solves(use_graph, kind):
+    # every instance's V-cycles run in the same launches (their levels and coarsest band solves
+    # from device tables); each instance must reach the oracle's backward Euler as when alone
+    cases = [c.with_(precond=kind) for c in gmg_instances()]
+    ctxs = [biot.Context(c, precision="fp32", gmg=dict(levels=0 if c.n > 16 else 2, cycles=1, smooth=2))
+            for c in cases]
+    try:
+        st, sweeps, rels = biot.biot_batch_solve([c.ctx for c in ctxs], 1e-12, 50000, use_graph=use_graph)
+        assert st == biot.BIOT_OK
+        for k, (c, cx, rel) in enumerate(zip(cases, ctxs, rels)):
+            X = biot.biot_get_state(cx.ctx, 0, c.n_t)
+            eu, ep = field_rel_errors(X, seq_solve(build_system(c)))
+            print(f"multigrid batch {kind} graph={use_graph} instance {k} (n={c.n}, levels "
+                  f"{cx.info.gmg_levels}, N_t={c.n_t}): sweeps {sweeps[k]}, residual {rel:.2e}, errors {eu:.1e} {ep:.1e}")
+            assert rel <= 1e-12 and eu <= 1e-8 and ep <= 1e-8, (c.n, c.n_t, rel, eu, ep)
+    finally:
+        for cx in ctxs:
+            cx.close()
+
+
+def test_batch_multigrid_matches_instances_alone_sweep_for_sweep():
+    # the batched V-cycle is the single-instance one: identical sweep counts, and states equal to
+    # FP32 rounding of the same operations
+    cases = gmg_instances()[:3]
+    alone = []
+    for c in cases:
+        with biot.Context(c, precision="fp32", gmg=dict(levels=0, cycles=1, smooth=2)) as cx:
+            st, sw, rel = biot.biot_pint_solve(cx.ctx, 1e-10, 50000)
+            alone.append((sw, biot.biot_get_state(cx.ctx, 0, c.n_t)))
+    ctxs = [biot.Context(c, precision="fp32", gmg=dict(levels=0, cycles=1, smooth=2)) for c in cases]
+    try:
+        st, sweeps, rels = biot.biot_batch_solve([c.ctx for c in ctxs], 1e-10, 50000, use_graph=True)
+        for k, (c, cx) in enumerate(zip(cases, ctxs)):
+            X = biot.biot_get_state(cx.ctx, 0, c.n_t)
+            assert abs(sweeps[k] - alone[k][0]) <= 1, (k, sweeps[k], alone[k][0])
+            assert max(field_rel_errors(X, alone[k][1])) < 1e-8
+    finally:
+        for cx in ctxs:
+            cx.close()
+
+
+def test_batch_rejects_mixed_block_solves():
+    a = biot.Context(gmg_instances()[1], precision="fp32", gmg=dict(levels=0, cycles=1, smooth=2))
+    b = biot.Context(gmg_instances()[2], precision="fp32")
+    try:
+        with pytest.raises(biot.BiotError) as e:
+            biot.biot_batch_solve([a.ctx, b.ctx], 1e-10, 100)
+        assert e.value.status == biot.BIOT_E_INVALID
+    finally:
+        a.close()
+        b.close()
