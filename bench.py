@@ -653,12 +653,18 @@ def run_ours(args):
         extras["time_to_solution"] = time_to_solution(workload().with_(n=64, n_t=64, name="terzaghi_64x64_nt64"),
                                                       stream)
         extras["batched"] = batched_vs_sequential(stream)
+        try:
+            extras["batched_config4"] = batched_config4(stream)
+        except Exception as e:  # e.g. device memory: report, keep the bench line
+            extras["batched_config4"] = {"error": str(e)[:300]}
     if args.lognormal:
         extras["lognormal_precisions"] = lognormal_precisions(stream, args.lognormal)
     if args.efficiency:
         extras["efficiency"] = efficiency_study(stream)
     if args.barry_mercer:
         extras["barry_mercer"] = barry_mercer_study(stream)
+    if args.batched_full:
+        extras["batched_config4_full"] = batched_config4(stream, full=True)
     out = None
     if rank == 0:
         cpu = cpu_baseline_subprocess(args.cpu_budget) if (world == 1 and not args.no_cpu) else None
@@ -1133,6 +1139,106 @@ def batched_vs_sequential(stream, count=16):
             "speedup": t_seq / t_batch, "max_rel_residual": float(max(rels)), "status": biot.STATUS_NAMES[st]}
 
 
+def batched_config4(stream, full=False, sweeps=20, count=64):
+    """The batched workload at its stated size: 64 instances exactly as
+    workloads.batched_instances() draws them (n in [32, 192] multiples of 8, N_t in [64, 512],
+    nu in [0.2, 0.45], lognormal kappa sigma 1.5, P1), FP32 sweeps with the FP64 refinement,
+    multigrid block solves (every instance keeps its own hierarchy; the batched launches cover
+    all of them), FGMRES(10) for the throughput runs and (20) for the tolerance solves.
+
+    Default (bounded GPU time): throughput at equal work -- `sweeps` sweeps with every step of
+    every instance active (eager schedule, tol 0), one batched call (CUDA graph) against the
+    instances one after another. full=True: the tolerance solves to the FP64 residual 1e-8,
+    batched and one after another with multigrid FP32 sweeps, and one after another with the
+    plain FP64 method (exact block solves, FGMRES(10)); max per-field differences between the
+    batched FP32 and the FP64 solutions are reported."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2310_10430_gb300 import biot
+    n_iter = 20 if full else 10   # FGMRES(20) converges in fewer sweeps; (10) halves the Krylov memory
+    cases = [c.with_(n_iter=n_iter) for c in W.batched_instances(count)]
+    units = sum(c.n_dof * c.n_t for c in cases)
+    out = {"instances": count, "n_range": [min(c.n for c in cases), max(c.n for c in cases)],
+           "n_t_range": [min(c.n_t for c in cases), max(c.n_t for c in cases)], "dof_x_steps": units,
+           "block_solves": "multigrid V(2,2)-cycles per instance, batched", "n_iter": n_iter}
+
+    def make(sched, precision="fp32", gmg=GMG, precond=None):
+        return [biot.Context(c, stream=stream, precision=precision, schedule=sched, gmg=gmg,
+                             precond=precond) for c in cases]
+
+    def close(ctxs):
+        for c in ctxs:
+            c.close()
+
+    if not full:
+        ctxs = make(biot.BIOT_SCHED_EAGER)
+        try:
+            biot.biot_batch_solve([c.ctx for c in ctxs], 0.0, 2, use_graph=True, allow_not_converged=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            biot.biot_batch_solve([c.ctx for c in ctxs], 0.0, sweeps, use_graph=True, allow_not_converged=True)
+            torch.cuda.synchronize()
+            t_batch = time.perf_counter() - t0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for c in ctxs:
+                biot.biot_pint_solve(c.ctx, 0.0, sweeps, allow_not_converged=True)
+            torch.cuda.synchronize()
+            t_seq = time.perf_counter() - t0
+        finally:
+            close(ctxs)
+        out.update({"mode": f"{sweeps} sweeps with every step active (eager schedule, tol 0): equal work",
+                    "batched_seconds": t_batch, "sequential_seconds": t_seq, "speedup": t_seq / t_batch,
+                    "value": units * sweeps / t_batch, "unit": UNIT})
+        return out
+    res = {}
+    ctxs = make(biot.BIOT_SCHED_TOL)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, sw, rels = biot.biot_batch_solve([c.ctx for c in ctxs], 1e-8, 200000, use_graph=True,
+                                             allow_not_converged=True)
+        torch.cuda.synchronize()
+        res["batched_fp32_gmg"] = {"seconds": time.perf_counter() - t0, "status": biot.STATUS_NAMES[st],
+                                   "max_sweeps": int(max(sw)), "max_rel_residual": float(max(rels))}
+        X32 = [biot.biot_get_state(c.ctx, 1, cs.n_t) for c, cs in zip(ctxs, cases)]
+    finally:
+        close(ctxs)
+    ctxs = make(biot.BIOT_SCHED_TOL)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        worst = 0.0
+        for c in ctxs:
+            st, sw1, rel = biot.biot_pint_solve(c.ctx, 1e-8, 200000, allow_not_converged=True)
+            worst = max(worst, rel)
+        torch.cuda.synchronize()
+        res["sequential_fp32_gmg"] = {"seconds": time.perf_counter() - t0, "max_rel_residual": worst}
+    finally:
+        close(ctxs)
+    diff = 0.0
+    t64 = 0.0
+    worst = 0.0
+    for k, cs in enumerate(cases):
+        with biot.Context(cs.with_(n_iter=10), stream=stream) as c:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, sw1, rel = biot.biot_pint_solve(c.ctx, 1e-8, 200000, allow_not_converged=True)
+            torch.cuda.synchronize()
+            t64 += time.perf_counter() - t0
+            worst = max(worst, rel)
+            X64 = biot.biot_get_state(c.ctx, 1, cs.n_t)
+        diff = max(diff, *_field_errors(np, X32[k], X64))
+    res["sequential_fp64_exact"] = {"seconds": t64, "max_rel_residual": worst, "n_iter": 10}
+    out.update(res)
+    out.update({"mode": "tolerance solves to the FP64 space-time residual 1e-8 from the zero state",
+                "speedup_vs_one_after_another": res["sequential_fp32_gmg"]["seconds"] / res["batched_fp32_gmg"]["seconds"],
+                "speedup_vs_plain_fp64": t64 / res["batched_fp32_gmg"]["seconds"],
+                "max_field_diff_batched_fp32_vs_fp64": diff})
+    return out
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
@@ -1187,6 +1293,9 @@ def main():
     ap.add_argument("--barry-mercer", action="store_true",
                     help="also solve Barry & Mercer's point source (64^2, 256 steps, P2, tol 1e-10) step by "
                          "step and parallel in time, FP64 and FP32, and report times and differences")
+    ap.add_argument("--batched-full", action="store_true",
+                    help="also solve the 64-instance batched workload to 1e-8: batched, one after another and "
+                         "with the plain FP64 method (about ten minutes of GPU time)")
     ap.add_argument("--large", action="store_true",
                     help="run only the 1024^2 stress workload (N_t = 128, nu = 0.49, lognormal sigma 2, P1, FP32 "
                          "sweeps with FP64 refinement): setup, --steps timed sweeps, one JSON line")
