@@ -72,8 +72,14 @@ typedef enum {
 typedef enum {
   BIOT_TERZAGHI = 0,         /* consolidation column: top load, drained top, fixed bottom, roller sides */
   BIOT_MMS_TRIG = 1,         /* manufactured cos t cos 3 pi x cos 3 pi y solution, Dirichlet on all sides (Sec. 4.1) */
-  BIOT_BARRY_MERCER = 2      /* point source -0.5 load delta_(a/4, b/4) sin(beta t), beta = (lambda + 2 mu) K / (a b);
+  BIOT_BARRY_MERCER = 2,     /* point source -0.5 load delta_(a/4, b/4) sin(beta t), beta = (lambda + 2 mu) K / (a b);
                                 drained, zero tangential displacement on every side (Sec. 4.2) */
+  BIOT_MANDEL = 3            /* quarter domain under a rigid frictionless plate pressed with the force F = load
+                                (Sec. 4.3): x = a drained and traction-free, x = 0 and y = 0 symmetry planes
+                                (u_x = 0, u_y = 0, no flux), impervious top with u_y constant along x, imposed
+                                by the penalty 1e6 (lambda + 2 mu) (u_y(i+1) - u_y(i))^2 / 2 over consecutive top
+                                nodes, the force as the traction (0, -F / a); initial state the undrained response
+                                of Sec. 4.3 (Skempton B = 1) */
 } biot_problem;
 
 typedef enum {

@@ -58,3 +58,33 @@ def l2_error_p1(coords, tris, nodal, exact_fn):
         vh = lb[0] * vals[:, 0] + lb[1] * vals[:, 1] + lb[2] * vals[:, 2]
         total += QUAD7_W[q] * (vh - exact_fn(x, y)) ** 2
     return float(np.sqrt(np.sum(total * area)))
+
+
+def mandel_pressure(x, t, E, nu, K, F=1.0, a=1.0, terms=200):
+    """Pressure of Mandel's problem (the analytic series the paper cites for Sec. 4.3) for
+    alpha = 1 and no storage (Skempton B = 1):
+
+        p(x, t) = 2 F B (1 + nu_u) / (3 a) sum_i sin(al_i) / (al_i - sin(al_i) cos(al_i))
+                  (cos(al_i x / a) - cos(al_i)) exp(-al_i^2 c t / a^2),
+
+    al_i the positive roots of tan(al) = (1 - nu) / (nu_u - nu) al (bracketed one per branch of
+    tan and found by bisection), c = 2 K B^2 G (1 - nu) (1 + nu_u)^2 / (9 (1 - nu_u) (nu_u - nu)),
+    G = E / (2 (1 + nu)). At t -> 0+ it tends to the undrained p0 = F B (1 + nu_u) / (3 a)."""
+    from scipy.optimize import brentq
+    B = 1.0
+    nu_u = (3 * nu + B * (1 - 2 * nu)) / (3 - B * (1 - 2 * nu))
+    G = E / (2 * (1 + nu))
+    c = 2 * K * B ** 2 * G * (1 - nu) * (1 + nu_u) ** 2 / (9 * (1 - nu_u) * (nu_u - nu))
+    r = (1 - nu) / (nu_u - nu)
+    f = lambda al: np.sin(al) - r * al * np.cos(al)
+    roots = []
+    i = 0
+    while len(roots) < terms:
+        lo, hi = max(1e-9, (i - 0.5) * np.pi + 1e-12), (i + 0.5) * np.pi - 1e-12
+        if f(lo) * f(hi) < 0:
+            roots.append(brentq(f, lo, hi, xtol=1e-15))
+        i += 1
+    al = np.array(roots)
+    x = np.asarray(x, dtype=np.float64)
+    coef = np.sin(al) / (al - np.sin(al) * np.cos(al)) * np.exp(-al ** 2 * c * t / a ** 2)
+    return 2 * F * B * (1 + nu_u) / (3 * a) * ((np.cos(np.outer(x, al) / a) - np.cos(al)) @ coef)

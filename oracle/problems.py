@@ -12,6 +12,16 @@ printed source g carries a sign error in its first term (it must be symmetric
 under x <-> y because the solution is). Reading A3: both sources are derived
 here from the PDE (biotsys1)-(biotsys2) for the stated solution.
 
+Mandel's problem (Sec. 4.3, reading A19): the quarter domain [0, a] x [0, b] under a rigid,
+frictionless plate pressed down with the total force F (the quarter's share); x = a drained and
+traction-free (p = 0), x = 0 and y = 0 symmetry planes (u_x = 0, resp. u_y = 0, no flux), the
+top impervious with its vertical displacement constant along x. The constraint is imposed by
+a penalty: k_p (u_y(i+1) - u_y(i))^2 / 2 for consecutive top nodes with k_p = 1e6 (lambda + 2 mu),
+and the force as the uniform traction (0, -F / a) on the top (under the constraint only its
+total matters). Initial state: the undrained response printed in Sec. 4.3, p0 = F B (1 + nu_u)
+/ (3 a), u = (F nu_u x / (2 G a), -F (1 - nu_u) y / (2 G a)), with Skempton's B = 1 (alpha = 1
+and no storage: incompressible constituents) and nu_u = (3 nu + B (1 - 2 nu)) / (3 - B (1 - 2 nu)).
+
 Barry & Mercer's problem (Sec. 4.2): the domain [0, a] x [0, b] is drained on every side
 (p = 0) with zero tangential displacement there (u_y = 0 on x = 0, a; u_x = 0 on y = 0, b;
 the normal component is left free, traction-free in the normal direction: reading A14), a
@@ -131,14 +141,46 @@ def dirichlet_dofs(case):
     elif case.problem == "mms":
         nodes = np.unique(np.concatenate(list(sides.values())))
         d = [3 * nodes, 3 * nodes + 1, 3 * nodes + 2]
+    elif case.problem == "mandel":
+        d = [3 * sides["left"], 3 * sides["bottom"] + 1, 3 * sides["right"] + 2]
     else:
         raise ValueError(case.problem)
     return np.unique(np.concatenate(d))
 
 
+MANDEL_PENALTY = 1e6   # k_p / (lambda + 2 mu) of the rigid-plate constraint
+
+
+def mandel_undrained(case):
+    """(B, nu_u, G, p0) of Mandel's undrained response (Sec. 4.3) for alpha = 1, no storage."""
+    lam, mu = lame(case.E, case.nu)
+    B = 1.0
+    nu_u = (3 * case.nu + B * (1 - 2 * case.nu)) / (3 - B * (1 - 2 * case.nu))
+    p0 = case.load * B * (1 + nu_u) / (3 * case.Lx)
+    return B, nu_u, mu, p0
+
+
+def mandel_plate_penalty(case):
+    """Sparse n_dof x n_dof matrix of the rigid-plate penalty: for consecutive top nodes i, i+1,
+    k_p [[1, -1], [-1, 1]] on their u_y DOFs (the pairs are mesh neighbours, so the pattern of AA
+    already holds every entry)."""
+    import scipy.sparse as sp
+    lam, mu = lame(case.E, case.nu)
+    kp = MANDEL_PENALTY * (lam + 2 * mu)
+    top = boundary_nodes(case.n)["top"]
+    rows, cols, vals = [], [], []
+    for a, b in zip(top[:-1], top[1:]):
+        ia, ib = 3 * a + 1, 3 * b + 1
+        rows += [ia, ia, ib, ib]
+        cols += [ia, ib, ia, ib]
+        vals += [kp, -kp, -kp, kp]
+    nd = 3 * (case.n + 1) ** 2
+    return sp.csr_matrix((vals, (rows, cols)), shape=(nd, nd))
+
+
 def dirichlet_values(case, coords, dofs, t):
     """Prescribed values g_D(t) at the constrained DOFs."""
-    if case.problem in ("terzaghi", "barry_mercer"):
+    if case.problem in ("terzaghi", "barry_mercer", "mandel"):
         return np.zeros(dofs.shape[0])
     node, field = dofs // 3, dofs % 3
     u1, u2, p = mms_exact(coords[node, 0], coords[node, 1], t)
@@ -151,6 +193,12 @@ def initial_state(case, coords):
     if case.problem == "mms":
         u1, u2, p = mms_exact(coords[:, 0], coords[:, 1], 0.0)
         x0[0::3], x0[1::3], x0[2::3] = u1, u2, p
+    elif case.problem == "mandel":
+        B, nu_u, G, p0 = mandel_undrained(case)
+        F, a = case.load, case.Lx
+        x0[0::3] = F * nu_u * coords[:, 0] / (2 * G * a)
+        x0[1::3] = -F * (1 - nu_u) * coords[:, 1] / (2 * G * a)
+        x0[2::3] = p0
     return x0
 
 
@@ -160,6 +208,8 @@ def load_vector(case, coords, tris, t):
     out = np.zeros(3 * nn)
     if case.problem == "terzaghi":
         out[1::3] += top_traction_y(case.n, coords, -case.load)
+    elif case.problem == "mandel":
+        out[1::3] += top_traction_y(case.n, coords, -case.load / case.Lx)
     elif case.problem == "barry_mercer":
         nodes, w = point_source_weights(case.n, case.Lx, case.Ly, case.Lx / 4.0, case.Ly / 4.0)
         g = -0.5 * case.load * np.sin(barry_mercer_beta(case) * t)

@@ -15,7 +15,7 @@ import scipy.sparse as sp
 
 from .mesh import structured_mesh
 from .fem import assemble, stabilisation_beta
-from .problems import dirichlet_dofs, dirichlet_values, initial_state, load_vector
+from .problems import dirichlet_dofs, dirichlet_values, initial_state, load_vector, mandel_plate_penalty
 
 
 @dataclass
@@ -73,6 +73,9 @@ def build_system(case, beta=None) -> BiotSystem:
         beta = stabilisation_beta(case.E, case.nu, h, case.beta_mode)
     AA_full, Ap_full = assemble(coords, tris, case.E, case.nu, case.alpha,
                                 case.kappa_elem(), case.tau, beta)
+    if case.problem == "mandel":  # the rigid plate (reading A19): a penalty on the top row's u_y
+        AA_full = (AA_full + mandel_plate_penalty(case)).tocsr()
+        AA_full.sort_indices()
     n_dof = AA_full.shape[0]
     D = dirichlet_dofs(case)
     sign = np.where(D % 3 == 2, -1.0, 1.0)

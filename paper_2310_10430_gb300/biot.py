@@ -21,7 +21,7 @@ STATUS_NAMES = ["BIOT_OK", "BIOT_E_INVALID", "BIOT_E_OOM", "BIOT_E_CUDA", "BIOT_
                 "BIOT_E_NOT_CONVERGED", "BIOT_E_DIVERGED", "BIOT_E_TIMEOUT"]
 BIOT_PRECOND_TRI, BIOT_PRECOND_DIAG = 1, 2
 BIOT_FP64, BIOT_FP32, BIOT_BF16VAL_FP32ACC = 0, 1, 2
-BIOT_TERZAGHI, BIOT_MMS_TRIG, BIOT_BARRY_MERCER = 0, 1, 2
+BIOT_TERZAGHI, BIOT_MMS_TRIG, BIOT_BARRY_MERCER, BIOT_MANDEL = 0, 1, 2, 3
 BIOT_BETA_H2, BIOT_BETA_H, BIOT_BETA_NONE = 0, 1, 2
 BIOT_SCHED_TOL, BIOT_SCHED_PAPER, BIOT_SCHED_EAGER = 0, 1, 2
 BIOT_INNER_EXACT, BIOT_INNER_GMG = 0, 1
@@ -340,7 +340,8 @@ def biot_destroy(ctx):
 
 # ---- convenience: a context built from a workload description ---------------
 
-_PROBLEMS = {"terzaghi": BIOT_TERZAGHI, "mms": BIOT_MMS_TRIG, "barry_mercer": BIOT_BARRY_MERCER}
+_PROBLEMS = {"terzaghi": BIOT_TERZAGHI, "mms": BIOT_MMS_TRIG, "barry_mercer": BIOT_BARRY_MERCER,
+             "mandel": BIOT_MANDEL}
 _BETA = {"h2": BIOT_BETA_H2, "h": BIOT_BETA_H, "none": BIOT_BETA_NONE}
 _PRECOND = {"tri": BIOT_PRECOND_TRI, "diag": BIOT_PRECOND_DIAG}
 _PRECISION = {"fp64": BIOT_FP64, "fp32": BIOT_FP32, "bf16": BIOT_BF16VAL_FP32ACC}

@@ -543,7 +543,8 @@ biot_status biot_assemble(biot_ctx* ctx, const biot_params* p) {
     return fail(ctx, BIOT_E_INVALID, "material or time step out of range");
   if (p->n_t < 1 || p->n_iter < 1 || p->n_iter > kMaxIter)
     return fail(ctx, BIOT_E_INVALID, "n_t >= 1 and 1 <= n_iter <= %d required", kMaxIter);
-  if (p->problem != BIOT_TERZAGHI && p->problem != BIOT_MMS_TRIG && p->problem != BIOT_BARRY_MERCER)
+  if (p->problem != BIOT_TERZAGHI && p->problem != BIOT_MMS_TRIG && p->problem != BIOT_BARRY_MERCER &&
+      p->problem != BIOT_MANDEL)
     return fail(ctx, BIOT_E_INVALID, "problem");
   if (p->beta_mode < BIOT_BETA_H2 || p->beta_mode > BIOT_BETA_NONE) return fail(ctx, BIOT_E_INVALID, "beta_mode");
   if (p->schedule != BIOT_SCHED_TOL && p->schedule != BIOT_SCHED_PAPER && p->schedule != BIOT_SCHED_EAGER)

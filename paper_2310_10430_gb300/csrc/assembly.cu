@@ -174,7 +174,7 @@ __global__ void k_assemble(int n, double hx, double hy, int colour, Material m, 
   }
 }
 
-// Dirichlet DOFs of the three boundary-condition families.
+// Dirichlet DOFs of the four boundary-condition families.
 __global__ void k_dirichlet_mask(int n, int problem, uint8_t* __restrict__ dmask) {
   const int nn = (n + 1) * (n + 1);
   int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -189,6 +189,10 @@ __global__ void k_dirichlet_mask(int n, int problem, uint8_t* __restrict__ dmask
     m0 = (j == 0 || j == n) ? 1 : 0;    // tangential u_x on the horizontal sides
     m1 = (i == 0 || i == n) ? 1 : 0;    // tangential u_y on the vertical sides
     m2 = (i == 0 || i == n || j == 0 || j == n) ? 1 : 0;  // drained everywhere
+  } else if (problem == BIOT_MANDEL) {
+    m0 = i == 0 ? 1 : 0;                // symmetry plane x = 0
+    m1 = j == 0 ? 1 : 0;                // symmetry plane y = 0
+    m2 = i == n ? 1 : 0;                // drained x = a
   } else {
     const bool bnd = (i == 0 || i == n || j == 0 || j == n);
     m0 = m1 = m2 = bnd ? 1 : 0;
@@ -309,7 +313,7 @@ __global__ void k_rhs(int n, int n_dof, int n_t, int ldx, int problem, double hx
   const int nx = n + 1, v = r / 3, f = r % 3, i = v % nx, j = v / nx;
   double* Fr = F + (size_t)r * ldx;
   Fr[0] = 0.0;
-  if (problem == BIOT_TERZAGHI) {
+  if (problem == BIOT_TERZAGHI || problem == BIOT_MANDEL) {  // `load`: the top traction's magnitude
     double val = 0.0;
     if (f == 1 && j == n && !dmask[r]) val = -load * 0.5 * hx * ((i > 0 ? 1.0 : 0.0) + (i < n ? 1.0 : 0.0));
     for (int k = 1; k <= n_t; ++k) Fr[k] = val;  // Dirichlet data are zero
@@ -335,8 +339,13 @@ __global__ void k_rhs(int n, int n_dof, int n_t, int ldx, int problem, double hx
   }
 }
 
+// Mandel's undrained initial state (Sec. 4.3): u = (ux_x x, uy_y y), p = p0.
+struct Undrained {
+  double ux_x, uy_y, p0;
+};
+
 // Initial state x0 (column 0) and the zero initial guess X^{n,0} = 0 (Alg. 3).
-__global__ void k_init_state(int n, int n_dof, int n_t, int ldx, int problem, double hx, double hy,
+__global__ void k_init_state(int n, int n_dof, int n_t, int ldx, int problem, double hx, double hy, Undrained ud,
                              double* __restrict__ X) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_dof) return;
@@ -345,9 +354,33 @@ __global__ void k_init_state(int n, int n_dof, int n_t, int ldx, int problem, do
   if (problem == BIOT_MMS_TRIG) {
     const int nx = n + 1, v = r / 3;
     x0 = mms_phi((double)(v % nx) * hx, (double)(v / nx) * hy);
+  } else if (problem == BIOT_MANDEL) {
+    const int nx = n + 1, v = r / 3, f = r % 3;
+    x0 = f == 0 ? ud.ux_x * ((double)(v % nx) * hx) : f == 1 ? ud.uy_y * ((double)(v / nx) * hy) : ud.p0;
   }
   Xr[0] = x0;
   for (int k = 1; k < ldx; ++k) Xr[k] = 0.0;
+}
+
+// Mandel's rigid plate (reading of Sec. 4.3): the penalty kp (u_y(i+1) - u_y(i))^2 / 2 over
+// consecutive top nodes, added to the u_y row of every top node (one thread per node: its
+// diagonal gets kp per top neighbour, each top neighbour's entry -kp; no two threads share a row).
+__global__ void k_mandel_penalty(int n, double kp, const int32_t* __restrict__ nodeptr,
+                                 const int32_t* __restrict__ nbr, const int32_t* __restrict__ rowptr,
+                                 double* __restrict__ val) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  const int v = n * (n + 1) + i;
+  const int32_t np = nodeptr[v];
+  const int deg = nodeptr[v + 1] - np;
+  const int32_t r1 = rowptr[3 * v] + 3 * deg;  // the u_y row of node v
+  for (int k = 0; k < deg; ++k) {
+    const int m = nbr[np + k];
+    double add = 0.0;
+    if (m == v) add = kp * ((i > 0 ? 1.0 : 0.0) + (i < n ? 1.0 : 0.0));
+    else if ((m == v - 1 && i > 0) || (m == v + 1 && i < n)) add = -kp;
+    val[r1 + 3 * k + 1] += add;
+  }
 }
 
 // Symmetric elimination: zero Dirichlet rows and columns (pattern kept), diagonal
@@ -401,6 +434,9 @@ biot_status build_pattern(biot_ctx* ctx) {
   return BIOT_OK;
 }
 
+// k_p / (lambda + 2 mu) of Mandel's rigid-plate penalty (reading of Sec. 4.3)
+constexpr double kMandelPenalty = 1e6;
+
 biot_status assemble_system(biot_ctx* ctx) {
   const biot_params& p = ctx->prm;
   const int n = ctx->n, nn = ctx->n_nodes, nd = ctx->n_dof;
@@ -423,6 +459,20 @@ biot_status assemble_system(biot_ctx* ctx) {
     BIOT_LAUNCH(k_assemble, div_up(cells_per_colour, 128), 128, 0, s, n, hx, hy, colour, m, ctx->kappa, ctx->nodeptr,
                 ctx->nbr, ctx->rowptr, ctx->val, ctx->apval);
   BIOT_LAUNCH(k_dirichlet_mask, div_up(nn, 256), 256, 0, s, n, p.problem, ctx->dmask);
+  Undrained ud{0.0, 0.0, 0.0};
+  double tload = p.load;
+  if (p.problem == BIOT_MANDEL) {
+    BIOT_LAUNCH(k_mandel_penalty, div_up(n + 1, 128), 128, 0, s, n, kMandelPenalty * (lam + 2.0 * mu), ctx->nodeptr,
+                ctx->nbr, ctx->rowptr, ctx->val);
+    // Skempton B = 1 (alpha = 1, no storage), nu_u = (3 nu + B (1 - 2 nu)) / (3 - B (1 - 2 nu)); the
+    // force F = load on the quarter's top as the traction F / a
+    const double B = 1.0, nu = p.nu, a = ctx->Lx;
+    const double nu_u = (3.0 * nu + B * (1.0 - 2.0 * nu)) / (3.0 - B * (1.0 - 2.0 * nu));
+    ud.ux_x = p.load * nu_u / (2.0 * mu * a);
+    ud.uy_y = -p.load * (1.0 - nu_u) / (2.0 * mu * a);
+    ud.p0 = p.load * B * (1.0 + nu_u) / (3.0 * a);
+    tload = p.load / a;
+  }
 
   // right-hand sides (needs the matrices before elimination for the lifting)
   double *su = nullptr, *sg = nullptr, *lift = nullptr, *tt = nullptr;
@@ -460,9 +510,9 @@ biot_status assemble_system(biot_ctx* ctx) {
     BIOT_LAUNCH(k_lifting, div_up(nd, 256), 256, 0, s, n, nd, hx, hy, ctx->rowptr, ctx->col, ctx->val, ctx->nodeptr,
                 ctx->apval, ctx->dmask, lift, lift + nd);
   }
-  BIOT_LAUNCH(k_rhs, div_up(nd, 128), 128, 0, s, n, nd, p.n_t, ctx->ldx, p.problem, hx, hy, p.tau, p.load, ctx->dmask,
+  BIOT_LAUNCH(k_rhs, div_up(nd, 128), 128, 0, s, n, nd, p.n_t, ctx->ldx, p.problem, hx, hy, p.tau, tload, ctx->dmask,
               su, sg, sg + nn, lift, lift + nd, tt, tt + p.n_t + 1, ps, ctx->F);
-  BIOT_LAUNCH(k_init_state, div_up(nd, 128), 128, 0, s, n, nd, p.n_t, ctx->ldx, p.problem, hx, hy, ctx->X);
+  BIOT_LAUNCH(k_init_state, div_up(nd, 128), 128, 0, s, n, nd, p.n_t, ctx->ldx, p.problem, hx, hy, ud, ctx->X);
   BIOT_LAUNCH(k_eliminate, div_up(nd, 256), 256, 0, s, nd, ctx->rowptr, ctx->col, ctx->nodeptr, ctx->nbr, ctx->dmask,
               ctx->val, ctx->apval);
   BIOT_LAUNCH(k_dscale, div_up(nd, 256), 256, 0, s, nd, ctx->rowptr, ctx->col, ctx->val, ctx->dsc, ctx->dsq);

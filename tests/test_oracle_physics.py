@@ -19,7 +19,7 @@ import workloads as W
 from oracle.analytic import QUAD7_BARY, QUAD7_W, l2_error_p1, terzaghi
 from oracle.fem import lame
 from oracle.problems import mms_exact, mms_f_as_printed, mms_sources
-from oracle.solvers import seq_solve
+from oracle.solvers import field_rel_errors, seq_solve
 from oracle.system import build_system
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -210,3 +210,87 @@ def test_barry_mercer_beta_against_hand_worked_value():
     assert barry_mercer_beta(case) == pytest.approx(g["beta"], rel=1e-14)
     assert barry_mercer_beta(case.with_(Lx=2.0, Ly=0.5)) == pytest.approx(g["beta"], rel=1e-14)
     assert barry_mercer_beta(case.with_(Lx=2.0, Ly=2.0)) == pytest.approx(g["beta"] / 4.0, rel=1e-14)
+
+
+# ---- Mandel's problem (Sec. 4.3) ----
+
+def test_mandel_series_limits_and_mandel_cryer_effect():
+    # the cited analytic series: t -> 0+ gives the undrained pressure printed in Sec. 4.3,
+    # p0 = F B (1 + nu_u) / (3 a) = 0.5 (nu = 0, B = 1, nu_u = 0.5, F = a = 1); the centre
+    # pressure first rises above p0 (the Mandel-Cryer effect the paper describes), then drains
+    from oracle.analytic import mandel_pressure
+    xs = np.array([0.0, 0.25, 0.5, 0.75])
+    p_small = mandel_pressure(xs, 1e-7, 1e4, 0.0, 1e-6, terms=400)
+    np.testing.assert_allclose(p_small, 0.5, rtol=2e-3)
+    centre = [float(mandel_pressure([0.0], t, 1e4, 0.0, 1e-6)[0]) for t in (1.0, 5.0, 10.0, 20.0)]
+    assert all(c > 0.5 for c in centre) and centre[2] > centre[0]
+    assert abs(float(mandel_pressure([0.0], 500.0, 1e4, 0.0, 1e-6)[0])) < 1e-3
+    assert abs(float(mandel_pressure([1.0], 3.0, 1e4, 0.0, 1e-6)[0])) < 1e-12   # drained edge
+
+
+def test_mandel_discrete_pressure_matches_the_series():
+    # the paper's setting h = 1/32, tau = 0.025: the oracle's backward Euler with the penalty
+    # plate and the printed undrained initial state against the series, at t = 1, 5, 10
+    from oracle.analytic import mandel_pressure
+    errs = {}
+    for n in (16, 32):
+        case = W.mandel(n, 400, 0.025)
+        X = seq_solve(build_system(case))
+        P = X[:, 2::3].reshape(-1, n + 1, n + 1)
+        xs = np.linspace(0.0, 1.0, n + 1)
+        for k in (40, 200, 400):
+            pa = mandel_pressure(xs, k * 0.025, case.E, case.nu, 1e-6)
+            errs[(n, k)] = np.abs(P[k, n // 2, :] - pa).max() / 0.5   # p does not depend on y
+    assert errs[(32, 40)] < 0.02 and errs[(32, 200)] < 0.005 and errs[(32, 400)] < 0.003, errs
+    assert errs[(16, 40)] > 2.0 * errs[(32, 40)], errs   # converges under refinement
+
+
+def test_mandel_penalty_plate_approximates_the_rigid_constraint():
+    # exact constraint by master-slave elimination: every top u_y equals one unknown U, whose test
+    # function is 1 on the whole top (so the force enters as the sum of the top loads); the
+    # penalty k_p = 1e6 (lambda + 2 mu) must agree to about 1 / 1e6
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    from oracle.fem import assemble, stabilisation_beta
+    from oracle.mesh import boundary_nodes, structured_mesh
+    from oracle.problems import mandel_plate_penalty
+    from oracle.system import eliminate
+    case = W.mandel(8, 6, 0.5)
+    s = build_system(case)
+    Xp = seq_solve(s)
+    AA = (s.AA - eliminate(mandel_plate_penalty(case), s.dir_dofs, None)).tocsr()   # without the penalty
+    nd = s.n_dof
+    top_uy = 3 * boundary_nodes(case.n)["top"] + 1
+    keep = np.setdiff1d(np.arange(nd), top_uy)
+    T = sp.lil_matrix((nd, keep.size + 1))
+    T[keep, np.arange(keep.size)] = 1.0
+    T[top_uy, keep.size] = 1.0
+    T = T.tocsr()
+    K = (T.T @ AA @ T).tocsc()
+    lu = spla.splu(K)
+    X = np.zeros_like(Xp)
+    X[0] = s.x0
+    for k in range(1, s.F.shape[0]):
+        X[k] = T @ lu.solve(T.T @ (s.Ap @ X[k - 1] + s.F[k]))
+    eu, ep = field_rel_errors(Xp, X)
+    assert eu < 1e-5 and ep < 1e-5, (eu, ep)
+    assert np.ptp(X[-1, top_uy]) == 0.0 and np.ptp(Xp[-1, top_uy]) < 1e-5 * np.abs(Xp[-1, top_uy]).max()
+
+
+def test_mandel_initial_state_is_the_undrained_response():
+    # a very short first step leaves the printed undrained state (Sec. 4.3; u_y = -F (1 - nu_u)
+    # y / (2 G a), reading A19) unchanged up to the drained column at x = a, whose effect is
+    # O(h): the change of the displacements halves with h, that of the pressure shrinks, so the
+    # printed state is the h -> 0 limit of the discrete undrained response
+    du, dv, dp = [], [], []
+    for n in (16, 32, 64):
+        case = W.mandel(n, 1, 1e-6)
+        s = build_system(case)
+        X = seq_solve(s)
+        U0, V0 = s.x0[0::3], s.x0[1::3]
+        du.append(np.abs(X[1, 0::3] - U0).max() / np.abs(U0).max())
+        dv.append(np.abs(X[1, 1::3] - V0).max() / np.abs(V0).max())
+        dp.append(np.abs(X[1, 2::3].reshape(n + 1, n + 1)[:, : n - 3] - 0.5).max())
+    for d in (du, dv):
+        assert d[0] < 0.03 and all(1.7 < d[k] / d[k + 1] < 2.3 for k in range(2)), d
+    assert dp[0] < 0.01 and dp[0] > dp[1] > dp[2], dp

@@ -24,6 +24,7 @@ import numpy as np
 TERZAGHI = "terzaghi"
 MMS = "mms"
 BARRY_MERCER = "barry_mercer"
+MANDEL = "mandel"
 
 
 @dataclass(frozen=True)
@@ -171,3 +172,10 @@ def large_1024() -> BiotCase:
     k = lognormal_kappa(1024, -6.0, 2.0, 0.1, 4321)
     return BiotCase(n=1024, E=1e4, nu=0.49, alpha=1.0, kappa=k, tau=1e-3, n_t=128,
                     problem=TERZAGHI, precond="tri", tol=1e-8, name="large_1024x1024_nt128")
+
+
+def mandel(n: int = 32, n_t: int = 40, tau: float = 0.025) -> BiotCase:
+    """Mandel's problem (Sec. 4.3): quarter domain a = b = 1, K = 1e-6, E = 1e4, nu = 0, B = 1
+    (alpha = 1, no storage), F = 1, P1, tol 1e-7; the paper's plot uses h = 1/32, tau = 0.025."""
+    return BiotCase(n=n, E=1e4, nu=0.0, alpha=1.0, kappa=1e-6, tau=tau, n_t=n_t, problem=MANDEL,
+                    precond="tri", tol=1e-7, load=1.0, name=f"mandel_{n}x{n}_nt{n_t}")
