@@ -354,6 +354,9 @@ typedef struct {
   int32_t strips;                       /* substructured block solves: strips (0: plain band) */
   int32_t variant_sep_u, variant_sep_p; /* substructured: separator variants (variant_*: interiors) */
   double ms_sep_u, ms_sep_p;            /* substructured: the separator pair's part of ms_u, ms_p */
+  int32_t spmm_variant;                 /* reduced precision: SpMM shape (0: 16-byte vectors, unroll 4,
+                                           2 CTAs per SM, 2 x 152 CTAs; others vary them) */
+  double ms_spmm, ms_spmm_default;      /* one SpMM at full window: chosen shape, default shape */
 } biot_tuning;
 
 /* Pick the band triangular-solve kernel variant (register-streamed; TMA-staged
@@ -372,7 +375,12 @@ typedef struct {
  * block products (variant 100), keeps the fastest, caches the choices under keys
  * "sub:" + precision, rows, half-band and window, and reports the interior variants,
  * the separator variants, the interior + separator pair times (ms_u, ms_p), their
- * separator parts (ms_sep_u, ms_sep_p) and the strip count. */
+ * separator parts (ms_sep_u, ms_sep_p) and the strip count. In the reduced-precision
+ * modes it also times the SpMM w = D^{-1/2} AA z in each of its shapes (16- or 8-byte
+ * vectors per lane, i.e. 4 or 2 columns; neighbour-loop unrolling 1, 2 or 4; registers
+ * for 2 to 4 CTAs per SM; grids of 2 to 4 x 152 CTAs) at full window width and keeps
+ * the fastest (cache key "spmm:" + precision, rows and window); with multigrid block
+ * solves only the SpMM is tuned. */
 biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out);
 
 /* Failure-detection test hook. Every bulk copy of band rows into shared memory is

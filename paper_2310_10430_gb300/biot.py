@@ -59,6 +59,7 @@ class BiotTuning(ctypes.Structure):
         ("from_cache", ctypes.c_int32), ("strips", ctypes.c_int32),
         ("variant_sep_u", ctypes.c_int32), ("variant_sep_p", ctypes.c_int32),
         ("ms_sep_u", ctypes.c_double), ("ms_sep_p", ctypes.c_double),
+        ("spmm_variant", ctypes.c_int32), ("ms_spmm", ctypes.c_double), ("ms_spmm_default", ctypes.c_double),
     ]
 
     def as_dict(self):

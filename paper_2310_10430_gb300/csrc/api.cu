@@ -827,10 +827,22 @@ biot_status biot_timing_read(biot_ctx* ctx, int32_t kc, double* total_ms, int64_
 biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out) {
   if (bad_ctx(ctx)) return fail(nullptr, BIOT_E_INVALID, "ctx is NULL");
   BIOT_TRY(need_precond(ctx));
-  if (ctx->gmg) {  // multigrid block solves: no band-solve variants to choose
-    if (out) *out = biot_tuning{};
+  // the SpMM shape (reduced-precision sweeps), for every kind of block solve
+  std::map<std::string, int> cache = read_tune_cache(cache_path);
+  int sp_hit = 0;
+  double sp_ms = 0.0, sp_def = 0.0;
+  BIOT_TRY(spmm_tune(ctx, &cache, &sp_hit, &sp_ms, &sp_def));
+  const bool sp_cached = sp_hit || !low_precision(ctx);
+  auto finish = [&](biot_tuning res, bool hits) -> biot_status {
+    res.spmm_variant = ctx->spmm_var;
+    res.ms_spmm = sp_ms;
+    res.ms_spmm_default = sp_def;
+    res.from_cache = (hits && sp_cached) ? 1 : 0;
+    if (!res.from_cache) write_tune_cache(cache_path, cache);
+    if (out) *out = res;
     return BIOT_OK;
-  }
+  };
+  if (ctx->gmg) return finish(biot_tuning{}, true);  // multigrid block solves: no band-solve variants
   const bool fp64 = !low_precision(ctx);
   const int pi = fp64 ? 0 : 1;
   const int nc = ctx->wcap;
@@ -842,12 +854,9 @@ biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out) {
     // substructured block solves: time the interior and separator variants of A and S (or
     // take them from the cache, keyed "sub:" + precision, rows, half-band and window)
     double ms[2] = {0.0, 0.0}, ms_sep[2] = {0.0, 0.0};
-    std::map<std::string, int> cache = read_tune_cache(cache_path);
     int hits = 0;
     BIOT_TRY(sub_tune(ctx, ms, ms_sep, &cache, &hits));
     BIOT_TRY(device_status(ctx));
-    res.from_cache = hits == 4 ? 1 : 0;
-    if (!res.from_cache) write_tune_cache(cache_path, cache);
     const SubBlock* su = ctx->sub[0];
     const SubBlock* sp = ctx->sub[1];
     res.ms_u = ms[0];
@@ -865,10 +874,8 @@ biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out) {
     res.variant_sep_p = sp->varS[pi];
     res.ms_sep_u = ms_sep[0];
     res.ms_sep_p = ms_sep[1];
-    if (out) *out = res;
-    return BIOT_OK;
+    return finish(res, hits == 4);
   }
-  std::map<std::string, int> cache = read_tune_cache(cache_path);
   const int def_u = band_variant_default(fp64, bu), def_p = band_variant_default(fp64, bp);
   // clean inputs for the timing runs
   const size_t es = fp64 ? 8 : 4;
@@ -914,16 +921,13 @@ biot_status biot_tune(biot_ctx* ctx, const char* cache_path, biot_tuning* out) {
     }
   }
   BIOT_TRY(device_status(ctx));
-  res.from_cache = (hit_u && hit_p) ? 1 : 0;
   res.tma_u = kBandVariants[res.variant_u].tma;
   res.nb_u = kBandVariants[res.variant_u].nb;
   res.threads_u = kBandVariants[res.variant_u].threads;
   res.tma_p = kBandVariants[res.variant_p].tma;
   res.nb_p = kBandVariants[res.variant_p].nb;
   res.threads_p = kBandVariants[res.variant_p].threads;
-  if (!res.from_cache) write_tune_cache(cache_path, cache);
-  if (out) *out = res;
-  return BIOT_OK;
+  return finish(res, hit_u && hit_p);
 }
 
 int64_t biot_launch_count(void) { return g_launches.load(); }

@@ -201,6 +201,7 @@ struct biot_ctx {
   biot::LowPrec lp;             // reduced-precision sweep buffers (BIOT_FP32 / BIOT_BF16VAL_FP32ACC)
   int band_var_u[2] = {0, 0};   // band-solve variant for A, [FP64, FP32] (kBandVariants index)
   int band_var_p[2] = {0, 0};   // same for S
+  int spmm_var = 0;             // tuned shape of the FP32 / BF16-value SpMM (spmm.cu)
   void* dnb_u[2] = {nullptr, nullptr};  // compact NB x NB diagonal-block inverses of A, [FP64, FP32]
   void* dnb_p[2] = {nullptr, nullptr};  // same for S
   int dnb_nb_u[2] = {0, 0};     // NB they were built for (0: none)
@@ -301,6 +302,10 @@ void launch_residual_raw(int n_nodes, const int32_t* nodeptr, const int32_t* nbr
 void launch_residual_lp(biot_ctx* ctx, int lo, int ncols);
 // w = d .* (AA z) for columns [c0, c0 + ncols); partial |w|^2 into slot 0.
 template <typename T> void launch_spmm_scaled(biot_ctx* ctx, const T* z, T* w, int c0, int ncols);
+// Norm partials per column the SpMM writes (its grid), and the SpMM shape tuner.
+int spmm_blocks(const biot_ctx* ctx);
+biot_status spmm_tune(biot_ctx* ctx, std::map<std::string, int>* cache, int* hit, double* ms_best,
+                      double* ms_default);
 // t_p[v][c] = sum_m B^T[v][m] z_u[m][c] - v_p[v][c]/d (P1 coupling).
 template <typename T> void launch_coupling(biot_ctx* ctx, const T* z, const T* vin, T* tp, int c0, int ncols);
 

@@ -647,7 +647,7 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
     T* Zj = Z + j * vs;
     precond_apply<T>(ctx, Vj, Zj, c0, ncols);
     launch_spmm_scaled<T>(ctx, Zj, Wv, c0, ncols);
-    reduce_partials(ctx, 1, ncols, cs + CS_WN0 * ld, ld, c0);
+    reduce_partials(ctx, 1, ncols, cs + CS_WN0 * ld, ld, c0, spmm_blocks(ctx));
     for (int pass = 0; pass < 2; ++pass) {
       double* h = pass == 0 ? h1 : h2;
       dots(V, j + 1, Wv);

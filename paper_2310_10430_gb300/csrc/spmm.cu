@@ -15,6 +15,9 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <cstdio>
+#include <map>
+#include <string>
 
 namespace biot {
 
@@ -171,20 +174,33 @@ template <> struct Vec16<double> {
   __device__ __forceinline__ static V make(const double* o) { return make_double2(o[0], o[1]); }
 };
 
+// VEC-wide vector of XT for the tuned SpMM variants (8 or 16 bytes).
+template <typename T, int N> struct VecN;
+template <> struct VecN<float, 4> : Vec16<float> {};
+template <> struct VecN<double, 2> : Vec16<double> {};
+template <> struct VecN<float, 2> {
+  using V = float2;
+  static constexpr int n = 2;
+  __device__ __forceinline__ static void get(const V& v, float* o) { o[0] = v.x; o[1] = v.y; }
+  __device__ __forceinline__ static V make(const float* o) { return make_float2(o[0], o[1]); }
+};
+
 // spmm_body with 16-byte accesses: a lane owns VEC consecutive columns, so every DOF row
 // of z is read with one 128-bit load per lane and a warp covers 32 * VEC columns per
 // pass. The column range is widened down to a multiple of VEC; lanes mask what lies
 // outside [c0, c0 + ncols). Needs ld % VEC == 0 and 16-byte aligned z and w. The sums
 // run in the same order as spmm_body, and the per-column norm partials land in the same
 // slots part[block * ld + column].
-template <typename XT, typename VT>
+// VEC (columns per lane) and UNR (neighbour-loop unrolling) are tuned per mesh and window
+// (biot_tune); the default is the 16-byte form with UNR = 4.
+template <typename XT, typename VT, int VEC = Vec16<XT>::n, int UNR = 4>
 __device__ __forceinline__ void spmm_vec_body(int nn, const int32_t* __restrict__ nodeptr,
               const int32_t* __restrict__ nbr, const int32_t* __restrict__ rowptr, const VT* __restrict__ val,
               const double* __restrict__ dsc, const XT* __restrict__ z, XT* __restrict__ w, int ld, int c0,
               int ncols, double* __restrict__ part) {
   using A = typename Acc<XT>::T;
-  using V = typename Vec16<XT>::V;
-  constexpr int VEC = Vec16<XT>::n;
+  using VN = VecN<XT, VEC>;
+  using V = typename VN::V;
   __shared__ double sm[kWarps][32 * VEC];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per = (nn + gridDim.x - 1) / gridDim.x;
@@ -205,14 +221,14 @@ __device__ __forceinline__ void spmm_vec_body(int nn, const int32_t* __restrict_
       A a0[VEC], a1[VEC], a2[VEC];
 #pragma unroll
       for (int q = 0; q < VEC; ++q) a0[q] = a1[q] = a2[q] = 0;
-#pragma unroll 4
+#pragma unroll UNR
       for (int k = 0; k < deg; ++k) {
         const int m = nbr[np + k];
         const XT* zm = z + (size_t)(3 * m) * ld + cc;
         XT x0[VEC], x1[VEC], x2[VEC];
-        Vec16<XT>::get(*reinterpret_cast<const V*>(zm), x0);
-        Vec16<XT>::get(*reinterpret_cast<const V*>(zm + ld), x1);
-        Vec16<XT>::get(*reinterpret_cast<const V*>(zm + 2 * ld), x2);
+        VN::get(*reinterpret_cast<const V*>(zm), x0);
+        VN::get(*reinterpret_cast<const V*>(zm + ld), x1);
+        VN::get(*reinterpret_cast<const V*>(zm + 2 * ld), x2);
         const VT* e0 = val + r0 + 3 * k;
         const VT* e1 = val + r1 + 3 * k;
         const VT* e2 = val + r2 + 3 * k;
@@ -239,9 +255,9 @@ __device__ __forceinline__ void spmm_vec_body(int nn, const int32_t* __restrict_
       }
       XT* w0 = w + (size_t)(3 * v) * ld + c;
       if (full) {
-        *reinterpret_cast<V*>(w0) = Vec16<XT>::make(o0);
-        *reinterpret_cast<V*>(w0 + ld) = Vec16<XT>::make(o1);
-        *reinterpret_cast<V*>(w0 + 2 * ld) = Vec16<XT>::make(o2);
+        *reinterpret_cast<V*>(w0) = VN::make(o0);
+        *reinterpret_cast<V*>(w0 + ld) = VN::make(o1);
+        *reinterpret_cast<V*>(w0 + 2 * ld) = VN::make(o2);
       } else if (any) {
 #pragma unroll
         for (int q = 0; q < VEC; ++q)
@@ -265,12 +281,12 @@ __device__ __forceinline__ void spmm_vec_body(int nn, const int32_t* __restrict_
   }
 }
 
-template <typename XT, typename VT>
-__global__ void __launch_bounds__(kWarps * 32, 2)
+template <typename XT, typename VT, int VEC = Vec16<XT>::n, int UNR = 4, int MINB = 2>
+__global__ void __launch_bounds__(kWarps * 32, MINB)
 k_spmm_vec(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
            const int32_t* __restrict__ rowptr, const VT* __restrict__ val, const double* __restrict__ dsc,
            const XT* __restrict__ z, XT* __restrict__ w, int ld, int c0, int ncols, double* __restrict__ part) {
-  spmm_vec_body<XT, VT>(nn, nodeptr, nbr, rowptr, val, dsc, z, w, ld, c0, ncols, part);
+  spmm_vec_body<XT, VT, VEC, UNR>(nn, nodeptr, nbr, rowptr, val, dsc, z, w, ld, c0, ncols, part);
 }
 
 template <typename XT, typename VT>
@@ -391,10 +407,59 @@ void launch_spmm_scaled<double>(biot_ctx* ctx, const double* z, double* w, int c
                 ctx->nodeptr, ctx->nbr, ctx->rowptr, ctx->val, ctx->dsc, z, w, ctx->wcap, c0, ncols, ctx->part);
 }
 
+// Tuned shapes of the FP32 / BF16-value SpMM (biot_tune): columns per lane (16- or 8-byte
+// vectors), unrolling of the neighbour loop, CTAs per SM the registers are sized for, and the
+// grid in multiples of the 152 SMs (also the number of norm partials per column).
+struct SpmmVariant {
+  int vec, unr, minb, gmul;
+};
+constexpr SpmmVariant kSpmmVariants[] = {{4, 4, 2, 2}, {4, 2, 3, 3}, {4, 2, 4, 4}, {2, 4, 2, 2}, {2, 2, 4, 4},
+                                         {4, 1, 4, 4}};
+constexpr int kSpmmVariantCount = sizeof(kSpmmVariants) / sizeof(kSpmmVariants[0]);
+
+template <typename VT>
+static void launch_spmm_variant(biot_ctx* ctx, int v, const VT* val, const float* z, float* w, int c0, int ncols) {
+  const int grid = kSpmmVariants[v].gmul * 152;
+#define BIOT_SPMM_CASE(id, VEC, UNR, MINB)                                                                         \
+  case id:                                                                                                          \
+    BIOT_LAUNCH((k_spmm_vec<float, VT, VEC, UNR, MINB>), grid, kWarps * 32, 0, ctx->stream, ctx->n_nodes,          \
+                ctx->nodeptr, ctx->nbr, ctx->rowptr, val, ctx->dsc, z, w, ctx->wcap, c0, ncols, ctx->part);         \
+    break;
+  switch (v) {
+    BIOT_SPMM_CASE(1, 4, 2, 3)
+    BIOT_SPMM_CASE(2, 4, 2, 4)
+    BIOT_SPMM_CASE(3, 2, 4, 2)
+    BIOT_SPMM_CASE(4, 2, 2, 4)
+    BIOT_SPMM_CASE(5, 4, 1, 4)
+    default:
+      BIOT_LAUNCH((k_spmm_vec<float, VT>), grid, kWarps * 32, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr, ctx->nbr,
+                  ctx->rowptr, val, ctx->dsc, z, w, ctx->wcap, c0, ncols, ctx->part);
+  }
+#undef BIOT_SPMM_CASE
+}
+
+static bool spmm_variant_ok(const biot_ctx* ctx, int v, const float* z, const float* w) {
+  const int vec = kSpmmVariants[v].vec;
+  return ctx->wcap % vec == 0 && reinterpret_cast<uintptr_t>(z) % (4 * vec) == 0 &&
+         reinterpret_cast<uintptr_t>(w) % (4 * vec) == 0;
+}
+
+// Blocks (norm partials per column) of the SpMM launch_spmm_scaled issues for this context.
+int spmm_blocks(const biot_ctx* ctx) {
+  if (ctx->prm.precision == BIOT_FP64) return kRedBlocks;
+  return kSpmmVariants[ctx->spmm_var].gmul * 152;
+}
+
 template <>
 void launch_spmm_scaled<float>(biot_ctx* ctx, const float* z, float* w, int c0, int ncols) {
   KTimer tm(ctx, BIOT_KC_SPMM);
   const bool vec = vec_ok<float>(ctx, z, w);
+  const int v = ctx->spmm_var;
+  if (v != 0 && spmm_variant_ok(ctx, v, z, w)) {
+    if (ctx->prm.precision == BIOT_BF16VAL_FP32ACC) launch_spmm_variant(ctx, v, ctx->lp.val_bf16, z, w, c0, ncols);
+    else launch_spmm_variant(ctx, v, ctx->lp.val, z, w, c0, ncols);
+    return;
+  }
   if (ctx->prm.precision == BIOT_BF16VAL_FP32ACC) {
     if (vec)
       BIOT_LAUNCH((k_spmm_vec<float, __nv_bfloat16>), kRedBlocks, kWarps * 32, 0, ctx->stream, ctx->n_nodes,
@@ -441,6 +506,70 @@ void launch_batched_spmm(const InstDev* tab, int count, bool bf16, int j, cudaSt
 
 void launch_batched_coupling(const InstDev* tab, int count, int j, cudaStream_t s) {
   BIOT_LAUNCH(kb_coupling, dim3(256, 1, count), 256, 0, s, tab, j);
+}
+
+// Time every SpMM shape on this context's FP32 (or BF16) values at full window width (w = d .*
+// AA z on the first two Krylov vectors; best of three after a warm-up) and keep the fastest;
+// cached under "spmm:" + precision, rows and window. Returns the chosen and the default times.
+biot_status spmm_tune(biot_ctx* ctx, std::map<std::string, int>* cache, int* hit, double* ms_best,
+                      double* ms_default) {
+  *hit = 0;
+  *ms_best = *ms_default = 0.0;
+  if (ctx->prm.precision == BIOT_FP64) return BIOT_OK;
+  char key[96];
+  snprintf(key, sizeof(key), "spmm:%s:N%d:w%d", ctx->prm.precision == BIOT_FP32 ? "fp32" : "bf16", ctx->n_dof,
+           ctx->wcap);
+  const float* z = ctx->lp.Z;
+  float* w = ctx->lp.Wv;
+  auto time_v = [&](int v) -> double {
+    const int save = ctx->spmm_var;
+    ctx->spmm_var = v;
+    const bool was = ctx->timing;
+    ctx->timing = false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, ctx->stream);
+      launch_spmm_scaled<float>(ctx, z, w, 0, ctx->wcap);
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best = std::min(best, (double)ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->timing = was;
+    ctx->spmm_var = save;
+    return best;
+  };
+  *ms_default = time_v(0);
+  if (cache && cache->count(key)) {
+    const int v = (*cache)[key];
+    if (v >= 0 && v < kSpmmVariantCount && spmm_variant_ok(ctx, v, z, w)) {
+      ctx->spmm_var = v;
+      *hit = 1;
+      *ms_best = time_v(v);
+      return BIOT_OK;
+    }
+  }
+  int best = 0;
+  double tbest = *ms_default;
+  for (int v = 1; v < kSpmmVariantCount; ++v) {
+    if (!spmm_variant_ok(ctx, v, z, w)) continue;
+    const double t = time_v(v);
+    if (t < tbest) {
+      tbest = t;
+      best = v;
+    }
+  }
+  ctx->spmm_var = best;
+  *ms_best = tbest;
+  if (cache) (*cache)[key] = best;
+  BIOT_CU(ctx, cudaGetLastError());
+  return BIOT_OK;
 }
 
 }  // namespace biot

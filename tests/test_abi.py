@@ -49,7 +49,8 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(biot.BiotParams) == 8 * 6 + 4 * 3 + 4 + 8 + 4 * 4
     # ... + inner, gmg_levels (int32) and the two power-method estimates (double)
     assert ctypes.sizeof(biot.BiotInfo) == 4 * 3 + 4 + 8 + 4 * 8 + 8 + 8 + 4 * 2 + 8 * 2
-    assert ctypes.sizeof(biot.BiotTuning) == 4 * 8 + 8 * 4 + 4 * 2 + 4 * 2 + 8 * 2
+    # ... + spmm_variant (int32, padded to 8) and the two SpMM times
+    assert ctypes.sizeof(biot.BiotTuning) == 4 * 8 + 8 * 4 + 4 * 2 + 4 * 2 + 8 * 2 + 8 + 8 * 2
 
 
 def test_invalid_arguments_rejected_on_host(L):

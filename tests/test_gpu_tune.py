@@ -63,3 +63,39 @@ def test_tuning_writes_cache(tmp_path):
     assert 0 <= t.variant_u < N_VARIANTS and t.ms_u <= t.ms_u_default * 1.05 + 1e-3
     txt = open(path).read()
     assert '"variant"' in txt and json.loads(txt)["band_solve_variants"]
+
+
+N_SPMM_VARIANTS = 6
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("variant", range(N_SPMM_VARIANTS))
+def test_each_spmm_shape_gives_the_same_solution(tmp_path, precision, variant):
+    # the SpMM shape (vector width, unrolling, occupancy, grid) changes only the order of the
+    # norm partials: the converged FP32 + refinement solve must still reach backward Euler
+    from oracle.solvers import seq_solve
+    case = W.terzaghi_small().with_(n=20, n_t=12, precond="tri")
+    ref = seq_solve(build_system(case))
+    with biot.Context(case, precision=precision) as c:
+        key = f"spmm:{precision}:N{case.n_dof}:w{c.info.window_cap}"
+        forced = tmp_path / "spmm.json"
+        forced.write_text('{"band_solve_variants": [\n' + f'  {{"key": "{key}", "variant": {variant}}}\n' + "]}\n")
+        t = biot.biot_tune(c.ctx, str(forced))
+        assert t.spmm_variant == variant
+        st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-12, 20000, allow_not_converged=(precision == "bf16"))
+        X = biot.biot_get_state(c.ctx, 0, case.n_t)
+    if rel <= 1e-12:
+        eu, ep = field_rel_errors(X, ref)
+        assert eu < 1e-8 and ep < 1e-8, (variant, eu, ep)
+
+
+def test_spmm_tuner_picks_and_caches(tmp_path):
+    case = W.terzaghi_small().with_(n=48, n_t=64)
+    cache = tmp_path / "tune.json"
+    with biot.Context(case, precision="fp32") as c:
+        t = biot.biot_tune(c.ctx, str(cache))
+        assert 0 <= t.spmm_variant < N_SPMM_VARIANTS and t.ms_spmm <= t.ms_spmm_default * 1.0001
+        entries = json.loads(cache.read_text())["band_solve_variants"]
+        assert any(e["key"].startswith("spmm:fp32:") for e in entries)
+        t2 = biot.biot_tune(c.ctx, str(cache))
+        assert t2.spmm_variant == t.spmm_variant and t2.from_cache == 1
