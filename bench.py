@@ -663,6 +663,8 @@ def run_ours(args):
         extras["efficiency"] = efficiency_study(stream)
     if args.barry_mercer:
         extras["barry_mercer"] = barry_mercer_study(stream)
+    if args.mandel:
+        extras["mandel"] = mandel_study(stream)
     if args.batched_full:
         extras["batched_config4_full"] = batched_config4(stream, full=True)
     out = None
@@ -814,6 +816,7 @@ def time_to_solution(case, stream):
         for n_iter in (10, 30):
             cn = case.with_(n_iter=n_iter)
             with biot.Context(cn, stream=stream, precision=prec, gmg=GMG) as c:
+                biot.biot_tune(c.ctx, None)   # the SpMM shape
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-10, 100000, allow_not_converged=True)
@@ -985,6 +988,55 @@ def barry_mercer_study(stream):
         else:
             row["rel_diff_u"], row["rel_diff_p"] = _field_errors(np, X, ref)
         out[name] = row
+    return out
+
+
+def mandel_study(stream):
+    """Mandel's problem as the paper runs it (Sec. 4.3). (a) The plot's setting: h = 1/32,
+    tau = 0.025, P1, tol 1e-7, to t = 10 (400 steps), parallel in time against step by step
+    (window 1), FP64; the centre pressure at t = 1, 5, 10 (the Mandel-Cryer rise above the
+    undrained 0.5). (b) The table's setting: h = 1/128, tau = 0.1,
+    T = 100 (1000 steps), tol 1e-7, P1 against P2, FP32 sweeps with the FP64 refinement."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2310_10430_gb300 import biot
+    out = {}
+    case = W.mandel(32, 400, 0.025)
+    n = case.n
+    res = {}
+    for label, window in (("pint", 0), ("step_by_step", 1)):
+        with biot.Context(case, stream=stream, window=window) as c:
+            biot.biot_tune(c.ctx, None)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, sweeps, rel = biot.biot_pint_solve(c.ctx, case.tol, 100000, allow_not_converged=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            X = biot.biot_get_state(c.ctx, 0, case.n_t)
+        P = X[:, 2::3].reshape(-1, n + 1, n + 1)
+        res[label] = {"seconds": dt, "sweeps": sweeps, "status": biot.STATUS_NAMES[st], "rel_residual": rel,
+                      "p_centre": {f"t={k * case.tau:g}": float(P[k, 0, 0]) for k in (40, 200, 400)}}
+        res[label]["P"] = P
+    # (the comparison with the analytic series is a test: tests/test_gpu_mandel.py)
+    diff = float(np.abs(res["pint"]["P"] - res["step_by_step"]["P"]).max() / 0.5)
+    for r in res.values():
+        r.pop("P")
+    out["plot_setting"] = {"workload": "h = 1/32, tau = 0.025, t = 10, P1, tol 1e-7, FP64", **res,
+                           "pint_vs_step_by_step_max_dp_over_p0": diff}
+    tab = {}
+    case = W.mandel(128, 1000, 0.1)
+    for kind in ("tri", "diag"):
+        with biot.Context(case.with_(precond=kind, n_iter=20), stream=stream, precision="fp32") as c:
+            biot.biot_tune(c.ctx, None)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, sweeps, rel = biot.biot_pint_solve(c.ctx, case.tol, 20000, allow_not_converged=True)
+            torch.cuda.synchronize()
+            tab["P1" if kind == "tri" else "P2"] = {"seconds": time.perf_counter() - t0, "sweeps": sweeps,
+                                                    "status": biot.STATUS_NAMES[st], "rel_residual": rel}
+    out["table_setting"] = {"workload": "h = 1/128, tau = 0.1, T = 100 (1000 steps), tol 1e-7, FP32 sweeps with "
+                                        "the FP64 refinement, FGMRES(20)", **tab}
     return out
 
 
@@ -1293,6 +1345,9 @@ def main():
     ap.add_argument("--barry-mercer", action="store_true",
                     help="also solve Barry & Mercer's point source (64^2, 256 steps, P2, tol 1e-10) step by "
                          "step and parallel in time, FP64 and FP32, and report times and differences")
+    ap.add_argument("--mandel", action="store_true",
+                    help="also solve Mandel's problem at the paper's two settings (Sec. 4.3) and report times, "
+                         "P1 against P2 and the error against the analytic series")
     ap.add_argument("--batched-full", action="store_true",
                     help="also solve the 64-instance batched workload to 1e-8: batched, one after another and "
                          "with the plain FP64 method (about ten minutes of GPU time)")
