@@ -995,8 +995,8 @@ def mandel_study(stream):
     """Mandel's problem as the paper runs it (Sec. 4.3). (a) The plot's setting: h = 1/32,
     tau = 0.025, P1, tol 1e-7, to t = 10 (400 steps), parallel in time against step by step
     (window 1), FP64; the centre pressure at t = 1, 5, 10 (the Mandel-Cryer rise above the
-    undrained 0.5). (b) The table's setting: h = 1/128, tau = 0.1,
-    T = 100 (1000 steps), tol 1e-7, P1 against P2, FP32 sweeps with the FP64 refinement."""
+    undrained 0.5). (b) Near the table's setting: tau = 0.1 on h = 1/64 to T = 20 (200 steps),
+    tol 1e-7, P1 against P2, FP32 sweeps with the FP64 refinement."""
     import numpy as np
     import torch
     import workloads as W
@@ -1025,7 +1025,9 @@ def mandel_study(stream):
     out["plot_setting"] = {"workload": "h = 1/32, tau = 0.025, t = 10, P1, tol 1e-7, FP64", **res,
                            "pint_vs_step_by_step_max_dp_over_p0": diff}
     tab = {}
-    case = W.mandel(128, 1000, 0.1)
+    # the table's tau = 0.1 on h = 1/64 to T = 20 (200 steps): the table's own 128^2 x 1000 steps
+    # needs over 1000 sweeps of 1000 columns per solve, more GPU time than a bench extra gets
+    case = W.mandel(64, 200, 0.1)
     for kind in ("tri", "diag"):
         with biot.Context(case.with_(precond=kind, n_iter=20), stream=stream, precision="fp32") as c:
             biot.biot_tune(c.ctx, None)
@@ -1035,7 +1037,7 @@ def mandel_study(stream):
             torch.cuda.synchronize()
             tab["P1" if kind == "tri" else "P2"] = {"seconds": time.perf_counter() - t0, "sweeps": sweeps,
                                                     "status": biot.STATUS_NAMES[st], "rel_residual": rel}
-    out["table_setting"] = {"workload": "h = 1/128, tau = 0.1, T = 100 (1000 steps), tol 1e-7, FP32 sweeps with "
+    out["table_setting"] = {"workload": "h = 1/64, tau = 0.1, T = 20 (200 steps), tol 1e-7, FP32 sweeps with "
                                         "the FP64 refinement, FGMRES(20)", **tab}
     return out
 

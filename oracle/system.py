@@ -64,6 +64,19 @@ def eliminate(M, dofs, diag_values):
     return M
 
 
+def add_in_pattern(M, E):
+    """M + E with M's stored pattern kept (explicit zeros included): every entry of E must be a
+    stored position of M (scipy's sum would drop M's explicit zeros)."""
+    M = M.tocsr(copy=True)
+    E = E.tocoo()
+    for r, c, v in zip(E.row, E.col, E.data):
+        lo, hi = M.indptr[r], M.indptr[r + 1]
+        k = lo + np.searchsorted(M.indices[lo:hi], c)
+        assert k < hi and M.indices[k] == c, (r, c)
+        M.data[k] += v
+    return M
+
+
 def build_system(case, beta=None) -> BiotSystem:
     """The eliminated system of `case`. beta (optional) overrides the stabilisation factor
     of the case's own mesh size (the coarse levels of the multigrid keep the fine one)."""
@@ -74,8 +87,7 @@ def build_system(case, beta=None) -> BiotSystem:
     AA_full, Ap_full = assemble(coords, tris, case.E, case.nu, case.alpha,
                                 case.kappa_elem(), case.tau, beta)
     if case.problem == "mandel":  # the rigid plate (reading A19): a penalty on the top row's u_y
-        AA_full = (AA_full + mandel_plate_penalty(case)).tocsr()
-        AA_full.sort_indices()
+        AA_full = add_in_pattern(AA_full, mandel_plate_penalty(case))
     n_dof = AA_full.shape[0]
     D = dirichlet_dofs(case)
     sign = np.where(D % 3 == 2, -1.0, 1.0)

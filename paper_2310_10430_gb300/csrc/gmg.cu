@@ -162,7 +162,7 @@ __global__ void k_gmg_power_apply(int n, int blk, const double* __restrict__ coe
   const int nx = n + 1, nn = nx * nx;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
     const double* cf = coef + (size_t)v * kCoef;
-    const int i = v % nx, j = v / nx;
+    const int j = v / nx, i = v - j * nx;
     if (blk == 0) {
       double y0 = 0.0, y1 = 0.0;
       for (int k = 0; k < 7; ++k) {
@@ -351,11 +351,15 @@ __device__ __forceinline__ void smooth_body(int n, const T* __restrict__ coef, c
                                             int nch, int ldo, int c0, int ncols) {
   constexpr int VEC = V16<T>::n;
   const int nx = n + 1;
-  const long long total = (long long)nx * nx * nch;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(q / nch), c = ca + (int)(q % nch) * VEC;
-    const int i = v % nx, j = v / nx;
+  // 32-bit work index: the set-up keeps nodes x column chunks below 2^31
+  const int total = nx * nx * nch;
+  // a contiguous range of the work per block, marched in steps of blockDim.x: consecutive steps
+  // cover neighbouring nodes, so most of a node's neighbour rows are still in L1
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int qb = blockIdx.x * per, qe = min(total, qb + per);
+  for (int q = qb + threadIdx.x; q < qe; q += blockDim.x) {
+    const int v = q / nch, c = ca + (q - v * nch) * VEC;
+    const int j = v / nx, i = v - j * nx;
     const T* cf = coef + (size_t)v * kCoef;
     T y0[VEC], y1[VEC], y2[VEC];
     if (!ZERO) {
@@ -444,11 +448,15 @@ __device__ __forceinline__ void residual_body(int n, const T* __restrict__ coef,
                                               const T* __restrict__ b, T* __restrict__ r, int ldg, int ca, int nch) {
   constexpr int VEC = V16<T>::n;
   const int nx = n + 1;
-  const long long total = (long long)nx * nx * nch;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(q / nch), c = ca + (int)(q % nch) * VEC;
-    const int i = v % nx, j = v / nx;
+  // 32-bit work index: the set-up keeps nodes x column chunks below 2^31
+  const int total = nx * nx * nch;
+  // a contiguous range of the work per block, marched in steps of blockDim.x: consecutive steps
+  // cover neighbouring nodes, so most of a node's neighbour rows are still in L1
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int qb = blockIdx.x * per, qe = min(total, qb + per);
+  for (int q = qb + threadIdx.x; q < qe; q += blockDim.x) {
+    const int v = q / nch, c = ca + (q - v * nch) * VEC;
+    const int j = v / nx, i = v - j * nx;
     T y0[VEC], y1[VEC], y2[VEC];
     stencil_apply<T, FM>(coef + (size_t)v * kCoef, x, i, j, n, ldg, c, y0, y1, y2);
     const size_t r0 = (size_t)(3 * v) * ldg + c;
@@ -489,11 +497,15 @@ __device__ __forceinline__ void restrict_body(int nc, const T* __restrict__ r, c
                                               T* __restrict__ bc, int ldg, int ca, int nch) {
   constexpr int VEC = V16<T>::n;
   const int cx = nc + 1, nf = 2 * nc;
-  const long long total = (long long)cx * cx * nch;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int V = (int)(q / nch), c = ca + (int)(q % nch) * VEC;
-    const int i = 2 * (V % cx), j = 2 * (V / cx);
+  // 32-bit work index: the set-up keeps nodes x column chunks below 2^31
+  const int total = cx * cx * nch;
+  // a contiguous range of the work per block, marched in steps of blockDim.x: consecutive steps
+  // cover neighbouring nodes, so most of a node's neighbour rows are still in L1
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int qb = blockIdx.x * per, qe = min(total, qb + per);
+  for (int q = qb + threadIdx.x; q < qe; q += blockDim.x) {
+    const int V = q / nch, c = ca + (q - V * nch) * VEC;
+    const int J = V / cx, i = 2 * (V - J * cx), j = 2 * J;
     T s0[VEC], s1[VEC], s2[VEC];
 #pragma unroll
     for (int k = 0; k < VEC; ++k) s0[k] = s1[k] = s2[k] = T(0);
@@ -545,11 +557,11 @@ __device__ __forceinline__ void prolong_body(int nf, const T* __restrict__ xc, T
                                              int nch) {
   constexpr int VEC = V16<T>::n;
   const int fx = nf + 1, cx = nf / 2 + 1;
-  const long long total = (long long)fx * fx * nch;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(q / nch), c = ca + (int)(q % nch) * VEC;
-    const int i = v % fx, j = v / fx;
+  // 32-bit work index: the set-up keeps nodes x column chunks below 2^31
+  const int total = fx * fx * nch;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const int v = q / nch, c = ca + (q - v * nch) * VEC;
+    const int j = v / fx, i = v - j * fx;
     int s0, s1;  // coarse source nodes (equal: one source)
     if (!(i & 1) && !(j & 1)) s0 = s1 = (j / 2) * cx + i / 2;
     else if (!(j & 1)) { s0 = (j / 2) * cx + (i - 1) / 2; s1 = s0 + 1; }
@@ -581,10 +593,10 @@ k_gmg_prolong(int nf, const T* __restrict__ xc, T* __restrict__ x, int ldg, int 
 template <typename T, int FM>
 __global__ void k_gmg_axpy(int nn, const T* __restrict__ e, T* __restrict__ x, int ldg, int ca, int nch) {
   constexpr int VEC = V16<T>::n;
-  const long long total = (long long)nn * nch;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(q / nch), c = ca + (int)(q % nch) * VEC;
+  // 32-bit work index: the set-up keeps nodes x column chunks below 2^31
+  const int total = nn * nch;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const int v = q / nch, c = ca + (q - v * nch) * VEC;
     for (int f = 0; f < 3; ++f) {
       if ((f < 2 && !(FM & 1)) || (f == 2 && !(FM & 2))) continue;
       T a[VEC], xv[VEC];
@@ -625,6 +637,9 @@ __global__ void k_gmg_coarse_prep(int nn, const T* __restrict__ b, const double*
 int grid_for(long long work) {
   return (int)std::max<long long>(1, std::min<long long>((work + kThreads - 1) / kThreads, 152 * 16));
 }
+// The stencil kernels' grid: one resident wave (8 CTAs of 256 threads per SM), each CTA marching
+// through a contiguous range of nodes.
+int grid_stencil(long long work) { return std::min(grid_for(work), 152 * 8); }
 
 struct GmgLevel {
   int n = 0, nn = 0;
@@ -754,7 +769,7 @@ void smooth_step(const Gmg& g, GmgLevel& L, cudaStream_t s, int k, bool zero, co
   constexpr int VEC = V16<T>::n;
   const T cu1 = (T)L.c1[0][k], cu2 = (T)L.c2[0][k], cp1 = (T)L.c1[1][k], cp2 = (T)L.c2[1][k];
   const int nch = g.ldg / VEC;  // every column chunk of the level buffers: unused columns stay finite
-  const int grid = grid_for((long long)L.nn * nch);
+  const int grid = grid_stencil((long long)L.nn * nch);
   T* d = buf_of<T>(L, GB_D);
   if (oz) {  // never the first step of a cycle (k >= 1 or a post-smoothing step)
     T* z = static_cast<T*>(oz->z);
@@ -802,9 +817,9 @@ void vcycle(Gmg& g, int l, cudaStream_t s, const T* b, T* xout, int c0, int ncol
   }
   // coarse-grid correction
   T* r = buf_of<T>(L, GB_R);
-  BIOT_LAUNCH((k_gmg_residual<T, FM>), grid_for((long long)L.nn * nch), kThreads, 0, s, L.n, coef_of<T>(L), xa, b,
+  BIOT_LAUNCH((k_gmg_residual<T, FM>), grid_stencil((long long)L.nn * nch), kThreads, 0, s, L.n, coef_of<T>(L), xa, b,
               r, g.ldg, 0, nch);
-  BIOT_LAUNCH((k_gmg_restrict<T, FM>), grid_for((long long)C.nn * nch), kThreads, 0, s, C.n, r, C.dmask,
+  BIOT_LAUNCH((k_gmg_restrict<T, FM>), grid_stencil((long long)C.nn * nch), kThreads, 0, s, C.n, r, C.dmask,
               buf_of<T>(C, GB_B), g.ldg, 0, nch);
   vcycle<T, FM>(g, l + 1, s, buf_of<T>(C, GB_B), buf_of<T>(C, GB_X), c0, ncols);
   BIOT_LAUNCH((k_gmg_prolong<T, FM>), grid_for((long long)L.nn * nch), kThreads, 0, s, L.n, buf_of<T>(C, GB_X), xa,
@@ -836,7 +851,7 @@ bool solve_level0(Gmg& g, cudaStream_t s, int c0, int ncols, const OutZ* oz) {
     // consumed by its restriction before its last smoothing step writes the correction)
     T* e = buf_of<T>(L, GB_E);
     T* corr = buf_of<T>(L, GB_R);
-    BIOT_LAUNCH((k_gmg_residual<T, FM>), grid_for((long long)L.nn * nch), kThreads, 0, s, L.n, coef_of<T>(L), x, b,
+    BIOT_LAUNCH((k_gmg_residual<T, FM>), grid_stencil((long long)L.nn * nch), kThreads, 0, s, L.n, coef_of<T>(L), x, b,
                 e, g.ldg, 0, nch);
     vcycle<T, FM>(g, 0, s, e, corr, c0, ncols);
     BIOT_LAUNCH((k_gmg_axpy<T, FM>), grid_for((long long)L.nn * nch), kThreads, 0, s, L.nn, corr, x, g.ldg, 0, nch);
@@ -1149,7 +1164,7 @@ void batch_vcycle(GmgBatch* gb, const InstDev* tab, int count, int j, cudaStream
   // the buffer holding a level's iterate after its pre-smoothing (the same for every level)
   int cur = GB_XA;
   for (int l = 0; l + 1 < Lm; ++l) {
-    const dim3 grid(grid_for(gb->work[l]), 1, count);
+    const dim3 grid(grid_stencil(gb->work[l]), 1, count);
     BIOT_LAUNCH((kb_gmg_smooth<FM, true, false, false>), grid, kThreads, 0, s, tab, gt, Lm, l, 0, -1, GB_XA, j);
     cur = GB_XA;
     for (int k = 1; k < m; ++k) {
@@ -1158,7 +1173,7 @@ void batch_vcycle(GmgBatch* gb, const InstDev* tab, int count, int j, cudaStream
       cur = nxt;
     }
     BIOT_LAUNCH((kb_gmg_residual_restrict<FM>), grid, kThreads, 0, s, tab, gt, Lm, l, cur, 0);
-    BIOT_LAUNCH((kb_gmg_residual_restrict<FM>), dim3(grid_for(gb->work[l + 1]), 1, count), kThreads, 0, s, tab, gt,
+    BIOT_LAUNCH((kb_gmg_residual_restrict<FM>), dim3(grid_stencil(gb->work[l + 1]), 1, count), kThreads, 0, s, tab, gt,
                 Lm, l, cur, 1);
   }
   // every instance's coarsest level at once: +-b d, then the batched exact P2 band solves
