@@ -77,7 +77,7 @@ typedef enum {
   BIOT_MANDEL = 3            /* quarter domain under a rigid frictionless plate pressed with the force F = load
                                 (Sec. 4.3): x = a drained and traction-free, x = 0 and y = 0 symmetry planes
                                 (u_x = 0, u_y = 0, no flux), impervious top with u_y constant along x, imposed
-                                by the penalty 1e6 (lambda + 2 mu) (u_y(i+1) - u_y(i))^2 / 2 over consecutive top
+                                by the penalty 1e4 (lambda + 2 mu) (u_y(i+1) - u_y(i))^2 / 2 over consecutive top
                                 nodes, the force as the traction (0, -F / a); initial state the undrained response
                                 of Sec. 4.3 (Skempton B = 1) */
 } biot_problem;

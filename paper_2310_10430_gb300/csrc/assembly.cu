@@ -435,7 +435,7 @@ biot_status build_pattern(biot_ctx* ctx) {
 }
 
 // k_p / (lambda + 2 mu) of Mandel's rigid-plate penalty (reading of Sec. 4.3)
-constexpr double kMandelPenalty = 1e6;
+constexpr double kMandelPenalty = 1e4;
 
 biot_status assemble_system(biot_ctx* ctx) {
   const biot_params& p = ctx->prm;

@@ -248,7 +248,8 @@ def test_mandel_discrete_pressure_matches_the_series():
 def test_mandel_penalty_plate_approximates_the_rigid_constraint():
     # exact constraint by master-slave elimination: every top u_y equals one unknown U, whose test
     # function is 1 on the whole top (so the force enters as the sum of the top loads); the
-    # penalty k_p = 1e6 (lambda + 2 mu) must agree to about 1 / 1e6
+    # penalty k_p = 1e4 (lambda + 2 mu) must agree to about 1 / 1e4 (the error scales with 1 / k_p:
+    # 1.2e-7, 1.2e-5, 1.2e-4 for 1e6, 1e4, 1e3)
     import scipy.sparse as sp
     import scipy.sparse.linalg as spla
     from oracle.fem import assemble, stabilisation_beta
@@ -273,8 +274,8 @@ def test_mandel_penalty_plate_approximates_the_rigid_constraint():
     for k in range(1, s.F.shape[0]):
         X[k] = T @ lu.solve(T.T @ (s.Ap @ X[k - 1] + s.F[k]))
     eu, ep = field_rel_errors(Xp, X)
-    assert eu < 1e-5 and ep < 1e-5, (eu, ep)
-    assert np.ptp(X[-1, top_uy]) == 0.0 and np.ptp(Xp[-1, top_uy]) < 1e-5 * np.abs(Xp[-1, top_uy]).max()
+    assert eu < 1e-4 and ep < 1e-4, (eu, ep)
+    assert np.ptp(X[-1, top_uy]) == 0.0 and np.ptp(Xp[-1, top_uy]) < 1e-4 * np.abs(Xp[-1, top_uy]).max()
 
 
 def test_mandel_initial_state_is_the_undrained_response():
@@ -294,3 +295,20 @@ def test_mandel_initial_state_is_the_undrained_response():
     for d in (du, dv):
         assert d[0] < 0.03 and all(1.7 < d[k] / d[k + 1] < 2.3 for k in range(2)), d
     assert dp[0] < 0.01 and dp[0] > dp[1] > dp[2], dp
+
+
+def test_mandel_pint_needs_longer_krylov_cycles_with_p2():
+    # with the rigid plate, one FGMRES(10) cycle per sweep stalls under P2 (the complex spectrum
+    # 1 +- i sqrt(eig(S^-1 B^T A^-1 B)) of P2^-1 AA), while FGMRES(30), the restart length of
+    # the GMRES the paper runs, converges to backward Euler like P1 does (reading A19)
+    from oracle.solvers import BlockPreconditioner, pint_sweeps
+    case = W.mandel(12, 10, 0.025)
+    s = build_system(case)
+    ref = seq_solve(s)
+    P2 = BlockPreconditioner(s, "diag")
+    X, nsw, conv, _ = pint_sweeps(s, P2, 10, mode="tol", tol=1e-9, max_sweeps=150)
+    assert not conv
+    X, nsw, conv, _ = pint_sweeps(s, P2, 30, mode="tol", tol=1e-10, max_sweeps=150)
+    assert conv and max(field_rel_errors(X, ref)) < 1e-8
+    X, nsw, conv, _ = pint_sweeps(s, BlockPreconditioner(s, "tri"), 10, mode="tol", tol=1e-10, max_sweeps=150)
+    assert conv and max(field_rel_errors(X, ref)) < 1e-8
