@@ -323,7 +323,10 @@ def sweep_bytes(info, ncols, n_iter, precision, precond, strips=0, dense_sep=(Tr
                   P1 adds the coupling B^T z_u: 4 P s_v + 2 n_nodes W s + n_nodes W s.
         SpMM      nnz (s_v + 4) + 4 (N+1) + 2 N W s
         CGS2      two passes of dots ((j+1) + ceil((j+1)/8)) N W s and Gram-Schmidt update
-                  (j+1+2) N W s, one norm N W s, one column scaling 2 N W s (not after the last)
+                  (j+1+2) N W s, one norm N W s, one column scaling 2 N W s (not after the last).
+                  FP32 / BF16 sweeps: the norm rides on the second update, and up to 12 basis
+                  vectors the first update also forms the second sweep's dots (no second dots
+                  pass)
       update      n_iter N W s (Z) + 2 N W 8 (X in FP64) and the initial scaling 2 N W s
     """
     import math
@@ -361,8 +364,13 @@ def sweep_bytes(info, ncols, n_iter, precision, precond, strips=0, dense_sep=(Tr
     out["spmm"] = n_iter * (nnz * (s_v + 4) + 4 * (N + 1) + 2 * N * W * s)
     kry = 2 * N * W * s + n_iter * N * W * s + 2 * N * W * 8
     for j in range(n_iter):
-        kry += 2 * (((j + 1) + math.ceil((j + 1) / 8)) * N * W * s + (j + 3) * N * W * s)
-        kry += N * W * s + (2 * N * W * s if j + 1 < n_iter else 0)
+        dots = ((j + 1) + math.ceil((j + 1) / 8)) * N * W * s
+        upd = (j + 3) * N * W * s
+        if fp64:
+            kry += 2 * (dots + upd) + N * W * s
+        else:
+            kry += dots + 2 * upd + (dots if j + 1 > 12 else 0)
+        kry += 2 * N * W * s if j + 1 < n_iter else 0
     out["krylov"] = kry
     out["total"] = sum(out.values())
     out["per_apply_block_solves"] = apply_b

@@ -117,6 +117,7 @@ template <> struct KVec<double> {
 // widened down to a multiple of VEC). Each column's products are summed in the same order as
 // in dots_body, so the partials are identical. Needs ld % VEC == 0 and 16-byte aligned rows.
 constexpr int kDotChunk = 8;
+constexpr int kFuseVecs = 12;  // basis vectors up to which the first update also forms the second's dots
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_dots_vec(const T* __restrict__ V, size_t vstride, int nvec, const T* __restrict__ w, int nrows, int ld, int c0,
@@ -276,6 +277,92 @@ k_gs_axpy_rows_vec(const T* __restrict__ V, size_t vstride, int nvec, const doub
           part[(size_t)blockIdx.x * ld + col] = sum;
         }
       }
+    }
+  }
+}
+
+// The first Gram-Schmidt sweep fused with the dot products of the second: w -= V h (h the
+// first sweep's coefficients, staged in shared memory as in k_gs_axpy_rows_vec; same
+// per-element arithmetic order), then the per-block partials of V_i . w with the updated w
+// as stored, in part[i][block][c]. The grid, the row partition, each thread's row order and
+// the block epilogue are those of k_dots_vec, so the partials are bit-identical to a separate
+// k_dots_vec pass over the stored w: one pass over V instead of two. V_i's row is read again
+// for the dot after the update (from L1/L2: the same 16 bytes the update just loaded).
+// Needs nvec <= NV (the dot accumulators live in registers).
+template <typename T, int NV>
+__global__ void __launch_bounds__(256, 2)
+k_gs_axpy_dots_vec(const T* __restrict__ V, size_t vstride, int nvec, const double* __restrict__ h,
+                   T* __restrict__ w, int nrows, int ld, int c0, int ncols, double* __restrict__ part) {
+  using VV = typename KVec<T>::V;
+  constexpr int VEC = KVec<T>::n;
+  __shared__ __align__(16) T sh[NV][32 * VEC];
+  __shared__ double sm[8][32 * VEC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = (nrows + gridDim.x - 1) / gridDim.x;
+  const int rb = blockIdx.x * per, re = min(nrows, rb + per);
+  const int ca = c0 & ~(VEC - 1), ce = c0 + ncols;
+  for (int cb = ca; cb < ce; cb += 32 * VEC) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < nvec * 32 * VEC; t += blockDim.x) {
+      const int i = t / (32 * VEC), q = t % (32 * VEC), col = cb + q;
+      sh[i][q] = col < ld ? (T)h[(size_t)i * ld + col] : T(0);
+    }
+    __syncthreads();
+    const int c = cb + lane * VEC;
+    const bool any = c < ce;
+    const bool full = c >= c0 && c + VEC <= ce;
+    T dacc[NV][VEC];
+#pragma unroll
+    for (int ii = 0; ii < NV; ++ii)
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) dacc[ii][q] = T(0);
+    if (any) {
+      for (int r = rb + warp; r < re; r += 8) {
+        T* wr = w + (size_t)r * ld + c;
+        T acc[VEC];
+        KVec<T>::get(*reinterpret_cast<const VV*>(wr), acc);
+#pragma unroll 4
+        for (int i = 0; i < nvec; ++i) {
+          T v[VEC], hq[VEC];
+          KVec<T>::get(*reinterpret_cast<const VV*>(V + (size_t)i * vstride + (size_t)r * ld + c), v);
+          KVec<T>::get(*reinterpret_cast<const VV*>(&sh[i][lane * VEC]), hq);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) acc[q] -= hq[q] * v[q];
+        }
+        if (full) {
+          *reinterpret_cast<VV*>(wr) = KVec<T>::make(acc);
+        } else {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q)
+            if (c + q >= c0 && c + q < ce) wr[q] = acc[q];
+        }
+#pragma unroll
+        for (int ii = 0; ii < NV; ++ii) {
+          if (ii < nvec) {
+            T v[VEC];
+            KVec<T>::get(*reinterpret_cast<const VV*>(V + (size_t)ii * vstride + (size_t)r * ld + c), v);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) dacc[ii][q] += v[q] * acc[q];
+          }
+        }
+      }
+    }
+    for (int ii = 0; ii < nvec; ++ii) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+        if (k == ii)
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) sm[warp][lane * VEC + q] = (double)dacc[k][q];
+      __syncthreads();
+      for (int t = threadIdx.x; t < 32 * VEC; t += blockDim.x) {
+        const int col = cb + t;
+        if (col >= c0 && col < ce) {
+          double sum = 0.0;
+          for (int u = 0; u < 8; ++u) sum += sm[u][t];
+          part[((size_t)ii * gridDim.x + blockIdx.x) * ld + col] = sum;
+        }
+      }
+      __syncthreads();
     }
   }
 }
@@ -648,11 +735,25 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
     precond_apply<T>(ctx, Vj, Zj, c0, ncols);
     launch_spmm_scaled<T>(ctx, Zj, Wv, c0, ncols);
     reduce_partials(ctx, 1, ncols, cs + CS_WN0 * ld, ld, c0, spmm_blocks(ctx));
+    const bool fused = vec && j + 1 <= kFuseVecs;
     for (int pass = 0; pass < 2; ++pass) {
       double* h = pass == 0 ? h1 : h2;
+      if (fused && pass == 1) {
+        reduce_partials(ctx, j + 1, ncols, h, ld, c0);  // the fused first update formed the partials
+        BIOT_LAUNCH((k_gs_axpy_rows_vec<T, true>), 2 * kRedBlocks, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0,
+                    ncols, ctx->part);
+        continue;
+      }
       dots(V, j + 1, Wv);
       reduce_partials(ctx, j + 1, ncols, h, ld, c0);
-      if (vec && pass == 0)
+      if (fused)  // pass 0: w -= V h1 and the partials of V^T w for h2 in one pass over V
+        if (j + 1 <= 8)
+          BIOT_LAUNCH((k_gs_axpy_dots_vec<T, 8>), kRedBlocks, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0, ncols,
+                      ctx->part);
+        else
+          BIOT_LAUNCH((k_gs_axpy_dots_vec<T, kFuseVecs>), kRedBlocks, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0,
+                      ncols, ctx->part);
+      else if (vec && pass == 0)
         BIOT_LAUNCH((k_gs_axpy_rows_vec<T, false>), 2 * kRedBlocks, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0,
                     ncols, ctx->part);
       else if (vec)  // the second sweep also forms the partial norms of the new w (2 x kRedBlocks

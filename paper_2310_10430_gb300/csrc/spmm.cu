@@ -548,7 +548,8 @@ biot_status spmm_tune(biot_ctx* ctx, std::map<std::string, int>* cache, int* hit
   *ms_default = time_v(0);
   if (cache && cache->count(key)) {
     const int v = (*cache)[key];
-    if (v >= 0 && v < kSpmmVariantCount && spmm_variant_ok(ctx, v, z, w)) {
+    // the default shape (0) is always usable: it falls back to the scalar kernel when rows are not 16-byte aligned
+    if (v >= 0 && v < kSpmmVariantCount && (v == 0 || spmm_variant_ok(ctx, v, z, w))) {
       ctx->spmm_var = v;
       *hit = 1;
       *ms_best = time_v(v);

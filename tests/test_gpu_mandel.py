@@ -48,13 +48,18 @@ def test_mandel_assembly_rhs_and_initial_state_match_oracle():
 @pytest.mark.parametrize("n,strips", [(16, None), (32, 2)])
 def test_mandel_pint_matches_backward_euler(kind, n, strips):
     # the plate penalty leaves the equilibrated system less well conditioned than the other
-    # problems: tol 1e-11 (FGMRES(30), the workload's cycle length)
+    # problems: |AA| |x| is 1e4-5e4 times |b| per step, so FP64 rounding alone leaves a residual
+    # of about 3e-12 of |b| at n = 32 (step 1). Tolerance 1e-10 (FGMRES(30), the workload's cycle
+    # length), well above that floor; the oracle reaches errors of 6e-12 (P2) and 2e-11 (P1)
+    # against backward Euler with it. The stopping test is per step, relative to each step's
+    # right-hand side f_n + M x_{n-1}; the returned residual is the space-time one relative to
+    # f_ST, whose steps n > 1 hold f_n alone, so it can sit a few times above the tolerance.
     case = W.mandel(n, 24, 0.025).with_(precond=kind)
     ref = seq_solve(build_system(case))
     with biot.Context(case, stream=torch.cuda.current_stream(), strips=strips) as c:
-        st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-11, 20000)
+        st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-10, 20000)
         X = biot.biot_get_state(c.ctx, 0, case.n_t)
-    assert st == biot.BIOT_OK and rel <= 1e-11
+    assert st == biot.BIOT_OK and rel <= 1e-9
     eu, ep = field_rel_errors(X, ref)
     assert eu < 1e-10 and ep < 1e-10, (eu, ep)
 
@@ -63,7 +68,7 @@ def test_mandel_fp32_refinement_reaches_1e8():
     case = W.mandel(16, 20, 0.025)
     ref = seq_solve(build_system(case))
     with biot.Context(case, stream=torch.cuda.current_stream(), precision="fp32") as c:
-        st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-11, 20000)
+        st, sweeps, rel = biot.biot_pint_solve(c.ctx, 1e-10, 20000)
         X = biot.biot_get_state(c.ctx, 0, case.n_t)
     eu, ep = field_rel_errors(X, ref)
     assert st == biot.BIOT_OK and eu < 1e-8 and ep < 1e-8, (eu, ep)

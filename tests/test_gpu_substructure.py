@@ -172,6 +172,8 @@ def forced_apply(tmp_path, case, precision, variant, separators, seed, strips=4)
         biot.biot_tune(c.ctx, str(probe))
         entries = json.loads(probe.read_text())["band_solve_variants"]
         for e in entries:
+            if not e["key"].startswith("sub:"):
+                continue  # the SpMM shape of the reduced-precision sweep ("spmm:...") keeps its choice
             # separators have half-band 2 d (n + 1) - 1 (d = 1, 2), strip interiors d (w + 2) - 1
             if (int(e["key"].split(":b")[1].split(":")[0]) >= 2 * (case.n + 1) - 1) == separators:
                 e["variant"] = variant

@@ -99,3 +99,21 @@ def test_spmm_tuner_picks_and_caches(tmp_path):
         assert any(e["key"].startswith("spmm:fp32:") for e in entries)
         t2 = biot.biot_tune(c.ctx, str(cache))
         assert t2.spmm_variant == t.spmm_variant and t2.from_cache == 1
+
+
+def test_cached_default_spmm_shape_hits_on_a_ragged_window(tmp_path):
+    # a window that is not a multiple of four columns: the vector shapes do not fit, and a cached
+    # default shape (the scalar kernel there) must still count as a cache hit
+    case = W.terzaghi_small().with_(n=16, n_t=6)
+    with biot.Context(case, precision="fp32") as c:
+        assert c.info.window_cap % 4 != 0
+        cache = tmp_path / "tune.json"
+        biot.biot_tune(c.ctx, str(cache))
+        entries = json.loads(cache.read_text())["band_solve_variants"]
+        for e in entries:
+            if e["key"].startswith("spmm:"):
+                e["variant"] = 0
+        cache.write_text('{"band_solve_variants": [\n' +
+                         ",\n".join(f'  {{"key": "{e["key"]}", "variant": {e["variant"]}}}' for e in entries) + "\n]}\n")
+        t = biot.biot_tune(c.ctx, str(cache))
+        assert t.spmm_variant == 0 and t.from_cache == 1
