@@ -390,8 +390,10 @@ def gmg_apply_bytes(n, W, s, precond, smooth=2, cycles=1, levels=0):
     """Algorithmic DRAM bytes of one P apply with multigrid block solves (biot_set_inner_solver).
 
     Per level l < L-1 (R = rows of the fields in the cycle, VB = R W s one vector pass): the first
-    smoothing step from zero 3 VB (b in, x and d out), every other step 5 VB (x, b, d in; x, d out;
-    the 7-point stencil's neighbour rows are cache hits), residual 3 VB, restriction VB + VB_c,
+    smoothing step from zero 2 VB (b in, x out: its increment is x, where the next step reads it),
+    every other step x and b in, x out, the increment d in unless the previous step started from
+    zero, d out unless it is the smoothing's last step (the 7-point stencil's neighbour rows are
+    cache hits): 5 VB for the middle steps, residual 3 VB, restriction VB + VB_c,
     prolongation 2 VB + VB_c, and the stencil coefficients (40 values per node) read by each of
     the 2 smooth + 1 passes over the level. Coarsest level: its input 2 VB (the band solves of a
     16^2 mesh are negligible). Level 0 adds the right-hand side (input rows in, b out: 2 VB) and
@@ -410,9 +412,15 @@ def gmg_apply_bytes(n, W, s, precond, smooth=2, cycles=1, levels=0):
                 tot += 2 * VB
                 continue
             VBc = rows_per_node * ((nl // 2) + 1) ** 2 * W * s
-            tot += 3 * VB + 5 * VB * (smooth - 1)        # pre-smoothing
+            for pre in (True, False):
+                for k in range(smooth):
+                    if pre and k == 0:
+                        tot += 2 * VB
+                        continue
+                    d_in = k > 0 and not (pre and k == 1)
+                    d_out = k + 1 < smooth
+                    tot += (3 + d_in + d_out) * VB
             tot += 3 * VB + VB + VBc + 2 * VB + VBc      # residual, restriction, prolongation
-            tot += 4 * VB + 5 * VB * (smooth - 1)        # post-smoothing
             tot += (2 * smooth + 1) * nn * 40 * s
         nn0 = (n + 1) ** 2
         VB0 = rows_per_node * nn0 * W * s
@@ -665,6 +673,16 @@ def run_ours(args):
             extras["batched_config4"] = batched_config4(stream)
         except Exception as e:  # e.g. device memory: report, keep the bench line
             extras["batched_config4"] = {"error": str(e)[:300]}
+        if world == 1:
+            # the 1024^2 stress workload's sweep with multigrid block solves (94 GB on the device);
+            # its time to error is the --large --large-gmg --large-error run
+            import types
+            try:
+                extras["large_1024"] = large_mesh(types.SimpleNamespace(
+                    steps=2, warmup=3, large_outer=0, large_gmg=True, large_error=False, large_n_iter=20,
+                    large_tols=None, large_ref_gmg=False, strips=None, tune_cache=None), quiet=True)
+            except Exception as e:
+                extras["large_1024"] = {"error": str(e)[:300]}
     if args.lognormal:
         extras["lognormal_precisions"] = lognormal_precisions(stream, args.lognormal)
     if args.efficiency:
@@ -771,7 +789,8 @@ def sweep_variant(case, precision, steps, warmup, stream, gmg=None):
                 "block_solves": ("multigrid V-cycles (%d levels, %s)" % (info.gmg_levels, gmg)) if gmg
                                 else "exact (substructured factorisations)",
                 "tuning": {k: tuning[k] for k in ("variant_u", "variant_p", "nb_u", "threads_u", "tma_u", "strips",
-                                                  "variant_sep_u", "variant_sep_p")}}
+                                                  "variant_sep_u", "variant_sep_p", "spmm_variant", "ms_spmm",
+                                                  "ms_spmm_default")}}
 
 
 def time_to_solution(case, stream):
@@ -1050,7 +1069,7 @@ def mandel_study(stream):
     return out
 
 
-def large_mesh(args):
+def large_mesh(args, quiet=False):
     """The 1024^2 stress workload (3,151,875 DOF, N_t = 128, nu = 0.49, lognormal kappa sigma 2,
     l = 0.1, P1): FP32 sweeps with the FP64 residual and update. One JSON line: the sweep
     throughput over args.steps timed sweeps (the bench metric, all N_t steps active), the
@@ -1067,9 +1086,22 @@ def large_mesh(args):
     case = W.large_1024()
     if args.large_n_iter:
         case = case.with_(n_iter=args.large_n_iter)
+    gmg = GMG if args.large_gmg else None
+    ref, ref_run = None, None
+    if args.large_outer > 0 and args.large_error and args.large_ref_gmg:
+        # the 1e-12 reference from a multigrid context (the faster path), solved and freed before
+        # the path under test is set up
+        with biot.Context(case.with_(n_iter=max(case.n_iter, 20)), stream=stream, precision="fp32", gmg=GMG) as cr:
+            biot.biot_tune(cr.ctx, None)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            st, sweeps, rel = biot.biot_pint_solve(cr.ctx, 1e-12, args.large_outer, allow_not_converged=True)
+            torch.cuda.synchronize()
+            ref_run = {"seconds": time.perf_counter() - t2, "sweeps": sweeps, "status": biot.STATUS_NAMES[st],
+                       "rel_residual": rel, "tol": 1e-12, "block_solves": "multigrid"}
+            ref = biot.biot_get_state(cr.ctx, 0, case.n_t)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    gmg = GMG if args.large_gmg else None
     with biot.Context(case, stream=stream, precision="fp32", strips=args.strips, gmg=gmg) as c:
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
@@ -1111,7 +1143,8 @@ def large_mesh(args):
                 return {"seconds": time.perf_counter() - t2, "sweeps": sweeps, "status": biot.STATUS_NAMES[st],
                         "rel_residual": rel, "tol": tol}
 
-            solve = solve_from_zero(case.tol)
+            tols = [float(t) for t in args.large_tols.split(",")] if args.large_tols else [case.tol]
+            solve = solve_from_zero(tols[0])
             if args.large_error:
                 # Error, not residual: at nu = 0.49 the two differ. The reference is the same FP64
                 # space-time system solved to a relative FP64 residual of 1e-12 (FP32 sweeps as the
@@ -1120,13 +1153,15 @@ def large_mesh(args):
                 # the zero state and timed; the time to error 1e-8 is the first whose per-field
                 # relative error against the reference is at most 1e-8.
                 X = biot.biot_get_state(c.ctx, 0, case.n_t)
-                ref_run = solve_from_zero(1e-12)
-                ref = biot.biot_get_state(c.ctx, 0, case.n_t)
+                if ref is None:
+                    ref_run = solve_from_zero(1e-12)
+                    ref = biot.biot_get_state(c.ctx, 0, case.n_t)
                 runs = []
                 eu, ep = _field_errors(np, X[1:], ref[1:])
                 runs.append(dict(solve, err_u=eu, err_p=ep))
                 del X
-                for tol in (1e-9, 1e-10, 1e-11):
+                ladder = tols[1:] if args.large_tols else [1e-9, 1e-10, 1e-11]
+                for tol in ladder:
                     if max(runs[-1]["err_u"], runs[-1]["err_p"]) <= 1e-8:
                         break
                     r = solve_from_zero(tol)
@@ -1169,7 +1204,8 @@ def large_mesh(args):
                               "frac": by["total"] / (ms / 1e3) / 1e9 / hbm},
            "max_rel_residual_after_sweeps": rel_swept, "tolerance_solve": solve,
            "time_to_error": time_to_error, "tuning": tuning}
-    print(json.dumps(out))
+    if not quiet:
+        print(json.dumps(out))
     return out
 
 
@@ -1388,6 +1424,12 @@ def main():
     ap.add_argument("--large-error", action="store_true",
                     help="with --large and --large-outer: also solve to 1e-12 as the reference and time the "
                          "solves until the per-field error (not the residual) is at most 1e-8")
+    ap.add_argument("--large-tols", default=None,
+                    help="comma-separated tolerance ladder of the --large-error solves (default: the "
+                         "workload's 1e-8, then 1e-9, 1e-10, 1e-11 until the error target is met)")
+    ap.add_argument("--large-ref-gmg", action="store_true",
+                    help="--large-error: solve the 1e-12 reference with multigrid block solves in a "
+                         "context of its own (whatever the path under test)")
     ap.add_argument("--large-n-iter", type=int, default=0,
                     help="with --large: FGMRES restart length (default: the workload's 10)")
     ap.add_argument("--gmg", action="store_true",

@@ -344,7 +344,12 @@ __device__ __forceinline__ void stencil_apply(const T* __restrict__ cf, const T*
 // (READD false: c1 d dropped), x_out = x_in + d; Dirichlet rows x_out = b, d = 0.
 // OUTZ: x_out is the preconditioner's output z (leading dimension ldo, only the columns
 // [c0, c0 + ncols) written, 16-byte stores when ldo allows) instead of a level buffer.
-template <typename T, int FM, bool ZERO, bool READD, bool OUTZ>
+// DMODE bit 0 (DM_FROM_X): the previous increment is read from x_in, which holds it after a
+// step from zero (x = 0 + d; on Dirichlet rows x = b but d is not used there); bit 1
+// (DM_NO_STORE): the new increment is not stored (no later step of the cycle reads it).
+// Each saves one pass over a level vector.
+enum { DM_FROM_X = 1, DM_NO_STORE = 2 };
+template <typename T, int FM, bool ZERO, bool READD, bool OUTZ, int DMODE = 0>
 __device__ __forceinline__ void smooth_body(int n, const T* __restrict__ coef, const uint8_t* __restrict__ dmask,
                                             const T* __restrict__ xin, const T* __restrict__ b, T* __restrict__ d,
                                             T* __restrict__ xout, T cu1, T cu2, T cp1, T cp2, int ldg, int ca,
@@ -377,7 +382,13 @@ __device__ __forceinline__ void smooth_body(int n, const T* __restrict__ coef, c
         ldv(xin + r0, x0);
         ldv(xin + r0 + ldg, x1);
       }
-      if (READD) {
+      if (READD && (DMODE & DM_FROM_X)) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+          d0[k] = x0[k];
+          d1[k] = x1[k];
+        }
+      } else if (READD) {
         ldv(d + r0, d0);
         ldv(d + r0 + ldg, d1);
       }
@@ -407,15 +418,22 @@ __device__ __forceinline__ void smooth_body(int n, const T* __restrict__ coef, c
         stv(xout + r0, x0);
         stv(xout + r0 + ldg, x1);
       }
-      stv(d + r0, d0);
-      stv(d + r0 + ldg, d1);
+      if (!(DMODE & DM_NO_STORE)) {
+        stv(d + r0, d0);
+        stv(d + r0 + ldg, d1);
+      }
     }
     if (FM & 2) {
       const size_t r2 = r0 + 2 * (size_t)ldg;
       T b2[VEC], x2[VEC], d2[VEC];
       ldv(b + r2, b2);
       if (!ZERO) ldv(xin + r2, x2);
-      if (READD) ldv(d + r2, d2);
+      if (READD && (DMODE & DM_FROM_X)) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) d2[k] = x2[k];
+      } else if (READD) {
+        ldv(d + r2, d2);
+      }
       const T mp = cf[kCoefMp];
       const bool dir2 = dmask[3 * v + 2] != 0;
 #pragma unroll
@@ -428,18 +446,18 @@ __device__ __forceinline__ void smooth_body(int n, const T* __restrict__ coef, c
       }
       if (OUTZ) store_out(xout + (size_t)(3 * v + 2) * ldo, x2, c, ldo, c0, ncols);
       else stv(xout + r2, x2);
-      stv(d + r2, d2);
+      if (!(DMODE & DM_NO_STORE)) stv(d + r2, d2);
     }
   }
 }
 
-template <typename T, int FM, bool ZERO, bool READD, bool OUTZ = false>
+template <typename T, int FM, bool ZERO, bool READD, bool OUTZ = false, int DMODE = 0>
 __global__ void __launch_bounds__(kThreads)
 k_gmg_smooth(int n, const T* __restrict__ coef, const uint8_t* __restrict__ dmask, const T* __restrict__ xin,
              const T* __restrict__ b, T* __restrict__ d, T* __restrict__ xout, T cu1, T cu2, T cp1, T cp2, int ldg,
              int ca, int nch, int ldo = 0, int c0 = 0, int ncols = 0) {
-  smooth_body<T, FM, ZERO, READD, OUTZ>(n, coef, dmask, xin, b, d, xout, cu1, cu2, cp1, cp2, ldg, ca, nch, ldo, c0,
-                                        ncols);
+  smooth_body<T, FM, ZERO, READD, OUTZ, DMODE>(n, coef, dmask, xin, b, d, xout, cu1, cu2, cp1, cp2, ldg, ca, nch, ldo,
+                                               c0, ncols);
 }
 
 // r = b - K x on the rows in FM.
@@ -765,31 +783,44 @@ struct OutZ {
 
 template <typename T, int FM>
 void smooth_step(const Gmg& g, GmgLevel& L, cudaStream_t s, int k, bool zero, const T* xin, const T* b, T* xout,
-                 const OutZ* oz = nullptr) {
+                 const OutZ* oz = nullptr, bool d_from_x = false) {
   constexpr int VEC = V16<T>::n;
   const T cu1 = (T)L.c1[0][k], cu2 = (T)L.c2[0][k], cp1 = (T)L.c1[1][k], cp2 = (T)L.c2[1][k];
   const int nch = g.ldg / VEC;  // every column chunk of the level buffers: unused columns stay finite
   const int grid = grid_stencil((long long)L.nn * nch);
   T* d = buf_of<T>(L, GB_D);
-  if (oz) {  // never the first step of a cycle (k >= 1 or a post-smoothing step)
+  // the increment is read only by the next step of the same smoothing (k + 1 < smooth); a step
+  // from zero leaves it in x, where the next step reads it
+  const bool keep_d = !zero && k + 1 < g.smooth;
+#define BIOT_SMOOTH(ZERO, READD, OUTZ, DMODE, ...)                                                                \
+  BIOT_LAUNCH((k_gmg_smooth<T, FM, ZERO, READD, OUTZ, DMODE>), grid, kThreads, 0, s, L.n, coef_of<T>(L), L.dmask, \
+              xin, b, d, __VA_ARGS__)
+  if (oz) {  // never the first step of a cycle (k >= 1 or a post-smoothing step): the last one
     T* z = static_cast<T*>(oz->z);
     if (k == 0)
-      BIOT_LAUNCH((k_gmg_smooth<T, FM, false, false, true>), grid, kThreads, 0, s, L.n, coef_of<T>(L), L.dmask, xin,
-                  b, d, z, cu1, cu2, cp1, cp2, g.ldg, 0, nch, oz->ld, oz->c0, oz->ncols);
+      BIOT_SMOOTH(false, false, true, DM_NO_STORE, z, cu1, cu2, cp1, cp2, g.ldg, 0, nch, oz->ld, oz->c0, oz->ncols);
+    else if (d_from_x)
+      BIOT_SMOOTH(false, true, true, DM_NO_STORE | DM_FROM_X, z, cu1, cu2, cp1, cp2, g.ldg, 0, nch, oz->ld, oz->c0,
+                  oz->ncols);
     else
-      BIOT_LAUNCH((k_gmg_smooth<T, FM, false, true, true>), grid, kThreads, 0, s, L.n, coef_of<T>(L), L.dmask, xin,
-                  b, d, z, cu1, cu2, cp1, cp2, g.ldg, 0, nch, oz->ld, oz->c0, oz->ncols);
+      BIOT_SMOOTH(false, true, true, DM_NO_STORE, z, cu1, cu2, cp1, cp2, g.ldg, 0, nch, oz->ld, oz->c0, oz->ncols);
     return;
   }
   if (zero)
-    BIOT_LAUNCH((k_gmg_smooth<T, FM, true, false>), grid, kThreads, 0, s, L.n, coef_of<T>(L), L.dmask, xin, b, d,
-                xout, cu1, cu2, cp1, cp2, g.ldg, 0, nch);
+    BIOT_SMOOTH(true, false, false, DM_NO_STORE, xout, cu1, cu2, cp1, cp2, g.ldg, 0, nch);
+  else if (k == 0 && keep_d)
+    BIOT_SMOOTH(false, false, false, 0, xout, cu1, cu2, cp1, cp2, g.ldg, 0, nch);
   else if (k == 0)
-    BIOT_LAUNCH((k_gmg_smooth<T, FM, false, false>), grid, kThreads, 0, s, L.n, coef_of<T>(L), L.dmask, xin, b, d,
-                xout, cu1, cu2, cp1, cp2, g.ldg, 0, nch);
+    BIOT_SMOOTH(false, false, false, DM_NO_STORE, xout, cu1, cu2, cp1, cp2, g.ldg, 0, nch);
+  else if (d_from_x && keep_d)
+    BIOT_SMOOTH(false, true, false, DM_FROM_X, xout, cu1, cu2, cp1, cp2, g.ldg, 0, nch);
+  else if (d_from_x)
+    BIOT_SMOOTH(false, true, false, DM_FROM_X | DM_NO_STORE, xout, cu1, cu2, cp1, cp2, g.ldg, 0, nch);
+  else if (keep_d)
+    BIOT_SMOOTH(false, true, false, 0, xout, cu1, cu2, cp1, cp2, g.ldg, 0, nch);
   else
-    BIOT_LAUNCH((k_gmg_smooth<T, FM, false, true>), grid, kThreads, 0, s, L.n, coef_of<T>(L), L.dmask, xin, b, d,
-                xout, cu1, cu2, cp1, cp2, g.ldg, 0, nch);
+    BIOT_SMOOTH(false, true, false, DM_NO_STORE, xout, cu1, cu2, cp1, cp2, g.ldg, 0, nch);
+#undef BIOT_SMOOTH
 }
 
 // One V-cycle on level l for the fields FM: x_out ~ K_l^{-1} b.
@@ -812,7 +843,7 @@ void vcycle(Gmg& g, int l, cudaStream_t s, const T* b, T* xout, int c0, int ncol
   // pre-smoothing from zero
   smooth_step<T, FM>(g, L, s, 0, true, nullptr, b, xa);
   for (int k = 1; k < g.smooth; ++k) {
-    smooth_step<T, FM>(g, L, s, k, false, xa, b, xb);
+    smooth_step<T, FM>(g, L, s, k, false, xa, b, xb, nullptr, k == 1);
     std::swap(xa, xb);
   }
   // coarse-grid correction
