@@ -354,8 +354,9 @@ typedef struct {
   int32_t strips;                       /* substructured block solves: strips (0: plain band) */
   int32_t variant_sep_u, variant_sep_p; /* substructured: separator variants (variant_*: interiors) */
   double ms_sep_u, ms_sep_p;            /* substructured: the separator pair's part of ms_u, ms_p */
-  int32_t spmm_variant;                 /* reduced precision: SpMM shape (0: 16-byte vectors, unroll 4,
-                                           2 CTAs per SM, 2 x 152 CTAs; others vary them) */
+  int32_t spmm_variant;                 /* reduced precision: SpMM shape 0-8 (0: 16-byte vectors, unroll 4,
+                                           2 CTAs per SM, 2 x 152 CTAs; 1-5 vary them; 6-7 deal the
+                                           nodes out to the grid's warps in turns) */
   double ms_spmm, ms_spmm_default;      /* one SpMM at full window: chosen shape, default shape */
 } biot_tuning;
 

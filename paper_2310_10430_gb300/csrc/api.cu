@@ -401,7 +401,7 @@ biot_status alloc_time_buffers(biot_ctx* ctx) {
   BIOT_TRY(dalloc(ctx, (void**)&ctx->F, sizeof(double) * nd * ld));
   BIOT_TRY(dalloc(ctx, (void**)&ctx->V, sizeof(double) * nd * wc * (lp ? 1 : ctx->n_iter + 1)));
   BIOT_TRY(dalloc(ctx, (void**)&ctx->Wv, sizeof(double) * nd * wc));
-  BIOT_TRY(dalloc(ctx, (void**)&ctx->part, sizeof(double) * kRedBlocks * (kMaxIter + 2) * wc));
+  BIOT_TRY(dalloc(ctx, (void**)&ctx->part, sizeof(double) * kPartBlocks * (kMaxIter + 2) * wc));
   BIOT_TRY(dalloc(ctx, (void**)&ctx->colscal, sizeof(double) * kColScalars * wc));
   BIOT_TRY(dalloc(ctx, (void**)&ctx->H, sizeof(double) * krylov_record_doubles() * wc));
   BIOT_TRY(dalloc(ctx, (void**)&ctx->hvec, sizeof(double) * 2 * (kMaxIter + 1) * wc));

@@ -31,6 +31,8 @@ extern std::atomic<int64_t> g_launches;
 // Fixed reduction grid: partial sums per block are reduced in a second pass in
 // block order, so every norm and dot product is deterministic.
 constexpr int kRedBlocks = 304;         // 2 x 152 SMs
+constexpr int kDotBlocks = 456;         // 3 x 152 SMs: the FP32 Gram-Schmidt dot products' grid (three CTAs per SM)
+constexpr int kPartBlocks = kDotBlocks > kRedBlocks ? kDotBlocks : kRedBlocks;
 constexpr int kMaxIter = 32;            // n_iter upper bound
 constexpr double kBreakdownRtol = 1e-14;  // lucky-breakdown test h_{j+1,j} <= rtol |A z_j|
 
@@ -180,7 +182,7 @@ struct biot_ctx {
   double* V = nullptr;          // (n_iter + 1) vectors
   double* Z = nullptr;          // n_iter vectors
   double* Wv = nullptr;         // Arnoldi candidate w
-  double* part = nullptr;       // [kRedBlocks][(kMaxIter + 2)][wcap] partial sums
+  double* part = nullptr;       // [kPartBlocks][(kMaxIter + 2)][wcap] partial sums
   double* colscal = nullptr;    // per-column scalars: see krylov.cu (layout kColScalars x wcap)
   double* H = nullptr;          // [wcap][(kMaxIter + 1) * kMaxIter]
   double* hvec = nullptr;       // [kMaxIter + 1][wcap] reduced dots of the current step

@@ -358,11 +358,11 @@ __device__ __forceinline__ void smooth_body(int n, const T* __restrict__ coef, c
   const int nx = n + 1;
   // 32-bit work index: the set-up keeps nodes x column chunks below 2^31
   const int total = nx * nx * nch;
-  // a contiguous range of the work per block, marched in steps of blockDim.x: consecutive steps
-  // cover neighbouring nodes, so most of a node's neighbour rows are still in L1
-  const int per = (total + gridDim.x - 1) / gridDim.x;
-  const int qb = blockIdx.x * per, qe = min(total, qb + per);
-  for (int q = qb + threadIdx.x; q < qe; q += blockDim.x) {
+  // grid-stride over (node, column chunk) in the natural node order: the whole grid works on a
+  // band of a few mesh rows at a time, so the neighbour rows a step needs were read one or two
+  // steps before and are still in L2 (contiguous ranges per CTA kept the whole level live and
+  // read x from DRAM about three times)
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
     const int v = q / nch, c = ca + (q - v * nch) * VEC;
     const int j = v / nx, i = v - j * nx;
     const T* cf = coef + (size_t)v * kCoef;
@@ -468,11 +468,11 @@ __device__ __forceinline__ void residual_body(int n, const T* __restrict__ coef,
   const int nx = n + 1;
   // 32-bit work index: the set-up keeps nodes x column chunks below 2^31
   const int total = nx * nx * nch;
-  // a contiguous range of the work per block, marched in steps of blockDim.x: consecutive steps
-  // cover neighbouring nodes, so most of a node's neighbour rows are still in L1
-  const int per = (total + gridDim.x - 1) / gridDim.x;
-  const int qb = blockIdx.x * per, qe = min(total, qb + per);
-  for (int q = qb + threadIdx.x; q < qe; q += blockDim.x) {
+  // grid-stride over (node, column chunk) in the natural node order: the whole grid works on a
+  // band of a few mesh rows at a time, so the neighbour rows a step needs were read one or two
+  // steps before and are still in L2 (contiguous ranges per CTA kept the whole level live and
+  // read x from DRAM about three times)
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
     const int v = q / nch, c = ca + (q - v * nch) * VEC;
     const int j = v / nx, i = v - j * nx;
     T y0[VEC], y1[VEC], y2[VEC];
@@ -517,11 +517,8 @@ __device__ __forceinline__ void restrict_body(int nc, const T* __restrict__ r, c
   const int cx = nc + 1, nf = 2 * nc;
   // 32-bit work index: the set-up keeps nodes x column chunks below 2^31
   const int total = cx * cx * nch;
-  // a contiguous range of the work per block, marched in steps of blockDim.x: consecutive steps
-  // cover neighbouring nodes, so most of a node's neighbour rows are still in L1
-  const int per = (total + gridDim.x - 1) / gridDim.x;
-  const int qb = blockIdx.x * per, qe = min(total, qb + per);
-  for (int q = qb + threadIdx.x; q < qe; q += blockDim.x) {
+  // grid-stride in the natural order of the coarse nodes (the fine rows stay in L2)
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
     const int V = q / nch, c = ca + (q - V * nch) * VEC;
     const int J = V / cx, i = 2 * (V - J * cx), j = 2 * J;
     T s0[VEC], s1[VEC], s2[VEC];

@@ -119,7 +119,7 @@ template <> struct KVec<double> {
 constexpr int kDotChunk = 8;
 constexpr int kFuseVecs = 12;  // basis vectors up to which the first update also forms the second's dots
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_dots_vec(const T* __restrict__ V, size_t vstride, int nvec, const T* __restrict__ w, int nrows, int ld, int c0,
            int ncols, double* __restrict__ part) {
   using VV = typename KVec<T>::V;
@@ -284,17 +284,20 @@ k_gs_axpy_rows_vec(const T* __restrict__ V, size_t vstride, int nvec, const doub
 // The first Gram-Schmidt sweep fused with the dot products of the second: w -= V h (h the
 // first sweep's coefficients, staged in shared memory as in k_gs_axpy_rows_vec; same
 // per-element arithmetic order), then the per-block partials of V_i . w with the updated w
-// as stored, in part[i][block][c]. The grid, the row partition, each thread's row order and
-// the block epilogue are those of k_dots_vec, so the partials are bit-identical to a separate
-// k_dots_vec pass over the stored w: one pass over V instead of two. V_i's row is read again
-// for the dot after the update (from L1/L2: the same 16 bytes the update just loaded).
-// Needs nvec <= NV (the dot accumulators live in registers).
+// as stored, in part[i][block][c]. The row partition, each thread's row order and the block
+// epilogue are k_dots_vec's, so on the same grid the partials are bit-identical to a separate
+// k_dots_vec pass over the stored w: one pass over V instead of two. V_i's row is read again for
+// the dot after the update (from L1/L2: the same 16 bytes the update just loaded). Needs
+// nvec <= NV: the dot accumulators live in registers, which leave room for two CTAs per SM, so
+// it runs on 2 x 152 CTAs (k_dots_vec on 3 x 152); 8-byte vectors on 3 x 152 measured 13 %
+// slower.
 template <typename T, int NV>
 __global__ void __launch_bounds__(256, 2)
 k_gs_axpy_dots_vec(const T* __restrict__ V, size_t vstride, int nvec, const double* __restrict__ h,
                    T* __restrict__ w, int nrows, int ld, int c0, int ncols, double* __restrict__ part) {
-  using VV = typename KVec<T>::V;
-  constexpr int VEC = KVec<T>::n;
+  using KV = KVec<T>;
+  using VV = typename KV::V;
+  constexpr int VEC = KV::n;
   __shared__ __align__(16) T sh[NV][32 * VEC];
   __shared__ double sm[8][32 * VEC];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -320,17 +323,17 @@ k_gs_axpy_dots_vec(const T* __restrict__ V, size_t vstride, int nvec, const doub
       for (int r = rb + warp; r < re; r += 8) {
         T* wr = w + (size_t)r * ld + c;
         T acc[VEC];
-        KVec<T>::get(*reinterpret_cast<const VV*>(wr), acc);
+        KV::get(*reinterpret_cast<const VV*>(wr), acc);
 #pragma unroll 4
         for (int i = 0; i < nvec; ++i) {
           T v[VEC], hq[VEC];
-          KVec<T>::get(*reinterpret_cast<const VV*>(V + (size_t)i * vstride + (size_t)r * ld + c), v);
-          KVec<T>::get(*reinterpret_cast<const VV*>(&sh[i][lane * VEC]), hq);
+          KV::get(*reinterpret_cast<const VV*>(V + (size_t)i * vstride + (size_t)r * ld + c), v);
+          KV::get(*reinterpret_cast<const VV*>(&sh[i][lane * VEC]), hq);
 #pragma unroll
           for (int q = 0; q < VEC; ++q) acc[q] -= hq[q] * v[q];
         }
         if (full) {
-          *reinterpret_cast<VV*>(wr) = KVec<T>::make(acc);
+          *reinterpret_cast<VV*>(wr) = KV::make(acc);
         } else {
 #pragma unroll
           for (int q = 0; q < VEC; ++q)
@@ -340,7 +343,7 @@ k_gs_axpy_dots_vec(const T* __restrict__ V, size_t vstride, int nvec, const doub
         for (int ii = 0; ii < NV; ++ii) {
           if (ii < nvec) {
             T v[VEC];
-            KVec<T>::get(*reinterpret_cast<const VV*>(V + (size_t)ii * vstride + (size_t)r * ld + c), v);
+            KV::get(*reinterpret_cast<const VV*>(V + (size_t)ii * vstride + (size_t)r * ld + c), v);
 #pragma unroll
             for (int q = 0; q < VEC; ++q) dacc[ii][q] += v[q] * acc[q];
           }
@@ -724,7 +727,7 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
     else BIOT_LAUNCH(k_scale_cols<T>, eblk, 256, 0, s, src, dst, cs + CS_INVH * ld, nd, ld, c0, ncols);
   };
   auto dots = [&](const T* Vb, int nvec, const T* w) {
-    if (vec) BIOT_LAUNCH(k_dots_vec<T>, kRedBlocks, 256, 0, s, Vb, vs, nvec, w, nd, ld, c0, ncols, ctx->part);
+    if (vec) BIOT_LAUNCH(k_dots_vec<T>, kDotBlocks, 256, 0, s, Vb, vs, nvec, w, nd, ld, c0, ncols, ctx->part);
     else BIOT_LAUNCH(k_dots<T>, dim3(kRedBlocks, nvec), 256, 0, s, Vb, vs, w, nd, ld, c0, ncols, ctx->part);
   };
   BIOT_LAUNCH(k_fgmres_init, cblk, 128, 0, s, cs, ld, c0, ncols, ctx->H, ctx->kcol);
@@ -745,7 +748,7 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
         continue;
       }
       dots(V, j + 1, Wv);
-      reduce_partials(ctx, j + 1, ncols, h, ld, c0);
+      reduce_partials(ctx, j + 1, ncols, h, ld, c0, vec ? kDotBlocks : kRedBlocks);
       if (fused)  // pass 0: w -= V h1 and the partials of V^T w for h2 in one pass over V
         if (j + 1 <= 8)
           BIOT_LAUNCH((k_gs_axpy_dots_vec<T, 8>), kRedBlocks, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0, ncols,

@@ -193,7 +193,12 @@ template <> struct VecN<float, 2> {
 // slots part[block * ld + column].
 // VEC (columns per lane) and UNR (neighbour-loop unrolling) are tuned per mesh and window
 // (biot_tune); the default is the 16-byte form with UNR = 4.
-template <typename XT, typename VT, int VEC = Vec16<XT>::n, int UNR = 4>
+// ILV: the nodes are dealt out to the warps of the grid in turns (warp w of block b takes nodes
+// (t gridDim.x + b) kWarps + w, t = 0, 1, ...) instead of a contiguous range per block: the grid
+// then works on a band of a few mesh rows at a time, and the neighbour rows of z in the mesh rows
+// above and below are still in L2 (with contiguous ranges the whole of z is live at once and
+// those rows came back from DRAM: 2.9 reads of z per launch instead of 1.3).
+template <typename XT, typename VT, int VEC = Vec16<XT>::n, int UNR = 4, bool ILV = false>
 __device__ __forceinline__ void spmm_vec_body(int nn, const int32_t* __restrict__ nodeptr,
               const int32_t* __restrict__ nbr, const int32_t* __restrict__ rowptr, const VT* __restrict__ val,
               const double* __restrict__ dsc, const XT* __restrict__ z, XT* __restrict__ w, int ld, int c0,
@@ -214,7 +219,8 @@ __device__ __forceinline__ void spmm_vec_body(int nn, const int32_t* __restrict_
     A ww[VEC];
 #pragma unroll
     for (int q = 0; q < VEC; ++q) ww[q] = 0;
-    for (int v = vb + warp; v < ve; v += kWarps) {
+    for (int v = ILV ? blockIdx.x * kWarps + warp : vb + warp; v < (ILV ? nn : ve);
+         v += ILV ? gridDim.x * kWarps : kWarps) {
       const int32_t np = nodeptr[v];
       const int deg = nodeptr[v + 1] - np;
       const int32_t r0 = rowptr[3 * v], r1 = r0 + 3 * deg, r2 = r1 + 3 * deg;
@@ -281,12 +287,12 @@ __device__ __forceinline__ void spmm_vec_body(int nn, const int32_t* __restrict_
   }
 }
 
-template <typename XT, typename VT, int VEC = Vec16<XT>::n, int UNR = 4, int MINB = 2>
+template <typename XT, typename VT, int VEC = Vec16<XT>::n, int UNR = 4, int MINB = 2, bool ILV = false>
 __global__ void __launch_bounds__(kWarps * 32, MINB)
 k_spmm_vec(int nn, const int32_t* __restrict__ nodeptr, const int32_t* __restrict__ nbr,
            const int32_t* __restrict__ rowptr, const VT* __restrict__ val, const double* __restrict__ dsc,
            const XT* __restrict__ z, XT* __restrict__ w, int ld, int c0, int ncols, double* __restrict__ part) {
-  spmm_vec_body<XT, VT, VEC, UNR>(nn, nodeptr, nbr, rowptr, val, dsc, z, w, ld, c0, ncols, part);
+  spmm_vec_body<XT, VT, VEC, UNR, ILV>(nn, nodeptr, nbr, rowptr, val, dsc, z, w, ld, c0, ncols, part);
 }
 
 template <typename XT, typename VT>
@@ -408,29 +414,32 @@ void launch_spmm_scaled<double>(biot_ctx* ctx, const double* z, double* w, int c
 }
 
 // Tuned shapes of the FP32 / BF16-value SpMM (biot_tune): columns per lane (16- or 8-byte
-// vectors), unrolling of the neighbour loop, CTAs per SM the registers are sized for, and the
-// grid in multiples of the 152 SMs (also the number of norm partials per column).
+// vectors), unrolling of the neighbour loop, CTAs per SM the registers are sized for, the grid
+// in multiples of the 152 SMs (also the number of norm partials per column) and whether the
+// nodes are dealt out in turns (ilv, shapes 6-7) or in a contiguous range per block.
 struct SpmmVariant {
-  int vec, unr, minb, gmul;
+  int vec, unr, minb, gmul, ilv;
 };
-constexpr SpmmVariant kSpmmVariants[] = {{4, 4, 2, 2}, {4, 2, 3, 3}, {4, 2, 4, 4}, {2, 4, 2, 2}, {2, 2, 4, 4},
-                                         {4, 1, 4, 4}};
+constexpr SpmmVariant kSpmmVariants[] = {{4, 4, 2, 2, 0}, {4, 2, 3, 3, 0}, {4, 2, 4, 4, 0}, {2, 4, 2, 2, 0},
+                                         {2, 2, 4, 4, 0}, {4, 1, 4, 4, 0}, {4, 2, 4, 4, 1}, {4, 1, 4, 4, 1}};
 constexpr int kSpmmVariantCount = sizeof(kSpmmVariants) / sizeof(kSpmmVariants[0]);
 
 template <typename VT>
 static void launch_spmm_variant(biot_ctx* ctx, int v, const VT* val, const float* z, float* w, int c0, int ncols) {
   const int grid = kSpmmVariants[v].gmul * 152;
-#define BIOT_SPMM_CASE(id, VEC, UNR, MINB)                                                                         \
+#define BIOT_SPMM_CASE(id, VEC, UNR, MINB, ILV)                                                                    \
   case id:                                                                                                          \
-    BIOT_LAUNCH((k_spmm_vec<float, VT, VEC, UNR, MINB>), grid, kWarps * 32, 0, ctx->stream, ctx->n_nodes,          \
+    BIOT_LAUNCH((k_spmm_vec<float, VT, VEC, UNR, MINB, ILV>), grid, kWarps * 32, 0, ctx->stream, ctx->n_nodes,     \
                 ctx->nodeptr, ctx->nbr, ctx->rowptr, val, ctx->dsc, z, w, ctx->wcap, c0, ncols, ctx->part);         \
     break;
   switch (v) {
-    BIOT_SPMM_CASE(1, 4, 2, 3)
-    BIOT_SPMM_CASE(2, 4, 2, 4)
-    BIOT_SPMM_CASE(3, 2, 4, 2)
-    BIOT_SPMM_CASE(4, 2, 2, 4)
-    BIOT_SPMM_CASE(5, 4, 1, 4)
+    BIOT_SPMM_CASE(1, 4, 2, 3, false)
+    BIOT_SPMM_CASE(2, 4, 2, 4, false)
+    BIOT_SPMM_CASE(3, 2, 4, 2, false)
+    BIOT_SPMM_CASE(4, 2, 2, 4, false)
+    BIOT_SPMM_CASE(5, 4, 1, 4, false)
+    BIOT_SPMM_CASE(6, 4, 2, 4, true)
+    BIOT_SPMM_CASE(7, 4, 1, 4, true)
     default:
       BIOT_LAUNCH((k_spmm_vec<float, VT>), grid, kWarps * 32, 0, ctx->stream, ctx->n_nodes, ctx->nodeptr, ctx->nbr,
                   ctx->rowptr, val, ctx->dsc, z, w, ctx->wcap, c0, ncols, ctx->part);

@@ -65,7 +65,7 @@ def test_tuning_writes_cache(tmp_path):
     assert '"variant"' in txt and json.loads(txt)["band_solve_variants"]
 
 
-N_SPMM_VARIANTS = 6
+N_SPMM_VARIANTS = 8
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
