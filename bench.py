@@ -657,6 +657,18 @@ def run_ours(args):
                 "applies": band_n, "launches_per_apply": launches_per_apply,
                 "avg_apply_ms": band_ms / band_n, "avg_launch_ms": band_ms / band_n / launches_per_apply,
                 "share_of_step": band_ms / ms}
+    if args.gmg:
+        # multigrid block solves (profiling runs): the V-cycle apply against HBM
+        hbm, src = _hbm_peak()
+        s_el = 8 if fp64 else 4
+        by_apply = gmg_apply_bytes(case.n, (W_ + 3) // 4 * 4, s_el, case.precond, GMG["smooth"], GMG["cycles"],
+                                   GMG["levels"])
+        ach = by_apply / (band_ms / band_n / 1e3) / 1e9
+        roofline = {"kernel": "k_gmg_* (multigrid V-cycle apply of P2: smoothing, residual, transfers, coarsest "
+                              "band solve)", "bound": "hbm", "achieved": ach, "peak": hbm, "peak_source": src,
+                    "unit": "GB/s", "frac": ach / hbm, "traffic": None, "traffic_per": "P apply",
+                    "bytes_per_apply": by_apply, "applies": band_n, "avg_apply_ms": band_ms / band_n,
+                    "share_of_step": band_ms / ms}
 
     streaming = streaming_kernels(info, hi - lo + 1, args.precision, res_ms, res_n, spmm_ms, spmm_n)
 
@@ -699,7 +711,8 @@ def run_ours(args):
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(case, W_),
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "f32"}[args.precision],
+            "data": "synthetic", "config": config_dict(case, W_),
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_s * 1e3},
