@@ -652,9 +652,10 @@ __global__ void k_gmg_coarse_prep(int nn, const T* __restrict__ b, const double*
 int grid_for(long long work) {
   return (int)std::max<long long>(1, std::min<long long>((work + kThreads - 1) / kThreads, 152 * 16));
 }
-// The stencil kernels' grid: one resident wave (8 CTAs of 256 threads per SM), each CTA marching
-// through a contiguous range of nodes.
-int grid_stencil(long long work) { return std::min(grid_for(work), 152 * 8); }
+// The stencil kernels' grid: they walk their work grid-stride, so the grid must be resident at
+// once to sweep the mesh as one band: four CTAs of 256 threads per SM (their 48-61 registers
+// allow four; with eight the second wave re-read the first wave's band boundaries).
+int grid_stencil(long long work) { return std::min(grid_for(work), 152 * 4); }
 
 struct GmgLevel {
   int n = 0, nn = 0;

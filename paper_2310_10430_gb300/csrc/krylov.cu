@@ -370,6 +370,88 @@ k_gs_axpy_dots_vec(const T* __restrict__ V, size_t vstride, int nvec, const doub
   }
 }
 
+// k_gs_axpy_dots_vec for up to kDotChunk basis vectors with the dot accumulators in shared
+// memory (each thread owns its slots; the per-column order of the sums is unchanged), which
+// frees the registers for three CTAs per SM: it runs on k_dots_vec's grid (3 x 152 CTAs), so its
+// partials are bit-identical to a k_dots_vec pass over the stored w.
+template <typename T>
+__global__ void __launch_bounds__(256, 3)
+k_gs_axpy_dots_smem(const T* __restrict__ V, size_t vstride, int nvec, const double* __restrict__ h,
+                    T* __restrict__ w, int nrows, int ld, int c0, int ncols, double* __restrict__ part) {
+  using KV = KVec<T>;
+  using VV = typename KV::V;
+  constexpr int VEC = KV::n;
+  constexpr int NV = kDotChunk;
+  __shared__ __align__(16) T sh[NV][32 * VEC];
+  __shared__ __align__(16) T dsm[8][NV][32 * VEC];
+  __shared__ double sm[8][32 * VEC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int per = (nrows + gridDim.x - 1) / gridDim.x;
+  const int rb = blockIdx.x * per, re = min(nrows, rb + per);
+  const int ca = c0 & ~(VEC - 1), ce = c0 + ncols;
+  for (int cb = ca; cb < ce; cb += 32 * VEC) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < nvec * 32 * VEC; t += blockDim.x) {
+      const int i = t / (32 * VEC), q = t % (32 * VEC), col = cb + q;
+      sh[i][q] = col < ld ? (T)h[(size_t)i * ld + col] : T(0);
+    }
+    T zero[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) zero[q] = T(0);
+    for (int ii = 0; ii < nvec; ++ii) *reinterpret_cast<VV*>(&dsm[warp][ii][lane * VEC]) = KV::make(zero);
+    __syncthreads();
+    const int c = cb + lane * VEC;
+    const bool any = c < ce;
+    const bool full = c >= c0 && c + VEC <= ce;
+    if (any) {
+      for (int r = rb + warp; r < re; r += 8) {
+        T* wr = w + (size_t)r * ld + c;
+        T acc[VEC];
+        KV::get(*reinterpret_cast<const VV*>(wr), acc);
+#pragma unroll 4
+        for (int i = 0; i < nvec; ++i) {
+          T v[VEC], hq[VEC];
+          KV::get(*reinterpret_cast<const VV*>(V + (size_t)i * vstride + (size_t)r * ld + c), v);
+          KV::get(*reinterpret_cast<const VV*>(&sh[i][lane * VEC]), hq);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) acc[q] -= hq[q] * v[q];
+        }
+        if (full) {
+          *reinterpret_cast<VV*>(wr) = KV::make(acc);
+        } else {
+#pragma unroll
+          for (int q = 0; q < VEC; ++q)
+            if (c + q >= c0 && c + q < ce) wr[q] = acc[q];
+        }
+#pragma unroll 2
+        for (int ii = 0; ii < nvec; ++ii) {
+          T v[VEC], d[VEC];
+          KV::get(*reinterpret_cast<const VV*>(V + (size_t)ii * vstride + (size_t)r * ld + c), v);
+          VV* slot = reinterpret_cast<VV*>(&dsm[warp][ii][lane * VEC]);
+          KV::get(*slot, d);
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) d[q] += v[q] * acc[q];
+          *slot = KV::make(d);
+        }
+      }
+    }
+    for (int ii = 0; ii < nvec; ++ii) {
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) sm[warp][lane * VEC + q] = (double)dsm[warp][ii][lane * VEC + q];
+      __syncthreads();
+      for (int t = threadIdx.x; t < 32 * VEC; t += blockDim.x) {
+        const int col = cb + t;
+        if (col >= c0 && col < ce) {
+          double sum = 0.0;
+          for (int u = 0; u < 8; ++u) sum += sm[u][t];
+          part[((size_t)ii * gridDim.x + blockIdx.x) * ld + col] = sum;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // scale_cols_body with 16-byte accesses (src may alias dst).
 template <typename T>
 __global__ void k_scale_cols_vec(const T* src, T* dst, const double* __restrict__ scale, int nrows, int ld, int c0,
@@ -742,7 +824,8 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
     for (int pass = 0; pass < 2; ++pass) {
       double* h = pass == 0 ? h1 : h2;
       if (fused && pass == 1) {
-        reduce_partials(ctx, j + 1, ncols, h, ld, c0);  // the fused first update formed the partials
+        // the fused first update formed the partials
+        reduce_partials(ctx, j + 1, ncols, h, ld, c0, j + 1 <= kDotChunk ? kDotBlocks : kRedBlocks);
         BIOT_LAUNCH((k_gs_axpy_rows_vec<T, true>), 2 * kRedBlocks, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0,
                     ncols, ctx->part);
         continue;
@@ -750,8 +833,8 @@ biot_status fgmres_cycle(biot_ctx* ctx, int lo, int c0, int ncols) {
       dots(V, j + 1, Wv);
       reduce_partials(ctx, j + 1, ncols, h, ld, c0, vec ? kDotBlocks : kRedBlocks);
       if (fused)  // pass 0: w -= V h1 and the partials of V^T w for h2 in one pass over V
-        if (j + 1 <= 8)
-          BIOT_LAUNCH((k_gs_axpy_dots_vec<T, 8>), kRedBlocks, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0, ncols,
+        if (j + 1 <= kDotChunk)
+          BIOT_LAUNCH(k_gs_axpy_dots_smem<T>, kDotBlocks, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0, ncols,
                       ctx->part);
         else
           BIOT_LAUNCH((k_gs_axpy_dots_vec<T, kFuseVecs>), kRedBlocks, 256, 0, s, V, vs, j + 1, h, Wv, nd, ld, c0,
