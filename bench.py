@@ -726,7 +726,7 @@ def run_ours(args):
         }
         out.update(extras)
         if "variants" in extras:
-            # the benchmark spec's bandwidth target is about the reduced-precision sweep: its HBM roofline,
+            # the bandwidth target of the method is the reduced-precision sweep: its HBM roofline,
             # for the multigrid block solves (the streaming form) and for the exact factorisations
             out["roofline_fp32"] = dict(extras["variants"]["fp32_gmg"]["roofline"],
                                         sweep="FP32 sweep of the bench workload (FP64 residual and update), "
