@@ -39,11 +39,6 @@ __device__ __forceinline__ void reduce_body(const double* __restrict__ part, int
   out[(size_t)s * ldo + c] = acc;
 }
 
-__global__ void k_reduce(const double* __restrict__ part, int nblocks, int nslots, int ld, int c0, int ncols,
-                         double* __restrict__ out, int ldo) {
-  reduce_body(part, nblocks, nslots, ld, c0, ncols, out, ldo);
-}
-
 // The same sums with one warp per column: lane l adds blocks l, l + 32, l + 64, ... in order,
 // then the 32 lane sums are combined by a fixed butterfly (a fixed tree: deterministic).
 // Block: 8 warps = 8 columns.
@@ -176,42 +171,10 @@ k_dots_vec(const T* __restrict__ V, size_t vstride, int nvec, const T* __restric
   }
 }
 
-// gs_axpy_body with 16-byte accesses (same per-element arithmetic order); stores only the
-// columns in [c0, c0 + ncols).
-template <typename T>
-__global__ void k_gs_axpy_vec(const T* __restrict__ V, size_t vstride, int nvec, const double* __restrict__ h,
-                              T* __restrict__ w, int nrows, int ld, int c0, int ncols) {
-  using VV = typename KVec<T>::V;
-  constexpr int VEC = KVec<T>::n;
-  const int ca = c0 & ~(VEC - 1), ce = c0 + ncols;
-  const int ngrp = (ce - ca + VEC - 1) / VEC;
-  const long long total = (long long)nrows * ngrp;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / ngrp), c = ca + (int)(idx % ngrp) * VEC;
-    T acc[VEC];
-    KVec<T>::get(*reinterpret_cast<const VV*>(w + (size_t)r * ld + c), acc);
-    for (int i = 0; i < nvec; ++i) {
-      T v[VEC];
-      KVec<T>::get(*reinterpret_cast<const VV*>(V + (size_t)i * vstride + (size_t)r * ld + c), v);
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) acc[q] -= (T)h[(size_t)i * ld + c + q] * v[q];
-    }
-    T* wr = w + (size_t)r * ld + c;
-    if (c >= c0 && c + VEC <= ce) {
-      *reinterpret_cast<VV*>(wr) = KVec<T>::make(acc);
-    } else {
-#pragma unroll
-      for (int q = 0; q < VEC; ++q)
-        if (c + q >= c0 && c + q < ce) wr[q] = acc[q];
-    }
-  }
-}
-
 // w -= V h on the columns [c0, c0 + ncols) with the blocks owning row ranges (warps stride
 // the rows, a lane owns VEC consecutive columns, so every row access is one coalesced 16-byte
 // vector per lane) and the coefficients h[i][c] staged in shared memory per 32 VEC columns.
-// Same per-element arithmetic order as k_gs_axpy_vec. NORM: also the per-block partial sums
+// Same per-element arithmetic order as gs_axpy_body. NORM: also the per-block partial sums
 // of |w|^2 after the update, in part[block][c] (the layout k_dots_vec writes for one vector),
 // which saves the separate norm pass of the second Gram-Schmidt sweep.
 template <typename T, bool NORM>
